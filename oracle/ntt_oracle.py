@@ -1,0 +1,236 @@
+"""FP64 CPU oracle for the non-negative tensor-train (nTT) hot path.
+
+TEST INFRASTRUCTURE ONLY.  Imported by tests/, __graft_entry__.smoke() and the
+benchmark's CPU-baseline / reference legs; the CUDA product path never imports,
+links or calls anything here, and nothing here imports the CUDA path.
+
+Plain, slow, obviously-correct numpy in float64.  Every function cites the part
+of the paper it restates:
+
+* Eq. (2)  tensor-train element formula            -> tt_entry, tt_full
+* Eq. (3)  relative reconstruction error           -> rel_error
+* Eq. (4)  compression ratio                       -> compression_ratio
+* Algorithm 2 (distnTT) with fixed TT ranks        -> ntt_decompose
+* Algorithm 1 (distReshape) as a C-order reshape   -> unfold
+* Multiplicative-update NMF (Lee-Seung), which the paper times against BCD in
+  Section IV (strong scaling, Fig. 7c); update order H then W, epsilon added to
+  both denominators                                -> mu_update_H, mu_update_W, nmf_mu
+* objective 1/2 ||X - WH||_F^2 (Algorithm 3's objective)   -> objective
+* counter-based SplitMix64 initialisation (the paper only says "rand") -> uniform01
+
+Readings where the paper is silent or garbled (the list is repeated in the
+design notes):
+* initial factors are plain U[0,1) (Algorithm 3's normalised init is for BCD);
+* after each stage every column of W is divided by its L1 norm and the norm is
+  folded into the matching row of H (the product W H is unchanged); a zero
+  column is left as it is;
+* the unfolding X_l is (r_{l-1} n_l) x prod_{j>l} n_j (Algorithm 2's comment on
+  S is inconsistent; this is the shape its reshape produces);
+* best restart = lowest final objective, ties to the lowest restart index.
+
+Parity pins for every function live in tests/test_oracle_pins.py.  No function
+here is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+EPS_MU = 1e-12
+
+# --------------------------------------------------------------------------
+# Counter-based SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom
+# number generators", OOPSLA 2014).  Generator state advances by the golden
+# gamma; each output is the state passed through the 64-bit finaliser.  The
+# i-th output (0-based) of a generator seeded with s is mix64(s + (i+1)*gamma).
+# --------------------------------------------------------------------------
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z):
+    z = np.asarray(z, dtype=np.uint64)
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64_outputs(seed, index):
+    """Outputs number `index` (array, 0-based) of SplitMix64 seeded with `seed`."""
+    idx = np.asarray(index, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64(np.uint64(seed) + (idx + np.uint64(1)) * _GAMMA)
+
+
+def stream_key(seed, stage, restart, matrix):
+    """Key of the random stream for (stage, restart, matrix); matrix 0 = W, 1 = H.
+
+    key = output number (stage * 2^20 + restart * 2 + matrix) of SplitMix64(seed).
+    """
+    stream = (int(stage) << 20) + (int(restart) << 1) + int(matrix)
+    return int(splitmix64_outputs(int(seed), stream))
+
+
+def uniform01(key, index):
+    """U[0,1) values (x >> 40) * 2^-24 of SplitMix64(key) outputs at `index`.
+
+    24-bit values: exact in FP32 and FP64.
+    """
+    x = splitmix64_outputs(key, index) >> np.uint64(40)
+    return x.astype(np.float64) * (1.0 / 16777216.0)
+
+
+def init_factors(m, n, r, seed, stage, restart=0):
+    """W0 (m x r) and H0 (r x n), row-major element order, from the counter RNG."""
+    kw = stream_key(seed, stage, restart, 0)
+    kh = stream_key(seed, stage, restart, 1)
+    W0 = uniform01(kw, np.arange(m * r, dtype=np.uint64)).reshape(m, r)
+    H0 = uniform01(kh, np.arange(r * n, dtype=np.uint64)).reshape(r, n)
+    return W0, H0
+
+
+def init_columns_H(n, r, seed, stage, cols, restart=0):
+    """Columns `cols` of H0 (r x len(cols)) without forming all of H0."""
+    kh = stream_key(seed, stage, restart, 1)
+    cols = np.asarray(cols, dtype=np.uint64)
+    idx = np.arange(r, dtype=np.uint64)[:, None] * np.uint64(n) + cols[None, :]
+    return uniform01(kh, idx)
+
+
+# --------------------------------------------------------------------------
+# Multiplicative-update NMF.
+# --------------------------------------------------------------------------
+
+def mu_update_H(X, W, H, eps=EPS_MU):
+    """H <- max(0, H * (W^T X) / (W^T W H + eps))."""
+    num = W.T @ X
+    den = (W.T @ W) @ H + eps
+    return np.maximum(0.0, H * num / den)
+
+
+def mu_update_W(X, W, H, eps=EPS_MU):
+    """W <- max(0, W * (X H^T) / (W (H H^T) + eps))."""
+    num = X @ H.T
+    den = W @ (H @ H.T) + eps
+    return np.maximum(0.0, W * num / den)
+
+
+def objective(X, W, H):
+    """1/2 ||X - W H||_F^2 computed directly (no expanded Gram form)."""
+    R = X - W @ H
+    return 0.5 * float(np.sum(R * R))
+
+
+def nmf_mu(X, W0, H0, iters, eps=EPS_MU, record=True):
+    """Run `iters` full multiplicative-update iterations, H first then W.
+
+    Returns (W, H, trace) where trace[t] = 1/2 ||X - W_{t+1} H_{t+1}||^2.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    W = np.array(W0, dtype=np.float64)
+    H = np.array(H0, dtype=np.float64)
+    trace = []
+    for _ in range(int(iters)):
+        H = mu_update_H(X, W, H, eps)
+        W = mu_update_W(X, W, H, eps)
+        if record:
+            trace.append(objective(X, W, H))
+    return W, H, np.array(trace)
+
+
+def handoff_normalize(W, H):
+    """Divide each column of W by its L1 norm and multiply the matching row of H by it."""
+    W = np.array(W, dtype=np.float64)
+    H = np.array(H, dtype=np.float64)
+    s = W.sum(axis=0)
+    for j in range(W.shape[1]):
+        if s[j] > 0.0:
+            W[:, j] /= s[j]
+            H[j, :] *= s[j]
+    return W, H
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 with fixed ranks.
+# --------------------------------------------------------------------------
+
+def unfold(T, m):
+    """Algorithm 1 on one device: the C-order reshape of T into m x (size/m)."""
+    T = np.asarray(T)
+    return T.reshape(m, T.size // m)
+
+
+def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True):
+    """Non-negative tensor train of A with given TT ranks (Algorithm 2).
+
+    Stage l (0-based s = l-1): X = reshape(current, r_{l-1} n_l, rest); NMF of
+    rank r_l by multiplicative updates from the counter-RNG init; W becomes core
+    G_l (r_{l-1} x n_l x r_l) after the column-L1 hand-off normalisation and H
+    becomes the next `current`.  The last core is the final H.
+    Returns (cores, traces), traces[s] = objective trace of the kept restart.
+    """
+    A = np.asarray(A)
+    dims = A.shape
+    d = len(dims)
+    ranks = tuple(int(r) for r in ranks)
+    if len(ranks) != d + 1 or ranks[0] != 1 or ranks[-1] != 1:
+        raise ValueError("ranks must have d+1 entries with r_0 = r_d = 1")
+    cur = A.astype(np.float64)
+    cores, traces = [], []
+    for s in range(d - 1):
+        m = ranks[s] * dims[s]
+        n = math.prod(dims[s + 1:])
+        r = ranks[s + 1]
+        if r > min(m, n):
+            raise ValueError(f"rank r_{s+1}={r} exceeds min(m, n)=min({m},{n})")
+        X = unfold(cur, m)
+        best = None
+        for rs in range(restarts):
+            W0, H0 = init_factors(m, n, r, seed, s, rs)
+            W, H, tr = nmf_mu(X, W0, H0, iters, eps, record=True)
+            if best is None or tr[-1] < best[2][-1]:
+                best = (W, H, tr)
+        W, H, tr = best
+        W, H = handoff_normalize(W, H)
+        cores.append(W.reshape(ranks[s], dims[s], r))
+        traces.append(tr)
+        cur = H
+    cores.append(cur.reshape(ranks[d - 1], dims[d - 1], 1))
+    return cores, traces
+
+
+# --------------------------------------------------------------------------
+# Eq. (2)-(4).
+# --------------------------------------------------------------------------
+
+def tt_entry(cores, idx):
+    """Eq. (2): A[i_1..i_d] = G1[:, i_1, :] G2[:, i_2, :] ... Gd[:, i_d, :] (a 1x1 product)."""
+    v = np.ones((1, 1))
+    for g, i in zip(cores, idx):
+        v = v @ np.asarray(g, dtype=np.float64)[:, int(i), :]
+    return float(v[0, 0])
+
+
+def tt_full(cores):
+    """Eq. (2) for every index: contract the cores left to right into the full tensor."""
+    dims = [g.shape[1] for g in cores]
+    acc = np.asarray(cores[0], dtype=np.float64).reshape(dims[0], cores[0].shape[2])
+    for g in cores[1:]:
+        g = np.asarray(g, dtype=np.float64)
+        acc = np.tensordot(acc, g, axes=([acc.ndim - 1], [0]))
+    return acc.reshape(dims)
+
+
+def rel_error(A, cores):
+    """Eq. (3): ||A - A~||_F / ||A||_F with A~ the tensor of `cores`."""
+    A = np.asarray(A, dtype=np.float64)
+    At = tt_full(cores)
+    return float(np.linalg.norm((A - At).ravel()) / np.linalg.norm(A.ravel()))
+
+
+def compression_ratio(dims, ranks):
+    """Eq. (4): prod(n_i) / sum_i n_i r_{i-1} r_i."""
+    return math.prod(dims) / sum(n * ranks[i] * ranks[i + 1] for i, n in enumerate(dims))
