@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the non-negative tensor-train hot path on one GB300.
+
+Workload (one "step" = one job): the 6-way 32^6 FP32 tensor (1.07e9 entries,
+4.3 GB) built from random non-negative TT cores U[0,1) with ranks
+(1,8,16,16,16,8,1) plus 1% |Gaussian| noise; a job is the whole nTT
+(Algorithm 2: five NMFs of 200 multiplicative-update iterations each, hand-off
+normalisation, FP64 stage objectives) followed by the relative error of
+Eq. (3).  Inputs are synthetic and seeded; the tensor is larger than L2, so
+no flush is needed between steps.
+
+  value      NTT jobs/s with A resident in HBM (CUDA events on the stream)
+  e2e        the same through the host-buffer C-ABI call (A host->device,
+             cores and error device->host inside the timed region)
+  roofline   the dominant kernel: the fused MU pass of stage 1
+             (32 x 33,554,432, r = 8), algorithmic bytes m n 4 + 8 r n per
+             iteration over the measured iteration time, against the
+             measured HBM copy bandwidth
+  cpu_baseline  the FP64 oracle on the host cores on a bounded sample of the
+             same job, extrapolated to jobs/s
+
+Multi-GPU (torchrun): every rank runs its own independent job (the jobs
+share nothing), value = all ranks' jobs / max time over ranks.
+`--impl reference` times the FP64 oracle instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NMF-MU iterations/sec and HBM GB/s (% roofline) per NTT; NTT jobs/sec, p50/p99"
+UNIT = "NTT jobs/s"
+WORKLOAD = "c2_32x6"
+
+# DRAM traffic of one launch of the dominant kernel from an ncu capture, valid
+# only for the kernel source it was measured on (hash of mu_pass_impl.cuh).
+NCU_TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _kernel_sha():
+    p = os.path.join(ROOT, "paper_2008_01340_gb300", "csrc", "mu_pass_impl.cuh")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            f = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=f, stderr=subprocess.DEVNULL)
+            self._f = f
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = max(smax, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the job
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(A, cfg, budget_s=15.0):
+    """Time the oracle's MU iterations on column samples of every stage's
+    unfolding (about budget_s seconds in total) and extrapolate the whole job
+    (iterations x columns)."""
+    import numpy as np
+    import oracle
+    import synth
+
+    dims, ranks, iters = cfg["dims"], cfg["ranks"], cfg["iters"]
+    shapes = synth.stage_shapes(dims, ranks)
+    per_stage = budget_s / len(shapes)
+    total_s = 0.0
+    desc = []
+    spent = 0.0
+    for s, (m, n, r) in enumerate(shapes):
+        cols = min(n, max(1024, (1 << 25) // m))        # ~33M entries per sample
+        if s == 0:
+            X = np.ascontiguousarray(A.reshape(m, n)[:, :cols], dtype=np.float64)
+            src = "tensor columns"
+        else:
+            X = synth.uniform_matrix((m, cols), 900 + s).astype(np.float64)
+            src = "U[0,1) stand-in of H_{k-1}; the cost does not depend on the values"
+        W0 = synth.uniform_matrix((m, r), 800 + s).astype(np.float64)
+        H0 = synth.uniform_matrix((r, cols), 700 + s).astype(np.float64)
+        k = 0
+        t0 = time.perf_counter()
+        W, H = W0, H0
+        while True:
+            W, H, _ = oracle.nmf_mu(X, W, H, 1)
+            k += 1
+            el = time.perf_counter() - t0
+            if k >= 2 and (el >= per_stage or k >= 50):
+                break
+        dt = el / k
+        spent += el
+        total_s += dt * iters * (n / cols)
+        desc.append(f"stage {s+1}: {k} iters on {m}x{cols} of {m}x{n} ({src})")
+    cores = os.cpu_count() or 1
+    return {"value": 1.0 / total_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "; ".join(desc) + f"; extrapolated to {iters} iters x all columns per stage "
+                      f"(extrapolated job time {total_s:.1f} s)",
+            "seconds_spent": round(spent, 2)}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import synth
+    cfg = synth.CONFIGS[WORKLOAD]
+    A, _ = synth.tt_tensor(cfg["dims"], cfg["ranks"], cfg["core_dist"], cfg["noise"],
+                           cfg["data_seed"])
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(A, cfg, budget_s=10.0)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "note": "FP64 numpy oracle on host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ntt", choices=["ntt", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2008_01340_gb300 as ntt
+    from paper_2008_01340_gb300 import _build
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    ntt.lib()
+    dev = torch.device("cuda", local)
+
+    cfg = synth.CONFIGS[WORKLOAD]
+    dims, ranks, iters = cfg["dims"], cfg["ranks"], cfg["iters"]
+    N = math.prod(dims)
+    A_host = torch.empty(N, dtype=torch.float32).pin_memory()
+    A_np, info = synth.tt_tensor(dims, ranks, cfg["core_dist"], cfg["noise"], cfg["data_seed"],
+                                 out=A_host.numpy())
+    Ad = A_host.to(dev, non_blocking=False)
+    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, "f32", 0, cfg["init_seed"])
+    ws = ntt.empty_workspace(plan.workspace_size(), dev)
+    ws_rel = ntt.empty_workspace(ntt.ntt_reconstruct_workspace_size(dims, ranks), dev)
+    cores = [torch.empty(s, dtype=torch.float32, device=dev) for s in plan.core_shapes()]
+    err = torch.zeros(3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ntt.ntt_decompose(plan, Ad, cores, ws, stream)
+        ntt.ntt_rel_error(dims, ranks, cores, Ad, err, ws_rel, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stats = ntt.ntt_plan_get_stats(plan)
+    rel_err = float(err[0].item())
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1e3 / ms
+
+    # ---- end to end through the host-buffer C-ABI call
+    e2e_steps = args.e2e_steps or args.steps
+    ws_host = ntt.empty_workspace(plan.workspace_size_host(), dev)
+    cores_h = [torch.empty(s, dtype=torch.float32).pin_memory() for s in plan.core_shapes()]
+    err_h = torch.zeros(3, dtype=torch.float64).pin_memory()
+    ntt.ntt_decompose_host(plan, A_host, cores_h, ws_host, err_h, stream)   # warm (graph build)
+    torch.cuda.synchronize(dev)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        ntt.ntt_decompose_host(plan, A_host, cores_h, ws_host, err_h, stream)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = N * 4
+    d2h = sum(math.prod(s) for s in plan.core_shapes()) * 4 + 3 * 8
+
+    # ---- roofline of the dominant kernel (stage-1 fused pass)
+    st1 = stats["stages"][0]
+    per_iter_s = st1["iter_ms"] / 1e3 / st1["iters"]
+    achieved = st1["alg_bytes"] / per_iter_s / 1e9
+    peak, peak_src = _peaks()
+    traffic = None
+    if NCU_TRAFFIC["kernel_sha"] == _kernel_sha():
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "mu_pass_kernel<MP=32,R=8,f32> + combine, stage 1 (32 x 33554432, r=8)",
+                "alg_bytes_per_launch": st1["alg_bytes"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+
+    rel_launches = 0
+    # Eq. (3): chain products left and right of the split point, then one residual pass
+    s_split = 3
+    rel_launches = (s_split - 1) + (len(dims) - 1 - s_split) + 1
+    launches = (stats["launches"] + rel_launches) * args.steps
+
+    stage_rows = []
+    for s, st in enumerate(stats["stages"]):
+        it_s = st["iter_ms"] / 1e3 / st["iters"]
+        stage_rows.append({
+            "m": st["m"], "n": st["n"], "r": st["r"], "iters": st["iters"],
+            "mu_iters_per_s": round(1.0 / it_s, 1) if it_s > 0 else None,
+            "alg_GBps": round(st["alg_bytes"] / it_s / 1e9, 1) if it_s > 0 else None,
+            "frac_hbm": round(st["alg_bytes"] / it_s / 1e9 / peak, 4) if it_s > 0 else None,
+            "stage_ms": round(st["stage_ms"], 3),
+            "resid_half_sq": st["resid"], "xnorm2": st["xnorm2"]})
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": 32^6 FP32 tensor from random U[0,1) TT cores, ranks "
+                   "(1,8,16,16,16,8,1), 1% |Gaussian| noise; 200 MU iterations per unfolding + Eq. (3)",
+                   "global_batch": world, "l2_policy": "inputs larger than L2 (4.3 GB tensor)",
+                   "parallelism": f"independent jobs x{world}"},
+        "roofline": roofline,
+        "e2e": {"value": round(world * 1e3 / e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "rel_error": rel_err,
+        "stages": stage_rows,
+        "mu_iters_per_s_stage1": stage_rows[0]["mu_iters_per_s"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A_np, cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * ntt.h -- C ABI of the GB300 non-negative tensor-train (nTT) library.
+ *
+ * The library computes the nTT of a dense non-negative tensor by the chain of
+ * non-negative matrix factorisations of Algorithm 2 ("distnTT") of Bhattarai
+ * et al., "Distributed Non-Negative Tensor Train Decomposition": stage l
+ * factors the unfolding X_l (r_{l-1} n_l x prod_{j>l} n_j) as W H with
+ * W, H >= 0; W becomes TT core G_l (r_{l-1} x n_l x r_l) and H becomes the
+ * next unfolding; the last core is the final H.  Each NMF is iterated with
+ * the Lee-Seung multiplicative updates the paper times in Section IV:
+ *     H <- max(0, H o (W^T X) / (W^T W H + eps))
+ *     W <- max(0, W o (X H^T) / (W H H^T + eps))
+ * TT ranks are given (the paper's SVD rank rule of Algorithm 2 is not built:
+ * NULL ranks return NTT_ERR_UNSUPPORTED).
+ *
+ * Conventions for every entry point:
+ *  - All arrays are dense, row-major (C order).  Device pointers must point to
+ *    memory of the current CUDA device; host pointers are ordinary host memory
+ *    (pinned memory makes the host variants asynchronous).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it and the call returns without waiting,
+ *    unless stated otherwise.
+ *  - The caller allocates and frees every device buffer (tensor, cores,
+ *    factors, workspace).  The library owns only plan objects (host memory and
+ *    cached CUDA graphs) and never allocates device memory.
+ *  - Argument, shape and rank-feasibility errors are returned synchronously
+ *    and nothing is launched.  Device-side errors (a bounded wait that timed
+ *    out) are written to a status word in the workspace and reported by
+ *    ntt_plan_get_stats / ntt_status_of_workspace after the stream is synced.
+ *  - No call ever falls back to a CPU implementation.
+ */
+#ifndef NTT_H
+#define NTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NTT_MAX_D 16      /* maximum tensor order d */
+#define NTT_MAX_RANK 32   /* maximum TT rank r_k */
+#define NTT_MAX_ROWS 512  /* maximum unfolding height r_{k-1} n_k */
+
+typedef enum {
+  NTT_OK = 0,
+  NTT_ERR_INVALID_ARG = 1,      /* NULL pointer, bad size, bad enum */
+  NTT_ERR_RANK_INFEASIBLE = 2,  /* r_k > min(r_{k-1} n_k, prod_{j>k} n_j) (Alg. 2: N = min(m, n)) */
+  NTT_ERR_OOM = 3,              /* workspace too small / host allocation failed */
+  NTT_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  NTT_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (device status word) */
+  NTT_ERR_UNSUPPORTED = 6       /* shape or option outside what is built */
+} ntt_status;
+
+typedef enum { NTT_F32 = 0, NTT_BF16 = 1 } ntt_dtype;
+
+typedef struct ntt_plan_s* ntt_plan;
+
+/* Plan description (Algorithm 2's inputs with fixed ranks). */
+typedef struct {
+  int d;                 /* tensor order, 2 <= d <= NTT_MAX_D */
+  const int64_t* dims;   /* d mode sizes n_1..n_d (host) */
+  const int64_t* ranks;  /* d+1 TT ranks r_0..r_d with r_0 = r_d = 1 (host) */
+  int iters;             /* multiplicative-update iterations per stage (>= 1) */
+  float eps_mu;          /* epsilon added to both MU denominators (e.g. 1e-12) */
+  ntt_dtype x_dtype;     /* NTT_F32, or NTT_BF16: each unfolding is cast to BF16 and
+                            iterated with FP32 accumulation, then refined in FP32 */
+  int refine_iters;      /* FP32 iterations after the BF16 ones (BF16 form only) */
+  uint64_t seed;         /* seed of the counter-based initialisation */
+} ntt_plan_desc;
+
+/* Per-stage statistics, filled by ntt_plan_get_stats after the last call. */
+typedef struct {
+  int d;                            /* tensor order of the plan */
+  int status;                       /* device status word (ntt_status) */
+  int iters[NTT_MAX_D];             /* MU iterations run per stage (BF16 + FP32) */
+  int64_t m[NTT_MAX_D], n[NTT_MAX_D], r[NTT_MAX_D];   /* unfolding shapes */
+  double xnorm2[NTT_MAX_D];         /* ||X_l||_F^2 (FP64 reduction) */
+  double obj_first[NTT_MAX_D];      /* 1/2||X-WH||^2 after the first iteration (Gram form) */
+  double obj_last[NTT_MAX_D];       /* same after the last iteration (Gram form) */
+  double resid[NTT_MAX_D];          /* 1/2||X-WH||^2 at stage end, direct FP64 pass */
+  float stage_ms[NTT_MAX_D];        /* device time of each stage (CUDA events) */
+  float iter_ms[NTT_MAX_D];         /* device time of the stage's MU iteration loop */
+  float total_ms;                   /* device time of the whole decomposition */
+  double alg_bytes[NTT_MAX_D];      /* algorithmic bytes of one MU iteration of the stage:
+                                       m n sizeof(X) + 8 r n (X read once, H read+written) */
+  int64_t launches;                 /* kernels launched by one decomposition */
+} ntt_stats;
+
+/* Human-readable name of a status code (static string). */
+const char* ntt_status_string(ntt_status s);
+
+/* Library version string (static). */
+const char* ntt_version(void);
+
+/* Validate `desc` and build a plan (host only, no device work).  Checks the
+ * ranks against Algorithm 2's feasibility bound r_k <= min(r_{k-1} n_k,
+ * prod_{j>k} n_j), r_k <= NTT_MAX_RANK and r_{k-1} n_k <= NTT_MAX_ROWS.
+ * On success *out owns a plan to be released with ntt_plan_destroy. */
+ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out);
+
+/* Device workspace bytes needed by ntt_decompose with this plan. */
+ntt_status ntt_plan_workspace_size(ntt_plan plan, size_t* bytes);
+
+/* Device workspace bytes needed by ntt_decompose_host (adds room for A). */
+ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes);
+
+/* Algorithm 2 on the device.
+ *   A         device, prod(dims) FP32 entries, C order, >= 0; read only.
+ *   cores     host array of d device pointers; core k (0-based) receives
+ *             G_{k+1} as r_k x n_{k+1} x r_{k+1} FP32 (written).
+ *   workspace device, >= ntt_plan_workspace_size bytes, 256-byte aligned;
+ *             overwritten.
+ * Stage l uses W = core l as its m x r factor and H in the workspace (the
+ * last stage writes H straight into the last core), so no reshape copies are
+ * made: each reshape of Algorithm 1/2 is a C-order view.  The whole
+ * decomposition is one cached CUDA graph per (A, cores, workspace) triple,
+ * launched on `stream`. */
+ntt_status ntt_decompose(ntt_plan plan, const float* A, float* const* cores,
+                         void* workspace, void* stream);
+
+/* Same as ntt_decompose with A and the cores in HOST memory: A is copied to
+ * the workspace, the decomposition runs, the cores are copied back, all on
+ * `stream` (asynchronous with pinned host memory; sync before reading).
+ * err_host (nullable, 3 doubles) receives Eq. (3) of the result as
+ * ntt_rel_error reports it.  workspace: ntt_plan_workspace_size_host bytes. */
+ntt_status ntt_decompose_host(ntt_plan plan, const float* A_host, float* const* cores_host,
+                              double* err_host, void* workspace, void* stream);
+
+/* Synchronise the stream of the last decomposition and read its statistics. */
+ntt_status ntt_plan_get_stats(ntt_plan plan, ntt_stats* out);
+
+/* Release a plan and its cached graphs. */
+ntt_status ntt_plan_destroy(ntt_plan plan);
+
+/* Workspace bytes for nmf_mu_step on an m x n problem of rank r. */
+ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype, size_t* bytes);
+
+/* `iters` multiplicative-update iterations (H first, then W) of one NMF,
+ * in place on W and H -- the inner loop of every stage of Algorithm 2.
+ *   X       device m x n, FP32 (x_dtype NTT_F32) or BF16 (NTT_BF16), >= 0.
+ *   W       device m x r FP32 (in/out), H device r x n FP32 (in/out).
+ *   obj_dev device array of `iters` doubles or NULL; obj_dev[t] receives
+ *           1/2||X - W_{t+1} H_{t+1}||_F^2 in the expanded Gram form
+ *           ||X||^2 - 2<W, X H^T> + <W^T W, H H^T>, reduced in FP64.
+ *   ws      device workspace of nmf_mu_workspace_size bytes (overwritten).
+ * 1 <= r <= NTT_MAX_RANK, 1 <= m <= NTT_MAX_ROWS, n >= 1. */
+ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
+                       float* W, float* H, int iters, float eps_mu, double* obj_dev,
+                       void* ws, void* stream);
+
+/* Device status word left in an nmf_mu_step workspace (sync first). */
+ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out);
+
+/* Counter-based U[0,1) fill: out[i] = (SplitMix64(key) output i >> 40) * 2^-24
+ * with key = SplitMix64(seed) output (stage * 2^20 + restart * 2 + matrix)
+ * (Steele, Lea & Flood 2014).  This is the initialisation of W (matrix 0)
+ * and H (matrix 1) in every stage.  out: device, `count` FP32. */
+ntt_status ntt_uniform_init(uint64_t seed, int stage, int restart, int matrix, int64_t count,
+                            float* out, void* stream);
+
+/* Workspace bytes of ntt_reconstruct / ntt_rel_error for these cores. */
+ntt_status ntt_reconstruct_workspace_size(int d, const int64_t* dims, const int64_t* ranks,
+                                          size_t* bytes);
+
+/* Eq. (2): the full tensor of a TT.  cores: host array of d device pointers
+ * (core k is r_k x n_{k+1} x r_{k+1} FP32); A_out device prod(dims) FP32.
+ * The chain is split at the mode s that balances the two halves: the
+ * products G_1..G_s and G_{s+1}..G_d are formed first, then multiplied. */
+ntt_status ntt_reconstruct(int d, const int64_t* dims, const int64_t* ranks,
+                           const float* const* cores, float* A_out, void* ws, void* stream);
+
+/* Eq. (3): err_dev[0] = ||A - A~||_F / ||A||_F (FP64), A~ the TT of `cores`,
+ * computed without materialising A~ (split-chain product fused with the
+ * difference and an FP64 reduction).  A: device prod(dims) FP32.
+ * err_dev[1] and err_dev[2] receive ||A - A~||^2 and ||A||^2. */
+ntt_status ntt_rel_error(int d, const int64_t* dims, const int64_t* ranks,
+                         const float* const* cores, const float* A, double* err_dev,
+                         void* ws, void* stream);
+
+/* Eq. (4): prod n_i / sum n_i r_{i-1} r_i (host arithmetic). */
+double ntt_compression_ratio(int d, const int64_t* dims, const int64_t* ranks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_H */

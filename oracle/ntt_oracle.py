@@ -170,7 +170,8 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True):
     rank r_l by multiplicative updates from the counter-RNG init; W becomes core
     G_l (r_{l-1} x n_l x r_l) after the column-L1 hand-off normalisation and H
     becomes the next `current`.  The last core is the final H.
-    Returns (cores, traces), traces[s] = objective trace of the kept restart.
+    Returns (cores, traces), traces[s] = objective trace of the kept restart
+    (with record=False only the final objective of each stage).
     """
     A = np.asarray(A)
     dims = A.shape
@@ -190,7 +191,9 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True):
         best = None
         for rs in range(restarts):
             W0, H0 = init_factors(m, n, r, seed, s, rs)
-            W, H, tr = nmf_mu(X, W0, H0, iters, eps, record=True)
+            W, H, tr = nmf_mu(X, W0, H0, iters, eps, record=record)
+            if not record:
+                tr = np.array([objective(X, W, H)])
             if best is None or tr[-1] < best[2][-1]:
                 best = (W, H, tr)
         W, H, tr = best

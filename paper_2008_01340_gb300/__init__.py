@@ -1,0 +1,360 @@
+"""Python binding of libntt (the GB300 non-negative tensor-train library).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libntt.so (built in-tree from csrc/ by `build()`).  Tensors are
+torch CUDA tensors (device pointers via data_ptr()); streams are torch CUDA
+streams (default: the current stream).  There is no CPU fallback: a missing
+library or a failing call raises.
+
+Entry points mirror include/ntt.h:
+  ntt_plan_create / Plan.workspace_size / ntt_decompose / ntt_decompose_host /
+  ntt_plan_get_stats / nmf_mu_step / nmf_mu_workspace_size /
+  ntt_reconstruct / ntt_rel_error / ntt_uniform_init / ntt_compression_ratio
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libntt.so")
+
+NTT_MAX_D = 16
+NTT_MAX_RANK = 32
+NTT_MAX_ROWS = 512
+
+STATUS = {
+    0: "NTT_OK",
+    1: "NTT_ERR_INVALID_ARG",
+    2: "NTT_ERR_RANK_INFEASIBLE",
+    3: "NTT_ERR_OOM",
+    4: "NTT_ERR_CUDA",
+    5: "NTT_ERR_TIMEOUT",
+    6: "NTT_ERR_UNSUPPORTED",
+}
+NTT_F32, NTT_BF16 = 0, 1
+
+# Every symbol include/ntt.h declares.
+EXPORTS = (
+    "ntt_status_string", "ntt_version", "ntt_plan_create", "ntt_plan_workspace_size",
+    "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
+    "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
+    "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
+    "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio",
+)
+
+
+class NTTError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(self.code, self.code)}")
+
+
+class _PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("dims", ctypes.POINTER(ctypes.c_int64)),
+        ("ranks", ctypes.POINTER(ctypes.c_int64)),
+        ("iters", ctypes.c_int),
+        ("eps_mu", ctypes.c_float),
+        ("x_dtype", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int * NTT_MAX_D),
+        ("m", ctypes.c_int64 * NTT_MAX_D),
+        ("n", ctypes.c_int64 * NTT_MAX_D),
+        ("r", ctypes.c_int64 * NTT_MAX_D),
+        ("xnorm2", ctypes.c_double * NTT_MAX_D),
+        ("obj_first", ctypes.c_double * NTT_MAX_D),
+        ("obj_last", ctypes.c_double * NTT_MAX_D),
+        ("resid", ctypes.c_double * NTT_MAX_D),
+        ("stage_ms", ctypes.c_float * NTT_MAX_D),
+        ("iter_ms", ctypes.c_float * NTT_MAX_D),
+        ("total_ms", ctypes.c_float),
+        ("alg_bytes", ctypes.c_double * NTT_MAX_D),
+        ("launches", ctypes.c_int64),
+    ]
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load libntt.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    psz = ctypes.POINTER(ctypes.c_size_t)
+    L.ntt_status_string.restype = ctypes.c_char_p
+    L.ntt_status_string.argtypes = [i32]
+    L.ntt_version.restype = ctypes.c_char_p
+    L.ntt_version.argtypes = []
+    L.ntt_plan_create.argtypes = [ctypes.POINTER(_PlanDesc), ctypes.POINTER(vp)]
+    L.ntt_plan_workspace_size.argtypes = [vp, psz]
+    L.ntt_plan_workspace_size_host.argtypes = [vp, psz]
+    L.ntt_decompose.argtypes = [vp, vp, ctypes.POINTER(vp), vp, vp]
+    L.ntt_decompose_host.argtypes = [vp, vp, ctypes.POINTER(vp), vp, vp, vp]
+    L.ntt_plan_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    L.ntt_plan_destroy.argtypes = [vp]
+    L.nmf_mu_workspace_size.argtypes = [i64, i64, i32, i32, psz]
+    L.nmf_mu_step.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.ntt_status_of_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.ntt_uniform_init.argtypes = [ctypes.c_uint64, i32, i32, i32, i64, vp, vp]
+    L.ntt_reconstruct_workspace_size.argtypes = [i32, p64, p64, psz]
+    L.ntt_reconstruct.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp]
+    L.ntt_rel_error.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp, vp]
+    L.ntt_compression_ratio.restype = ctypes.c_double
+    L.ntt_compression_ratio.argtypes = [i32, p64, p64]
+    for name in EXPORTS:
+        if name not in ("ntt_status_string", "ntt_version", "ntt_compression_ratio"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib_handle = L
+    return L
+
+
+def _check(code, where):
+    if code != 0:
+        raise NTTError(code, where)
+
+
+def _i64arr(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int64 * len(vals))(*vals)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dev_ptr(t, dtype=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def empty_workspace(nbytes, device=None):
+    """Device workspace buffer (uint8, 256-byte aligned by the caching allocator)."""
+    import torch
+    t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                    device=device or torch.device("cuda", torch.cuda.current_device()))
+    if t.data_ptr() % 256:
+        raise RuntimeError("workspace is not 256-byte aligned")
+    return t
+
+
+@dataclass
+class Plan:
+    handle: ctypes.c_void_p
+    dims: tuple
+    ranks: tuple
+    iters: int
+    x_dtype: str
+    refine_iters: int
+
+    def workspace_size(self):
+        n = ctypes.c_size_t(0)
+        _check(lib().ntt_plan_workspace_size(self.handle, ctypes.byref(n)), "ntt_plan_workspace_size")
+        return n.value
+
+    def workspace_size_host(self):
+        n = ctypes.c_size_t(0)
+        _check(lib().ntt_plan_workspace_size_host(self.handle, ctypes.byref(n)),
+               "ntt_plan_workspace_size_host")
+        return n.value
+
+    def core_shapes(self):
+        return [(self.ranks[k], self.dims[k], self.ranks[k + 1]) for k in range(len(self.dims))]
+
+    def destroy(self):
+        if self.handle:
+            lib().ntt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0):
+    dims = tuple(int(n) for n in dims)
+    ranks = tuple(int(r) for r in ranks) if ranks is not None else None
+    d_arr = _i64arr(dims)
+    r_arr = _i64arr(ranks) if ranks is not None else None
+    desc = _PlanDesc()
+    desc.d = len(dims)
+    desc.dims = ctypes.cast(d_arr, ctypes.POINTER(ctypes.c_int64))
+    desc.ranks = ctypes.cast(r_arr, ctypes.POINTER(ctypes.c_int64)) if r_arr is not None else None
+    desc.iters = int(iters)
+    desc.eps_mu = float(eps_mu)
+    desc.x_dtype = NTT_BF16 if x_dtype == "bf16" else NTT_F32
+    desc.refine_iters = int(refine_iters)
+    desc.seed = int(seed)
+    h = ctypes.c_void_p()
+    _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
+    return Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[p.value if isinstance(p, ctypes.c_void_p) else p
+                                           for p in ptrs])
+
+
+def ntt_decompose(plan, A, cores, workspace, stream=None):
+    import torch
+    a = _dev_ptr(A, torch.float32, "A")
+    cps = _ptr_array([_dev_ptr(c, torch.float32, "core") for c in cores])
+    w = _dev_ptr(workspace, None, "workspace")
+    _check(lib().ntt_decompose(plan.handle, a, cps, w, _stream_ptr(stream)), "ntt_decompose")
+
+
+def ntt_decompose_host(plan, A_host, cores_host, workspace, err_host=None, stream=None):
+    """A_host, cores_host: CPU float32 tensors (pinned for asynchrony); err_host:
+    optional CPU float64 tensor of 3 entries receiving Eq. (3) of the result."""
+    import torch
+    for t in [A_host, *cores_host]:
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("host tensors must be contiguous CPU float32")
+    eptr = None
+    if err_host is not None:
+        if err_host.is_cuda or err_host.dtype != torch.float64 or err_host.numel() < 3:
+            raise TypeError("err_host must be a CPU float64 tensor of >= 3 entries")
+        eptr = ctypes.c_void_p(err_host.data_ptr())
+    cps = _ptr_array([c.data_ptr() for c in cores_host])
+    w = _dev_ptr(workspace, None, "workspace")
+    _check(lib().ntt_decompose_host(plan.handle, ctypes.c_void_p(A_host.data_ptr()), cps, eptr, w,
+                                    _stream_ptr(stream)), "ntt_decompose_host")
+
+
+def ntt_plan_get_stats(plan):
+    st = _Stats()
+    code = lib().ntt_plan_get_stats(plan.handle, ctypes.byref(st))
+    d = st.d
+    out = dict(status=STATUS.get(st.status, st.status), total_ms=st.total_ms,
+               launches=st.launches, stages=[])
+    for s in range(d - 1):
+        out["stages"].append(dict(
+            m=st.m[s], n=st.n[s], r=st.r[s], iters=st.iters[s], xnorm2=st.xnorm2[s],
+            obj_first=st.obj_first[s], obj_last=st.obj_last[s], resid=st.resid[s],
+            stage_ms=st.stage_ms[s], iter_ms=st.iter_ms[s], alg_bytes=st.alg_bytes[s]))
+    _check(code, "ntt_plan_get_stats")
+    return out
+
+
+def nmf_mu_workspace_size(m, n, r, x_dtype="f32"):
+    b = ctypes.c_size_t(0)
+    _check(lib().nmf_mu_workspace_size(int(m), int(n), int(r),
+                                       NTT_BF16 if x_dtype == "bf16" else NTT_F32, ctypes.byref(b)),
+           "nmf_mu_workspace_size")
+    return b.value
+
+
+def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=None):
+    """`iters` MU iterations on W (m x r) and H (r x n) in place; X is float32 or bfloat16."""
+    import torch
+    if X.dim() != 2 or W.dim() != 2 or H.dim() != 2:
+        raise ValueError("X, W, H must be matrices")
+    m, n = X.shape
+    r = W.shape[1]
+    if W.shape[0] != m or H.shape != (r, n):
+        raise ValueError("shape mismatch")
+    xd = "bf16" if X.dtype == torch.bfloat16 else "f32"
+    if workspace is None:
+        workspace = empty_workspace(nmf_mu_workspace_size(m, n, r, xd), X.device)
+    optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
+    _check(lib().nmf_mu_step(m, n, r, _dev_ptr(X, None, "X"),
+                             NTT_BF16 if xd == "bf16" else NTT_F32,
+                             _dev_ptr(W, torch.float32, "W"), _dev_ptr(H, torch.float32, "H"),
+                             int(iters), float(eps_mu), optr, _dev_ptr(workspace, None, "ws"),
+                             _stream_ptr(stream)), "nmf_mu_step")
+    return workspace
+
+
+def ntt_status_of_workspace(workspace):
+    v = ctypes.c_int(0)
+    _check(lib().ntt_status_of_workspace(_dev_ptr(workspace, None, "ws"), ctypes.byref(v)),
+           "ntt_status_of_workspace")
+    return STATUS.get(v.value, v.value)
+
+
+def ntt_uniform_init(seed, stage, restart, matrix, out, stream=None):
+    import torch
+    _check(lib().ntt_uniform_init(int(seed), int(stage), int(restart), int(matrix), out.numel(),
+                                  _dev_ptr(out, torch.float32, "out"), _stream_ptr(stream)),
+           "ntt_uniform_init")
+
+
+def ntt_reconstruct_workspace_size(dims, ranks):
+    b = ctypes.c_size_t(0)
+    _check(lib().ntt_reconstruct_workspace_size(len(dims), _i64arr(dims), _i64arr(ranks),
+                                                ctypes.byref(b)), "ntt_reconstruct_workspace_size")
+    return b.value
+
+
+def ntt_reconstruct(dims, ranks, cores, out, workspace=None, stream=None):
+    import torch
+    if workspace is None:
+        workspace = empty_workspace(ntt_reconstruct_workspace_size(dims, ranks), out.device)
+    cps = _ptr_array([_dev_ptr(c, torch.float32, "core") for c in cores])
+    _check(lib().ntt_reconstruct(len(dims), _i64arr(dims), _i64arr(ranks), cps,
+                                 _dev_ptr(out, torch.float32, "out"),
+                                 _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)),
+           "ntt_reconstruct")
+    return workspace
+
+
+def ntt_rel_error(dims, ranks, cores, A, err, workspace=None, stream=None):
+    """err: CUDA float64 tensor of >= 3 entries (rel error, ||A - A~||^2, ||A||^2)."""
+    import torch
+    if workspace is None:
+        workspace = empty_workspace(ntt_reconstruct_workspace_size(dims, ranks), A.device)
+    cps = _ptr_array([_dev_ptr(c, torch.float32, "core") for c in cores])
+    _check(lib().ntt_rel_error(len(dims), _i64arr(dims), _i64arr(ranks), cps,
+                               _dev_ptr(A, torch.float32, "A"), _dev_ptr(err, torch.float64, "err"),
+                               _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)),
+           "ntt_rel_error")
+    return workspace
+
+
+def ntt_compression_ratio(dims, ranks):
+    return lib().ntt_compression_ratio(len(dims), _i64arr(dims), _i64arr(ranks))
+
+
+def decompose(A, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, stream=None):
+    """Convenience wrapper: returns (cores, stats) for a CUDA float32 tensor A."""
+    import torch
+    plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed)
+    ws = empty_workspace(plan.workspace_size(), A.device)
+    cores = [torch.empty(s, dtype=torch.float32, device=A.device) for s in plan.core_shapes()]
+    ntt_decompose(plan, A.contiguous(), cores, ws, stream)
+    stats = ntt_plan_get_stats(plan)
+    plan.destroy()
+    return cores, stats
+
+
+def build(**kw):
+    from ._build import build as _b
+    return _b(**kw)

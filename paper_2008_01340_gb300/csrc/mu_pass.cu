@@ -1,0 +1,156 @@
+// Host side of the fused MU pass: bucket choice, TMA tensor maps, dispatch.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "ntt_internal.cuh"
+
+namespace ntt {
+
+#define NTT_DECL_BUCKET(B, MP)                                                                   \
+  cudaError_t launch_pass_##B##_m##MP(int R, const MuShape& s, const MuDev& d, float eps,       \
+                                      const CUtensorMap& mx, const CUtensorMap& mh,             \
+                                      cudaStream_t st);                                         \
+  bool info_pass_##B##_m##MP(int R, int* T, size_t* smem);
+NTT_DECL_BUCKET(f32, 16)
+NTT_DECL_BUCKET(f32, 32)
+NTT_DECL_BUCKET(f32, 64)
+NTT_DECL_BUCKET(f32, 128)
+NTT_DECL_BUCKET(f32, 256)
+NTT_DECL_BUCKET(f32, 512)
+NTT_DECL_BUCKET(bf16, 16)
+NTT_DECL_BUCKET(bf16, 32)
+NTT_DECL_BUCKET(bf16, 64)
+NTT_DECL_BUCKET(bf16, 128)
+NTT_DECL_BUCKET(bf16, 256)
+NTT_DECL_BUCKET(bf16, 512)
+#undef NTT_DECL_BUCKET
+
+static bool pass_info(int MP, int R, int bf16, int* T, size_t* smem) {
+#define NTT_CASE(MPV)                                                                  \
+  case MPV:                                                                            \
+    return bf16 ? info_pass_bf16_m##MPV(R, T, smem) : info_pass_f32_m##MPV(R, T, smem);
+  switch (MP) {
+    NTT_CASE(16)
+    NTT_CASE(32)
+    NTT_CASE(64)
+    NTT_CASE(128)
+    NTT_CASE(256)
+    NTT_CASE(512)
+    default:
+      return false;
+  }
+#undef NTT_CASE
+}
+
+int device_sms() {
+  static int sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      sms = 152;
+    cudaGetLastError();
+  });
+  return sms;
+}
+
+ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, MuShape* out) {
+  if (m < 1 || n < 1 || r < 1 || !out) return NTT_ERR_INVALID_ARG;
+  if (m > NTT_MAX_ROWS || r > NTT_MAX_RANK) return NTT_ERR_UNSUPPORTED;
+  if (n > (int64_t)INT32_MAX - 256) return NTT_ERR_UNSUPPORTED;
+  MuShape s;
+  s.m = m;
+  s.n = n;
+  s.r = r;
+  s.bf16 = bf16 ? 1 : 0;
+  int MP = 16;
+  while (MP < m) MP *= 2;
+  s.MP = MP;
+  s.R = r <= 8 ? 8 : (r <= 16 ? 16 : 32);
+  if (!pass_info(s.MP, s.R, s.bf16, &s.T, &s.smem)) return NTT_ERR_UNSUPPORTED;
+  const int64_t ntiles = (n + s.T - 1) / s.T;
+  int64_t grid = num_sms > 0 ? num_sms : 152;
+  if (grid > kMaxPassCtas) grid = kMaxPassCtas;
+  if (grid > ntiles) grid = ntiles;
+  s.grid = (int)grid;
+  s.tma = 0;
+  *out = s;
+  return NTT_OK;
+}
+
+bool mu_tma_ok(const MuShape& s, const void* X, const float* H) {
+  const int xb = s.bf16 ? 2 : 4;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(H) & 15)) return false;
+  if ((s.n * xb) % 16 != 0 || (s.n * 4) % 16 != 0) return false;
+  return true;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUtensorMap* mx,
+                          CUtensorMap* mh) {
+  auto fn = encode_fn();
+  if (!fn) return NTT_ERR_CUDA;
+  const int xb = s.bf16 ? 2 : 4;
+  const int br = s.MP < 256 ? s.MP : 256;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.m};
+    cuuint64_t strides[1] = {(cuuint64_t)(s.n * xb)};
+    cuuint32_t box[2] = {(cuuint32_t)s.T, (cuuint32_t)br};
+    cuuint32_t es[2] = {1, 1};
+    CUresult e = fn(mx, s.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    2, const_cast<void*>(X), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.r};
+    cuuint64_t strides[1] = {(cuuint64_t)(s.n * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)s.T, (cuuint32_t)s.R};
+    cuuint32_t es[2] = {1, 1};
+    CUresult e = fn(mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(H), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
+  }
+  return NTT_OK;
+}
+
+cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
+                           const CUtensorMap& mh, cudaStream_t st) {
+#define NTT_CASE(MPV)                                                       \
+  case MPV:                                                                 \
+    return s.bf16 ? launch_pass_bf16_m##MPV(s.R, s, d, eps, mx, mh, st)    \
+                  : launch_pass_f32_m##MPV(s.R, s, d, eps, mx, mh, st);
+  switch (s.MP) {
+    NTT_CASE(16)
+    NTT_CASE(32)
+    NTT_CASE(64)
+    NTT_CASE(128)
+    NTT_CASE(256)
+    NTT_CASE(512)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef NTT_CASE
+}
+
+}  // namespace ntt

@@ -1,0 +1,25 @@
+// Instantiations of the fused MU pass for X in bf16, padded rows MP = 128.
+#include "mu_pass_impl.cuh"
+
+namespace ntt {
+
+cudaError_t launch_pass_bf16_m128(int R, const MuShape& s, const MuDev& d, float eps,
+                                   const CUtensorMap& mx, const CUtensorMap& mh, cudaStream_t st) {
+  switch (R) {
+    case 8: return launch_pass_cfg<PassCfg<128, 8, true>>(s, d, eps, mx, mh, st);
+    case 16: return launch_pass_cfg<PassCfg<128, 16, true>>(s, d, eps, mx, mh, st);
+    case 32: return launch_pass_cfg<PassCfg<128, 32, true>>(s, d, eps, mx, mh, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool info_pass_bf16_m128(int R, int* T, size_t* smem) {
+  switch (R) {
+    case 8: pass_cfg_info<PassCfg<128, 8, true>>(T, smem); return true;
+    case 16: pass_cfg_info<PassCfg<128, 16, true>>(T, smem); return true;
+    case 32: pass_cfg_info<PassCfg<128, 32, true>>(T, smem); return true;
+    default: return false;
+  }
+}
+
+}  // namespace ntt

@@ -1,0 +1,25 @@
+// Instantiations of the fused MU pass for X in f32, padded rows MP = 512.
+#include "mu_pass_impl.cuh"
+
+namespace ntt {
+
+cudaError_t launch_pass_f32_m512(int R, const MuShape& s, const MuDev& d, float eps,
+                                   const CUtensorMap& mx, const CUtensorMap& mh, cudaStream_t st) {
+  switch (R) {
+    case 8: return launch_pass_cfg<PassCfg<512, 8, false>>(s, d, eps, mx, mh, st);
+    case 16: return launch_pass_cfg<PassCfg<512, 16, false>>(s, d, eps, mx, mh, st);
+    case 32: return launch_pass_cfg<PassCfg<512, 32, false>>(s, d, eps, mx, mh, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool info_pass_f32_m512(int R, int* T, size_t* smem) {
+  switch (R) {
+    case 8: pass_cfg_info<PassCfg<512, 8, false>>(T, smem); return true;
+    case 16: pass_cfg_info<PassCfg<512, 16, false>>(T, smem); return true;
+    case 32: pass_cfg_info<PassCfg<512, 32, false>>(T, smem); return true;
+    default: return false;
+  }
+}
+
+}  // namespace ntt

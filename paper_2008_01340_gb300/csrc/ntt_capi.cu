@@ -1,0 +1,695 @@
+// C ABI of libntt: plans, workspace layout, the stage loop of Algorithm 2,
+// CUDA-graph capture of the whole decomposition, statistics, and the
+// reconstruction / relative-error entry points (Eq. (2)-(4)).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ntt_internal.cuh"
+
+using namespace ntt;
+
+namespace {
+
+constexpr int kMaxResidBlocks = 4096;
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  }
+};
+
+int64_t prod(const int64_t* v, int a, int b) {  // prod v[a..b)
+  int64_t p = 1;
+  for (int i = a; i < b; ++i) p *= v[i];
+  return p;
+}
+
+#define NTT_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) {                       \
+      cudaGetLastError();                          \
+      return NTT_ERR_CUDA;                         \
+    }                                              \
+  } while (0)
+
+#define NTT_TRY(expr)                \
+  do {                               \
+    ntt_status s_ = (expr);          \
+    if (s_ != NTT_OK) return s_;     \
+  } while (0)
+
+// Scratch of one multiplicative-update NMF (shared by nmf_mu_step and stages).
+struct MuWs {
+  size_t status, tickets, scal, G, red, part, part64;
+};
+
+size_t mu_partial_floats(const MuShape& s) { return (size_t)s.grid * s.part_stride(); }
+
+// Launch the gram and `iters` (pass, combine) pairs of one NMF.
+ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
+                        cudaStream_t st) {
+  CUtensorMap mx, mh;
+  std::memset(&mx, 0, sizeof(mx));
+  std::memset(&mh, 0, sizeof(mh));
+  MuShape s = shp;
+  s.tma = mu_tma_ok(s, dev.X, dev.H) ? 1 : 0;
+  if (s.tma) NTT_TRY(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
+  for (int t = 0; t < iters; ++t) {
+    NTT_CUDA_TRY(launch_mu_pass(s, dev, eps, mx, mh, st));
+    MuDev d2 = dev;
+    NTT_CUDA_TRY(launch_mu_combine(s, d2, eps, t0 + t, st));
+  }
+  return NTT_OK;
+}
+
+ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
+                      int64_t N, int r, int mode, double scale, double* acc, double* rel,
+                      double* part64, unsigned* ticket, cudaStream_t st) {
+  ResidArgs a;
+  a.X = X;
+  a.xbf16 = xbf16;
+  a.L = L;
+  a.Rm = Rm;
+  a.M = M;
+  a.N = N;
+  a.r = r;
+  a.mode = mode;
+  a.part64 = part64;
+  a.ticket = ticket;
+  a.acc = acc;
+  a.rel = rel;
+  a.scale = scale;
+  int blocks = resid_blocks(device_sms());
+  if (blocks > kMaxResidBlocks) blocks = kMaxResidBlocks;
+  NTT_CUDA_TRY(launch_resid(a, blocks, st));
+  return NTT_OK;
+}
+
+int split_point(int d, const int64_t* dims) {
+  double total = 0.0;
+  for (int i = 0; i < d; ++i) total += std::log((double)dims[i]);
+  int best_s = 1;
+  double best = 1e300;
+  double left = 0.0;
+  for (int s = 1; s < d; ++s) {
+    left += std::log((double)dims[s - 1]);
+    const double score = std::fabs(left - 0.5 * total);
+    if (score < best) {
+      best = score;
+      best_s = s;
+    }
+  }
+  return best_s;
+}
+
+ntt_status check_tt(int d, const int64_t* dims, const int64_t* ranks) {
+  if (d < 2 || d > NTT_MAX_D || !dims || !ranks) return NTT_ERR_INVALID_ARG;
+  if (ranks[0] != 1 || ranks[d] != 1) return NTT_ERR_INVALID_ARG;
+  for (int i = 0; i < d; ++i)
+    if (dims[i] < 1) return NTT_ERR_INVALID_ARG;
+  for (int i = 1; i < d; ++i)
+    if (ranks[i] < 1 || ranks[i] > NTT_MAX_RANK) return NTT_ERR_UNSUPPORTED;
+  return NTT_OK;
+}
+
+// Layout of the reconstruction workspace: chain buffers for L and R.
+struct ChainWs {
+  int s = 1;
+  int64_t rows = 0, cols = 0;   // L is rows x r_s, R is r_s x cols
+  size_t L[2], R[2], part64, ticket, acc, total;
+};
+
+ChainWs chain_layout(int d, const int64_t* dims, const int64_t* ranks) {
+  ChainWs c;
+  c.s = split_point(d, dims);
+  Arena ar;
+  size_t lmax = 1, rmax = 1;
+  for (int k = 2; k <= c.s; ++k) {  // L_k = G_1..G_k : prod_{i<=k} n_i x r_k
+    const size_t sz = (size_t)prod(dims, 0, k) * ranks[k];
+    if (sz > lmax) lmax = sz;
+  }
+  for (int k = c.s + 1; k <= d - 1; ++k) {  // R_k = G_k..G_d: r_{k-1} x prod_{i>=k} n_i
+    const size_t sz = (size_t)ranks[k - 1] * prod(dims, k - 1, d);
+    if (sz > rmax) rmax = sz;
+  }
+  c.rows = prod(dims, 0, c.s);
+  c.cols = prod(dims, c.s, d);
+  c.L[0] = ar.take(lmax * 4);
+  c.L[1] = ar.take(lmax * 4);
+  c.R[0] = ar.take(rmax * 4);
+  c.R[1] = ar.take(rmax * 4);
+  c.part64 = ar.take(2 * kMaxResidBlocks * sizeof(double));
+  c.ticket = ar.take(64);
+  c.acc = ar.take(8 * sizeof(double));
+  c.total = ar.off;
+  return c;
+}
+
+// Form L = G_1..G_s and R = G_{s+1}..G_d in the chain workspace.
+ntt_status build_chain(int d, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                       const ChainWs& c, char* ws, const float** Lout, const float** Rout,
+                       cudaStream_t st) {
+  const float* L = cores[0];  // n_1 x r_1
+  int64_t rows = dims[0];
+  int li = 0;
+  for (int k = 2; k <= c.s; ++k) {
+    float* dst = reinterpret_cast<float*>(ws + c.L[li]);
+    // (rows x r_{k-1}) @ (r_{k-1} x n_k r_k)
+    NTT_CUDA_TRY(launch_small_mm(L, cores[k - 1], dst, rows, (int)ranks[k - 1], dims[k - 1] * ranks[k], st));
+    rows *= dims[k - 1];
+    L = dst;
+    li ^= 1;
+  }
+  const float* R = cores[d - 1];  // r_{d-1} x n_d
+  int64_t cols = dims[d - 1];
+  int ri = 0;
+  for (int k = d - 1; k >= c.s + 1; --k) {
+    float* dst = reinterpret_cast<float*>(ws + c.R[ri]);
+    // (r_{k-1} n_k x r_k) @ (r_k x cols)
+    NTT_CUDA_TRY(launch_small_mm(cores[k - 1], R, dst, ranks[k - 1] * dims[k - 1], (int)ranks[k], cols, st));
+    cols *= dims[k - 1];
+    R = dst;
+    ri ^= 1;
+  }
+  *Lout = L;
+  *Rout = R;
+  return NTT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Plan
+// ===========================================================================
+struct ntt_plan_s {
+  int d = 0;
+  std::vector<int64_t> dims, ranks;
+  int iters = 0;
+  float eps = 1e-12f;
+  ntt_dtype xdt = NTT_F32;
+  int refine = 0;
+  uint64_t seed = 0;
+
+  struct Stage {
+    int64_t m, n;
+    int r;
+    MuShape f32, bf16;
+    int iters_total;
+    size_t obj_off;  // index into the objective array
+    double alg_bytes;
+  };
+  std::vector<Stage> st;
+  // workspace layout
+  size_t off_status = 0, off_tickets = 0, off_scal = 0, off_obj = 0, off_G = 0, off_red = 0,
+         off_part = 0, off_part64 = 0, off_hs = 0, off_H[2] = {0, 0}, off_xb = 0, ws_bytes = 0;
+  size_t off_A = 0, off_cores = 0, ws_bytes_host = 0;
+  std::vector<size_t> core_off;
+  size_t obj_total = 0;
+  // graph cache
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  const void* gA = nullptr;
+  void* gws = nullptr;
+  std::vector<float*> gcores;
+  std::vector<cudaEvent_t> ev;   // 4 per stage + 2 total
+  int64_t launches = 0;          // kernels per decomposition
+  size_t off_chain = 0, off_err = 0;
+  cudaStream_t last_stream = nullptr;
+  void* last_ws = nullptr;
+  bool ran = false;
+
+  ~ntt_plan_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+  }
+};
+
+namespace {
+
+// Record the whole decomposition on stream `st` (captured or eager).
+ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, char* ws,
+                             cudaStream_t st) {
+  int* status = reinterpret_cast<int*>(ws + p->off_status);
+  unsigned* tickets = reinterpret_cast<unsigned*>(ws + p->off_tickets);
+  double* scal = reinterpret_cast<double*>(ws + p->off_scal);
+  double* obj = reinterpret_cast<double*>(ws + p->off_obj);
+  NTT_CUDA_TRY(cudaMemsetAsync(status, 0, 64, st));
+  NTT_CUDA_TRY(cudaMemsetAsync(tickets, 0, 64, st));
+  const int d = p->d;
+  int64_t launches = 0;
+  auto rec = [&](int i) -> cudaError_t {
+    return p->ev.empty() ? cudaSuccess : cudaEventRecord(p->ev[i], st);
+  };
+  NTT_CUDA_TRY(rec(4 * d));
+  for (int s = 0; s < d - 1; ++s) {
+    const auto& S = p->st[s];
+    NTT_CUDA_TRY(rec(4 * s));
+    const float* X = (s == 0) ? A : reinterpret_cast<const float*>(ws + p->off_H[(s - 1) % 2]);
+    float* W = cores[s];
+    float* H = (s == d - 2) ? cores[d - 1] : reinterpret_cast<float*>(ws + p->off_H[s % 2]);
+    NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 0), S.m * S.r, W, st));
+    NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 1), (int64_t)S.r * S.n, H, st));
+    double* xnorm2 = scal + s;
+    NTT_TRY(resid_into(X, 0, nullptr, nullptr, S.m, S.n, 0, 0, 1.0, xnorm2, nullptr,
+                       reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
+    MuDev dev;
+    dev.W = W;
+    dev.H = H;
+    dev.G = reinterpret_cast<float*>(ws + p->off_G);
+    dev.part = reinterpret_cast<float*>(ws + p->off_part);
+    dev.red = reinterpret_cast<float*>(ws + p->off_red);
+    dev.ticket = tickets;
+    dev.obj = obj + S.obj_off;
+    dev.xnorm2 = xnorm2;
+    dev.status = status;
+    NTT_CUDA_TRY(launch_gram(S.f32, dev, st));
+    launches += 4;
+    if (p->xdt == NTT_BF16) {
+      __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
+      NTT_CUDA_TRY(launch_cast_bf16(X, xb, S.m * S.n, st));
+      launches += 1;
+      NTT_CUDA_TRY(rec(4 * s + 2));
+      dev.X = xb;
+      NTT_TRY(run_mu_iters(S.bf16, dev, p->eps, p->iters, 0, st));
+      dev.X = X;
+      NTT_TRY(run_mu_iters(S.f32, dev, p->eps, p->refine, p->iters, st));
+    } else {
+      NTT_CUDA_TRY(rec(4 * s + 2));
+      dev.X = X;
+      NTT_TRY(run_mu_iters(S.f32, dev, p->eps, p->iters, 0, st));
+    }
+    NTT_CUDA_TRY(rec(4 * s + 3));
+    launches += 2LL * S.iters_total;
+    // stage-end objective, direct FP64 pass: 1/2 ||X - W H||^2
+    NTT_TRY(resid_into(X, 0, W, H, S.m, S.n, S.r, 1, 0.5, scal + NTT_MAX_D + s, nullptr,
+                       reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
+    NTT_CUDA_TRY(launch_handoff(W, H, S.m, S.n, S.r, reinterpret_cast<float*>(ws + p->off_hs), st));
+    launches += 3;
+    NTT_CUDA_TRY(rec(4 * s + 1));
+  }
+  NTT_CUDA_TRY(rec(4 * d + 1));
+  p->launches = launches;
+  return NTT_OK;
+}
+
+bool eager_mode() {
+  const char* e = std::getenv("NTT_EAGER");
+  return e && e[0] == '1';
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ntt_status_string(ntt_status s) {
+  switch (s) {
+    case NTT_OK: return "NTT_OK";
+    case NTT_ERR_INVALID_ARG: return "NTT_ERR_INVALID_ARG";
+    case NTT_ERR_RANK_INFEASIBLE: return "NTT_ERR_RANK_INFEASIBLE";
+    case NTT_ERR_OOM: return "NTT_ERR_OOM";
+    case NTT_ERR_CUDA: return "NTT_ERR_CUDA";
+    case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT";
+    case NTT_ERR_UNSUPPORTED: return "NTT_ERR_UNSUPPORTED";
+  }
+  return "NTT_ERR_UNKNOWN";
+}
+
+const char* ntt_version(void) { return "libntt 0.1 (sm_103a)"; }
+
+double ntt_compression_ratio(int d, const int64_t* dims, const int64_t* ranks) {
+  if (d < 1 || !dims || !ranks) return 0.0;
+  double num = 1.0, den = 0.0;
+  for (int i = 0; i < d; ++i) {
+    num *= (double)dims[i];
+    den += (double)dims[i] * (double)ranks[i] * (double)ranks[i + 1];
+  }
+  return den > 0.0 ? num / den : 0.0;
+}
+
+ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
+  if (!desc || !out) return NTT_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int d = desc->d;
+  if (d < 2 || d > NTT_MAX_D || !desc->dims) return NTT_ERR_INVALID_ARG;
+  if (!desc->ranks) return NTT_ERR_UNSUPPORTED;  // SVD rank selection is not built
+  if (desc->iters < 1 || !(desc->eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
+  if (desc->x_dtype != NTT_F32 && desc->x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
+  if (desc->refine_iters < 0) return NTT_ERR_INVALID_ARG;
+  const int64_t* dims = desc->dims;
+  const int64_t* ranks = desc->ranks;
+  if (ranks[0] != 1 || ranks[d] != 1) return NTT_ERR_INVALID_ARG;
+  for (int i = 0; i < d; ++i)
+    if (dims[i] < 1) return NTT_ERR_INVALID_ARG;
+  for (int k = 1; k < d; ++k) {
+    const int64_t m = ranks[k - 1] * dims[k - 1];
+    const int64_t n = prod(dims, k, d);
+    if (ranks[k] < 1) return NTT_ERR_INVALID_ARG;
+    if (ranks[k] > m || ranks[k] > n) return NTT_ERR_RANK_INFEASIBLE;
+    if (ranks[k] > NTT_MAX_RANK || m > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+  }
+  ntt_plan p = new (std::nothrow) ntt_plan_s();
+  if (!p) return NTT_ERR_OOM;
+  p->d = d;
+  p->dims.assign(dims, dims + d);
+  p->ranks.assign(ranks, ranks + d + 1);
+  p->iters = desc->iters;
+  p->eps = desc->eps_mu;
+  p->xdt = desc->x_dtype;
+  p->refine = desc->x_dtype == NTT_BF16 ? desc->refine_iters : 0;
+  p->seed = desc->seed;
+  const int sms = device_sms();
+  size_t max_part = 1, max_red = 1, maxH[2] = {1, 1}, max_xb = 1;
+  for (int s = 0; s < d - 1; ++s) {
+    ntt_plan_s::Stage S;
+    S.m = ranks[s] * dims[s];
+    S.n = prod(dims, s + 1, d);
+    S.r = (int)ranks[s + 1];
+    ntt_status e = mu_choose_shape(S.m, S.n, S.r, 0, sms, &S.f32);
+    if (e == NTT_OK && p->xdt == NTT_BF16) e = mu_choose_shape(S.m, S.n, S.r, 1, sms, &S.bf16);
+    if (e != NTT_OK) {
+      delete p;
+      return e;
+    }
+    S.iters_total = p->iters + p->refine;
+    S.obj_off = p->obj_total;
+    p->obj_total += S.iters_total;
+    const double xs = p->xdt == NTT_BF16 ? 2.0 : 4.0;
+    S.alg_bytes = (double)S.m * S.n * xs + 8.0 * S.r * S.n;
+    size_t pf = mu_partial_floats(S.f32);
+    if (p->xdt == NTT_BF16 && mu_partial_floats(S.bf16) > pf) pf = mu_partial_floats(S.bf16);
+    if (pf > max_part) max_part = pf;
+    if ((size_t)S.f32.part_stride() > max_red) max_red = S.f32.part_stride();
+    if (s < d - 2 && (size_t)(S.r * S.n) > maxH[s % 2]) maxH[s % 2] = (size_t)S.r * S.n;
+    if ((size_t)(S.m * S.n) > max_xb) max_xb = (size_t)(S.m * S.n);
+    p->st.push_back(S);
+  }
+  Arena ar;
+  p->off_status = ar.take(64);
+  p->off_tickets = ar.take(64);
+  p->off_scal = ar.take(4 * NTT_MAX_D * sizeof(double));
+  p->off_obj = ar.take(p->obj_total * sizeof(double));
+  p->off_G = ar.take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
+  p->off_red = ar.take(max_red * 4);
+  p->off_part = ar.take(max_part * 4);
+  p->off_part64 = ar.take(2 * kMaxResidBlocks * sizeof(double));
+  p->off_hs = ar.take(NTT_MAX_RANK * 4);
+  p->off_H[0] = ar.take(maxH[0] * 4);
+  p->off_H[1] = ar.take(maxH[1] * 4);
+  if (p->xdt == NTT_BF16) p->off_xb = ar.take(max_xb * 2);
+  p->ws_bytes = ar.off;
+  p->off_A = ar.take((size_t)prod(dims, 0, d) * 4);
+  for (int k = 0; k < d; ++k)
+    p->core_off.push_back(ar.take((size_t)ranks[k] * dims[k] * ranks[k + 1] * 4));
+  p->off_err = ar.take(8 * sizeof(double));
+  p->off_chain = ar.take(chain_layout(d, dims, ranks).total);
+  p->ws_bytes_host = ar.off;
+  *out = p;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_workspace_size(ntt_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return NTT_ERR_INVALID_ARG;
+  *bytes = plan->ws_bytes;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return NTT_ERR_INVALID_ARG;
+  *bytes = plan->ws_bytes_host;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_destroy(ntt_plan plan) {
+  if (!plan) return NTT_ERR_INVALID_ARG;
+  delete plan;
+  return NTT_OK;
+}
+
+ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* workspace,
+                         void* stream) {
+  if (!p || !A || !cores || !workspace) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return NTT_ERR_INVALID_ARG;
+  for (int k = 0; k < p->d; ++k)
+    if (!cores[k]) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  const int d = p->d;
+  if (p->ev.empty()) {
+    p->ev.assign(4 * d + 2, nullptr);
+    for (auto& e : p->ev) NTT_CUDA_TRY(cudaEventCreate(&e));
+  }
+  if (eager_mode()) {
+    NTT_TRY(enqueue_decompose(p, A, cores, ws, st));
+  } else {
+    bool hit = p->exec && p->gA == A && p->gws == workspace &&
+               p->gcores.size() == (size_t)d;
+    for (int k = 0; hit && k < d; ++k) hit = p->gcores[k] == cores[k];
+    if (!hit) {
+      if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+      }
+      if (!p->cap) NTT_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      NTT_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+      ntt_status e = enqueue_decompose(p, A, cores, ws, p->cap);
+      cudaError_t ce = cudaStreamEndCapture(p->cap, &g);
+      if (e != NTT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+      }
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return NTT_ERR_CUDA;
+      }
+      cudaError_t ie = cudaGraphInstantiate(&p->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        cudaGetLastError();
+        p->exec = nullptr;
+        return NTT_ERR_CUDA;
+      }
+      p->gA = A;
+      p->gws = workspace;
+      p->gcores.assign(cores, cores + d);
+    }
+    NTT_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+  }
+  p->last_stream = st;
+  p->last_ws = workspace;
+  p->ran = true;
+  return NTT_OK;
+}
+
+ntt_status ntt_decompose_host(ntt_plan p, const float* A_host, float* const* cores_host,
+                              double* err_host, void* workspace, void* stream) {
+  if (!p || !A_host || !cores_host || !workspace) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  const int d = p->d;
+  float* A_dev = reinterpret_cast<float*>(ws + p->off_A);
+  std::vector<float*> cdev(d);
+  for (int k = 0; k < d; ++k) cdev[k] = reinterpret_cast<float*>(ws + p->core_off[k]);
+  const size_t abytes = (size_t)prod(p->dims.data(), 0, d) * 4;
+  NTT_CUDA_TRY(cudaMemcpyAsync(A_dev, A_host, abytes, cudaMemcpyHostToDevice, st));
+  NTT_TRY(ntt_decompose(p, A_dev, cdev.data(), workspace, stream));
+  if (err_host) {
+    double* err_dev = reinterpret_cast<double*>(ws + p->off_err);
+    NTT_TRY(ntt_rel_error(d, p->dims.data(), p->ranks.data(), cdev.data(), A_dev, err_dev,
+                          ws + p->off_chain, stream));
+    NTT_CUDA_TRY(cudaMemcpyAsync(err_host, err_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  for (int k = 0; k < d; ++k) {
+    const size_t cb = (size_t)p->ranks[k] * p->dims[k] * p->ranks[k + 1] * 4;
+    NTT_CUDA_TRY(cudaMemcpyAsync(cores_host[k], cdev[k], cb, cudaMemcpyDeviceToHost, st));
+  }
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
+  if (!p || !out) return NTT_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->d = p->d;
+  for (int s = 0; s < p->d - 1; ++s) {
+    out->m[s] = p->st[s].m;
+    out->n[s] = p->st[s].n;
+    out->r[s] = p->st[s].r;
+    out->iters[s] = p->st[s].iters_total;
+    out->alg_bytes[s] = p->st[s].alg_bytes;
+  }
+  if (!p->ran) return NTT_OK;
+  NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  const char* ws = reinterpret_cast<const char*>(p->last_ws);
+  int status = 0;
+  NTT_CUDA_TRY(cudaMemcpy(&status, ws + p->off_status, sizeof(int), cudaMemcpyDeviceToHost));
+  out->status = status;
+  std::vector<double> scal(4 * NTT_MAX_D);
+  NTT_CUDA_TRY(cudaMemcpy(scal.data(), ws + p->off_scal, scal.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> obj(p->obj_total ? p->obj_total : 1);
+  if (p->obj_total)
+    NTT_CUDA_TRY(cudaMemcpy(obj.data(), ws + p->off_obj, p->obj_total * 8, cudaMemcpyDeviceToHost));
+  for (int s = 0; s < p->d - 1; ++s) {
+    out->xnorm2[s] = scal[s];
+    out->resid[s] = scal[NTT_MAX_D + s];
+    const auto& S = p->st[s];
+    out->obj_first[s] = obj[S.obj_off];
+    out->obj_last[s] = obj[S.obj_off + S.iters_total - 1];
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p->ev[4 * s], p->ev[4 * s + 1]) == cudaSuccess)
+      out->stage_ms[s] = ms;
+    if (cudaEventElapsedTime(&ms, p->ev[4 * s + 2], p->ev[4 * s + 3]) == cudaSuccess)
+      out->iter_ms[s] = ms;
+    cudaGetLastError();
+  }
+  float tot = 0.0f;
+  if (cudaEventElapsedTime(&tot, p->ev[4 * p->d], p->ev[4 * p->d + 1]) == cudaSuccess)
+    out->total_ms = tot;
+  out->launches = p->launches;
+  cudaGetLastError();
+  return status == 0 ? NTT_OK : (ntt_status)status;
+}
+
+// ---------------------------------------------------------------------------
+// Single NMF
+// ---------------------------------------------------------------------------
+static MuWs mu_ws_layout(const MuShape& s, size_t* total) {
+  Arena ar;
+  MuWs w;
+  w.status = ar.take(64);
+  w.tickets = ar.take(64);
+  w.scal = ar.take(8 * sizeof(double));
+  w.G = ar.take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
+  w.red = ar.take((size_t)s.part_stride() * 4);
+  w.part = ar.take(mu_partial_floats(s) * 4);
+  w.part64 = ar.take(2 * kMaxResidBlocks * sizeof(double));
+  *total = ar.off;
+  return w;
+}
+
+ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype, size_t* bytes) {
+  if (!bytes) return NTT_ERR_INVALID_ARG;
+  if (x_dtype != NTT_F32 && x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
+  mu_ws_layout(s, bytes);
+  return NTT_OK;
+}
+
+ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
+                       float* H, int iters, float eps_mu, double* obj_dev, void* ws,
+                       void* stream) {
+  if (!X || !W || !H || !ws || iters < 0 || !(eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
+  if (x_dtype != NTT_F32 && x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  if (r > m || r > n) return NTT_ERR_RANK_INFEASIBLE;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
+  size_t total = 0;
+  MuWs L = mu_ws_layout(s, &total);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  NTT_CUDA_TRY(cudaMemsetAsync(w + L.status, 0, 64, st));
+  NTT_CUDA_TRY(cudaMemsetAsync(w + L.tickets, 0, 64, st));
+  unsigned* tickets = reinterpret_cast<unsigned*>(w + L.tickets);
+  double* scal = reinterpret_cast<double*>(w + L.scal);
+  if (obj_dev)
+    NTT_TRY(resid_into(X, s.bf16, nullptr, nullptr, m, n, 0, 0, 1.0, scal, nullptr,
+                       reinterpret_cast<double*>(w + L.part64), tickets + 1, st));
+  MuDev dev;
+  dev.X = X;
+  dev.W = W;
+  dev.H = H;
+  dev.G = reinterpret_cast<float*>(w + L.G);
+  dev.part = reinterpret_cast<float*>(w + L.part);
+  dev.red = reinterpret_cast<float*>(w + L.red);
+  dev.ticket = tickets;
+  dev.obj = obj_dev;
+  dev.xnorm2 = scal;
+  dev.status = reinterpret_cast<int*>(w + L.status);
+  NTT_CUDA_TRY(launch_gram(s, dev, st));
+  return run_mu_iters(s, dev, eps_mu, iters, 0, st);
+}
+
+ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out) {
+  if (!ws || !out) return NTT_ERR_INVALID_ARG;
+  int v = 0;
+  NTT_CUDA_TRY(cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost));
+  *out = (ntt_status)v;
+  return NTT_OK;
+}
+
+ntt_status ntt_uniform_init(uint64_t seed, int stage, int restart, int matrix, int64_t count,
+                            float* out, void* stream) {
+  if (!out || count < 0 || stage < 0 || restart < 0 || (matrix != 0 && matrix != 1))
+    return NTT_ERR_INVALID_ARG;
+  NTT_CUDA_TRY(launch_uniform(stream_key(seed, stage, restart, matrix), count, out,
+                              reinterpret_cast<cudaStream_t>(stream)));
+  return NTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction and relative error
+// ---------------------------------------------------------------------------
+ntt_status ntt_reconstruct_workspace_size(int d, const int64_t* dims, const int64_t* ranks,
+                                          size_t* bytes) {
+  if (!bytes) return NTT_ERR_INVALID_ARG;
+  NTT_TRY(check_tt(d, dims, ranks));
+  *bytes = chain_layout(d, dims, ranks).total;
+  return NTT_OK;
+}
+
+ntt_status ntt_reconstruct(int d, const int64_t* dims, const int64_t* ranks,
+                           const float* const* cores, float* A_out, void* ws, void* stream) {
+  NTT_TRY(check_tt(d, dims, ranks));
+  if (!cores || !A_out || !ws) return NTT_ERR_INVALID_ARG;
+  for (int k = 0; k < d; ++k)
+    if (!cores[k]) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const ChainWs c = chain_layout(d, dims, ranks);
+  char* w = reinterpret_cast<char*>(ws);
+  const float *L, *R;
+  NTT_TRY(build_chain(d, dims, ranks, cores, c, w, &L, &R, st));
+  ResidArgs a;
+  a.L = L;
+  a.Rm = R;
+  a.out = A_out;
+  a.M = c.rows;
+  a.N = c.cols;
+  a.r = (int)ranks[c.s];
+  a.mode = 2;
+  NTT_CUDA_TRY(launch_resid(a, resid_blocks(device_sms()), st));
+  return NTT_OK;
+}
+
+ntt_status ntt_rel_error(int d, const int64_t* dims, const int64_t* ranks,
+                         const float* const* cores, const float* A, double* err_dev, void* ws,
+                         void* stream) {
+  NTT_TRY(check_tt(d, dims, ranks));
+  if (!cores || !A || !err_dev || !ws) return NTT_ERR_INVALID_ARG;
+  for (int k = 0; k < d; ++k)
+    if (!cores[k]) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const ChainWs c = chain_layout(d, dims, ranks);
+  char* w = reinterpret_cast<char*>(ws);
+  const float *L, *R;
+  NTT_TRY(build_chain(d, dims, ranks, cores, c, w, &L, &R, st));
+  unsigned* ticket = reinterpret_cast<unsigned*>(w + c.ticket);
+  NTT_CUDA_TRY(cudaMemsetAsync(ticket, 0, 64, st));
+  return resid_into(A, 0, L, R, c.rows, c.cols, (int)ranks[c.s], 1, 1.0,
+                    reinterpret_cast<double*>(w + c.acc), err_dev,
+                    reinterpret_cast<double*>(w + c.part64), ticket, st);
+}
+
+}  // extern "C"

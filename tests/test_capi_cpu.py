@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/ntt.h declares, and validates plans on the host."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2008_01340_gb300 as ntt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", hdr)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                             txt, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(ntt.LIB_PATH):
+        ntt.build()
+    return ntt.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "ntt_decompose" in names and "nmf_mu_step" in names and "ntt_rel_error" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(ntt.EXPORTS) <= set(names)
+
+
+def test_status_strings(lib):
+    for code, name in ntt.STATUS.items():
+        assert lib.ntt_status_string(code).decode() == name
+
+
+def test_compression_ratio_matches_eq4(lib):
+    for dims, ranks in [((5, 4, 5, 6), (1, 4, 3, 2, 1)), ((32,) * 6, (1, 8, 16, 16, 16, 8, 1)),
+                        ((8, 8, 8, 8), (1, 3, 3, 3, 1))]:
+        assert abs(ntt.ntt_compression_ratio(dims, ranks) - oracle.compression_ratio(dims, ranks)) < 1e-12
+
+
+def test_plan_validation(lib):
+    # r_1 > min(m, n) (Algorithm 2: N = min(m, n))
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((4, 4), (1, 5, 1), 10)
+    assert e.value.code == 2
+    # r_0 != 1
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((4, 4), (2, 2, 1), 10)
+    assert e.value.code == 1
+    # rank above the built maximum
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((64, 64, 64), (1, 33, 33, 1), 10)
+    assert e.value.code == 6
+    # unfolding taller than the built maximum (r_1 n_2 = 32 * 32 = 1024 > 512)
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((32, 32, 32), (1, 32, 16, 1), 10)
+    assert e.value.code == 6
+    # iters < 1
+    with pytest.raises(ntt.NTTError):
+        ntt.ntt_plan_create((8, 8), (1, 2, 1), 0)
+    # no ranks: SVD rank selection is not built
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((8, 8), None, 10)
+    assert e.value.code == 6
+
+
+def test_workspace_sizes(lib):
+    p = ntt.ntt_plan_create((32,) * 6, (1, 8, 16, 16, 16, 8, 1), 200)
+    ws = p.workspace_size()
+    # H_1 (8 x 32^5 FP32, 1.07 GB) and H_2 (16 x 32^4) live in the workspace
+    assert ws >= 4 * (8 * 32 ** 5 + 16 * 32 ** 4)
+    assert ws < 1.3e9
+    assert p.workspace_size_host() >= ws + 4 * 32 ** 6
+    pb = ntt.ntt_plan_create((16,) * 8, (1, 16, 32, 32, 32, 32, 32, 16, 1), 200, x_dtype="bf16",
+                             refine_iters=5)
+    assert pb.workspace_size() >= 2 * 16 ** 8        # BF16 copy of X_1
+    assert ntt.nmf_mu_workspace_size(32, 1000, 8) > 0
+    with pytest.raises(ntt.NTTError):
+        ntt.nmf_mu_workspace_size(600, 1000, 8)
+    assert ntt.ntt_reconstruct_workspace_size((32,) * 6, (1, 8, 16, 16, 16, 8, 1)) > 0
+
+
+def test_null_arguments_rejected_without_launch(lib):
+    p = ntt.ntt_plan_create((8, 8), (1, 2, 1), 5)
+    vp = ctypes.c_void_p
+    assert lib.ntt_decompose(p.handle, None, None, None, None) == 1
+    assert lib.nmf_mu_step(8, 8, 2, None, 0, None, None, 1, ctypes.c_float(1e-12), None, None, None) == 1
+    assert lib.ntt_plan_workspace_size(None, None) == 1
+    assert lib.ntt_uniform_init(1, 0, 0, 2, 10, vp(16), None) == 1   # bad matrix id

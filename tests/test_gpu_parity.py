@@ -1,0 +1,356 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (all stated per test):
+  * RNG initialisation: bit-exact.
+  * multiplicative-update iterates from identical W0, H0: relative Frobenius
+    difference <= 1e-4 after 10 updates, for W and for H (FP32 path against
+    the FP64 oracle on the same FP32 input).
+  * final relative reconstruction error of a whole nTT within 1e-3 absolute
+    of the oracle's.
+  * BF16-stored X: iterates within 1e-4 of the oracle run on the BF16-rounded
+    X; error against the FP32-X oracle stated and bounded by 5e-3.
+  * reconstruction (Eq. 2): relative difference <= 1e-5 per entry.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_ITERATE = 1e-4
+ABS_FINAL_EPS = 1e-3
+REL_BF16_VS_FP64 = 5e-3
+
+
+@pytest.fixture(scope="module")
+def ntt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2008_01340_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+def _fro_rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _x_matrix(kind, m, n, seed):
+    if kind == "uniform":
+        return synth.uniform_matrix((m, n), seed)
+    # low-rank non-negative plus noise: product of random factors
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = max(1, min(m, 6))
+    X = rng.random((m, k)) @ rng.random((k, n))
+    X += 0.01 * X.mean() * np.abs(rng.standard_normal(X.shape))
+    return X.astype(np.float32)
+
+
+# ------------------------------------------------------------------ RNG
+
+@pytest.mark.parametrize("count", [1, 255, 4096, 100003])
+def test_uniform_init_bit_exact(ntt, count):
+    for (seed, stage, restart, mtx) in [(0, 0, 0, 0), (102, 3, 0, 1), (2**63 + 5, 7, 5, 1)]:
+        out = torch.empty(count, dtype=torch.float32, device="cuda")
+        ntt.ntt_uniform_init(seed, stage, restart, mtx, out)
+        key = oracle.stream_key(seed, stage, restart, mtx)
+        ref = oracle.uniform01(key, np.arange(count, dtype=np.uint64)).astype(np.float32)
+        assert np.array_equal(out.cpu().numpy(), ref)
+
+
+# ------------------------------------------------------------------ one NMF
+
+SHAPES = [
+    # (m, n, r, kind)   n % 4 == 0 -> TMA tiles, otherwise cooperative loads
+    (32, 40000, 8, "lowrank"),       # MP=32, R=8, ragged last tile
+    (32, 116813, 8, "uniform"),      # several tiles per CTA, odd n
+    (8, 512, 3, "lowrank"),          # C1 stage 1
+    (24, 777, 3, "uniform"),         # odd n, r < 8
+    (16, 4096, 16, "uniform"),       # full-rank stage (r = m)
+    (100, 5000, 5, "lowrank"),       # MP=128
+    (64, 10000, 20, "uniform"),      # MP=64, R=32
+    (256, 3000, 16, "lowrank"),      # MP=256, ragged tile
+    (300, 2050, 12, "uniform"),      # MP=512, R=16, n % 4 == 2
+    (512, 1000, 32, "uniform"),      # MP=512, R=32
+    (1, 999, 1, "uniform"),          # degenerate m = r = 1
+]
+
+
+def _run_gpu_mu(ntt, X, W0, H0, iters, obj=True):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Wd = torch.from_numpy(W0.astype(np.float32)).cuda()
+    Hd = torch.from_numpy(H0.astype(np.float32)).cuda()
+    od = torch.zeros(max(iters, 1), dtype=torch.float64, device="cuda") if obj else None
+    ws = ntt.nmf_mu_step(Xd, Wd, Hd, iters, 1e-12, od)
+    torch.cuda.synchronize()
+    assert ntt.ntt_status_of_workspace(ws) == "NTT_OK"
+    return Wd.cpu().numpy(), Hd.cpu().numpy(), (od.cpu().numpy() if obj else None)
+
+
+@pytest.mark.parametrize("m,n,r,kind", SHAPES)
+def test_mu_iterates_match_oracle(ntt, m, n, r, kind):
+    X = _x_matrix(kind, m, n, seed=m * 7919 + n)
+    W0 = synth.uniform_matrix((m, r), seed=11 + m)
+    H0 = synth.uniform_matrix((r, n), seed=13 + n)
+    iters = 10
+    Wg, Hg, og = _run_gpu_mu(ntt, X, W0, H0, iters)
+    Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, iters)
+    assert _fro_rel(Wg, Wo) <= REL_ITERATE
+    assert _fro_rel(Hg, Ho) <= REL_ITERATE
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    # expanded Gram-form objective (FP64 combine) against the direct FP64 objective
+    assert np.allclose(og, tr, rtol=2e-3, atol=1e-6 * float(np.sum(X.astype(np.float64) ** 2)))
+
+
+def test_mu_single_iteration_every_entry(ntt):
+    # one iteration: element-by-element comparison, every entry of W and H
+    m, n, r = 32, 10000, 8
+    X = _x_matrix("lowrank", m, n, 5)
+    W0 = synth.uniform_matrix((m, r), 6)
+    H0 = synth.uniform_matrix((r, n), 7)
+    Wg, Hg, _ = _run_gpu_mu(ntt, X, W0, H0, 1)
+    Wo, Ho, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 1)
+    assert np.allclose(Hg, Ho, rtol=1e-5, atol=1e-6 * Ho.max())
+    assert np.allclose(Wg, Wo, rtol=1e-5, atol=1e-6 * Wo.max())
+
+
+def test_mu_zero_iterations_and_zero_columns(ntt):
+    m, n, r = 16, 1000, 4
+    X = _x_matrix("uniform", m, n, 1)
+    X[:, 100:200] = 0.0                       # columns of zeros -> H columns go to 0
+    X[3, :] = 0.0                             # a row of zeros -> that W row goes to 0
+    W0 = synth.uniform_matrix((m, r), 2)
+    H0 = synth.uniform_matrix((r, n), 3)
+    Wg, Hg, _ = _run_gpu_mu(ntt, X, W0, H0, 0, obj=False)
+    assert np.array_equal(Wg, W0) and np.array_equal(Hg, H0)
+    Wg, Hg, _ = _run_gpu_mu(ntt, X, W0, H0, 5)
+    Wo, Ho, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 5)
+    assert np.all(Hg[:, 100:200] == 0.0) and np.all(Wg[3] == 0.0)
+    assert _fro_rel(Wg, Wo) <= REL_ITERATE and _fro_rel(Hg, Ho) <= REL_ITERATE
+
+
+def test_mu_deterministic(ntt):
+    m, n, r = 32, 60000, 8
+    X = _x_matrix("lowrank", m, n, 9)
+    W0 = synth.uniform_matrix((m, r), 10)
+    H0 = synth.uniform_matrix((r, n), 11)
+    a = _run_gpu_mu(ntt, X, W0, H0, 7)
+    b = _run_gpu_mu(ntt, X, W0, H0, 7)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (256, 4096, 16), (16, 8192, 16)])
+def test_mu_bf16_x(ntt, m, n, r):
+    X = _x_matrix("lowrank", m, n, 21)
+    Xb = torch.from_numpy(X).to(torch.bfloat16)            # RN-even rounding of the input
+    Xb64 = Xb.to(torch.float64).numpy()
+    W0 = synth.uniform_matrix((m, r), 22)
+    H0 = synth.uniform_matrix((r, n), 23)
+    Wd = torch.from_numpy(W0).cuda()
+    Hd = torch.from_numpy(H0).cuda()
+    ws = ntt.nmf_mu_step(Xb.cuda(), Wd, Hd, 10)
+    torch.cuda.synchronize()
+    Wo, Ho, _ = oracle.nmf_mu(Xb64, W0, H0, 10)
+    assert _fro_rel(Wd.cpu().numpy(), Wo) <= REL_ITERATE
+    assert _fro_rel(Hd.cpu().numpy(), Ho) <= REL_ITERATE
+    # stated error of the BF16-stored path against FP64 on the original FP32 X
+    Wf, Hf, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
+    e_w = _fro_rel(Wd.cpu().numpy(), Wf)
+    e_h = _fro_rel(Hd.cpu().numpy(), Hf)
+    print(f"bf16 X ({m}x{n}, r={r}): iterate error vs FP64 oracle W {e_w:.2e} H {e_h:.2e}")
+    assert e_w <= REL_BF16_VS_FP64 and e_h <= REL_BF16_VS_FP64
+
+
+# ------------------------------------------------------------------ whole nTT
+
+def _decompose(ntt, A, ranks, iters, seed, x_dtype="f32", refine=0):
+    dims = A.shape
+    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, seed)
+    ws = ntt.empty_workspace(plan.workspace_size())
+    cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    ntt.ntt_decompose(plan, Ad, cores, ws)
+    stats = ntt.ntt_plan_get_stats(plan)
+    return [c.cpu().numpy() for c in cores], stats, plan, Ad, ws
+
+
+def test_ntt_c1_per_iterate(ntt):
+    c = synth.CONFIGS["c1_8x4"]
+    A, _ = synth.tt_tensor(c["dims"], c["ranks"], c["core_dist"], c["noise"], c["data_seed"])
+    cores_g, stats, *_ = _decompose(ntt, A, c["ranks"], 10, c["init_seed"])
+    cores_o, traces = oracle.ntt_decompose(A, c["ranks"], 10, seed=c["init_seed"])
+    assert stats["status"] == "NTT_OK"
+    for k, (g, o) in enumerate(zip(cores_g, cores_o)):
+        assert _fro_rel(g, o) <= REL_ITERATE * (k + 1), f"core {k}"
+    for s, st in enumerate(stats["stages"]):
+        assert abs(st["resid"] - traces[s][-1]) <= 1e-3 * traces[s][-1]
+
+
+def test_ntt_c1_full_config(ntt):
+    c = synth.CONFIGS["c1_8x4"]
+    A, _ = synth.tt_tensor(c["dims"], c["ranks"], c["core_dist"], c["noise"], c["data_seed"])
+    cores_g, stats, plan, Ad, _ = _decompose(ntt, A, c["ranks"], c["iters"], c["init_seed"])
+    cores_o, _ = oracle.ntt_decompose(A, c["ranks"], c["iters"], seed=c["init_seed"], record=False)
+    eg = oracle.rel_error(A, cores_g)
+    eo = oracle.rel_error(A, cores_o)
+    assert abs(eg - eo) <= ABS_FINAL_EPS
+    assert all(np.all(g >= 0) and np.all(np.isfinite(g)) for g in cores_g)
+    # the device relative error (Eq. 3) agrees with the oracle's on the GPU cores
+    err = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ntt.ntt_rel_error(c["dims"], c["ranks"], [torch.from_numpy(g).cuda() for g in cores_g], Ad, err)
+    assert abs(err[0].item() - eg) <= 1e-6
+
+
+def test_ntt_c2_recipe_16x6(ntt):
+    # the 32^6 recipe scaled to 16^6 so the oracle finishes end to end
+    c = synth.CONFIGS["c2_small_16x6"]
+    A, _ = synth.tt_tensor(c["dims"], c["ranks"], c["core_dist"], c["noise"], c["data_seed"])
+    cores_g, stats, *_ = _decompose(ntt, A, c["ranks"], c["iters"], c["init_seed"])
+    cores_o, _ = oracle.ntt_decompose(A, c["ranks"], c["iters"], seed=c["init_seed"], record=False)
+    eg, eo = oracle.rel_error(A, cores_g), oracle.rel_error(A, cores_o)
+    print(f"16^6 rel error gpu {eg:.6f} oracle {eo:.6f}")
+    assert abs(eg - eo) <= ABS_FINAL_EPS
+
+
+def test_ntt_bf16_form_small(ntt):
+    dims, ranks = (16, 16, 16, 16), (1, 8, 16, 8, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "exponential", 0.01, seed=3)
+    cores_g, stats, *_ = _decompose(ntt, A, ranks, 100, 103, x_dtype="bf16", refine=5)
+    cores_o, _ = oracle.ntt_decompose(A, ranks, 105, seed=103, record=False)
+    eg, eo = oracle.rel_error(A, cores_g), oracle.rel_error(A, cores_o)
+    print(f"bf16 form rel error gpu {eg:.6f} fp64 oracle (105 FP32 iterations) {eo:.6f}")
+    assert abs(eg - eo) <= REL_BF16_VS_FP64
+    assert stats["status"] == "NTT_OK"
+
+
+def test_ntt_host_variant_equals_device(ntt):
+    dims, ranks = (8, 9, 10, 7), (1, 4, 5, 3, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=8)
+    cores_d, *_ = _decompose(ntt, A, ranks, 30, 5)
+    plan = ntt.ntt_plan_create(dims, ranks, 30, 1e-12, "f32", 0, 5)
+    ws = ntt.empty_workspace(plan.workspace_size_host())
+    Ah = torch.from_numpy(A).pin_memory()
+    ch = [torch.empty(s, dtype=torch.float32).pin_memory() for s in plan.core_shapes()]
+    ntt.ntt_decompose_host(plan, Ah, ch, ws)
+    torch.cuda.synchronize()
+    for a, b in zip(cores_d, ch):
+        assert np.array_equal(a, b.numpy())
+
+
+def test_ntt_repeat_is_bitwise_identical(ntt):
+    dims, ranks = (12, 10, 14, 9), (1, 5, 6, 4, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=31)
+    plan = ntt.ntt_plan_create(dims, ranks, 40, 1e-12, "f32", 0, 7)
+    ws = ntt.empty_workspace(plan.workspace_size())
+    Ad = torch.from_numpy(A).cuda()
+    outs = []
+    for _ in range(2):
+        cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
+        ntt.ntt_decompose(plan, Ad, cores, ws)
+        torch.cuda.synchronize()
+        outs.append([c.cpu().numpy() for c in cores])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ Eq. (2), Eq. (3)
+
+@pytest.mark.parametrize("dims,ranks", [((5, 7, 3, 6), (1, 2, 3, 2, 1)),
+                                        ((8, 8, 8, 8), (1, 3, 3, 3, 1)),
+                                        ((3, 250, 3), (1, 3, 2, 1)),
+                                        ((17, 19), (1, 5, 1))])
+def test_reconstruct_and_rel_error(ntt, dims, ranks):
+    cores = [c.astype(np.float32) for c in synth.tt_cores(dims, ranks, "uniform", seed=41)]
+    ref = oracle.tt_full([c.astype(np.float64) for c in cores])
+    cd = [torch.from_numpy(c).cuda() for c in cores]
+    out = torch.empty(math.prod(dims), dtype=torch.float32, device="cuda")
+    ntt.ntt_reconstruct(dims, ranks, cd, out)
+    got = out.cpu().numpy().reshape(dims)
+    assert np.allclose(got, ref, rtol=1e-5, atol=0)
+    A = (ref * (1.0 + 0.05 * synth.uniform_matrix(ref.shape, 3))).astype(np.float32)
+    err = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ntt.ntt_rel_error(dims, ranks, cd, torch.from_numpy(A.ravel()).cuda(), err)
+    eo = oracle.rel_error(A, cores)
+    assert abs(err[0].item() - eo) <= 1e-5 * eo
+
+
+# ------------------------------------------------------------------ full size, bench launch config
+
+@pytest.fixture(scope="module")
+def c2_full():
+    c = synth.CONFIGS["c2_32x6"]
+    A, info = synth.tt_tensor(c["dims"], c["ranks"], c["core_dist"], c["noise"], c["data_seed"])
+    return c, A
+
+
+def test_c2_full_size_first_iteration_sampled(ntt, c2_full):
+    """Stage 1 of the 32^6 workload (32 x 33,554,432, r = 8), one MU iteration
+    from the counter-RNG init in the launch configuration of the benchmark:
+    H checked on sampled columns (each column of the H update is independent
+    given W0), W against the oracle's full FP64 P = X H^T and Q = H H^T."""
+    c, A = c2_full
+    m, n, r = 32, 32 ** 5, 8
+    seed = c["init_seed"]
+    X = A.reshape(m, n)
+    Xd = torch.from_numpy(X).cuda()
+    Wd = torch.empty((m, r), dtype=torch.float32, device="cuda")
+    Hd = torch.empty((r, n), dtype=torch.float32, device="cuda")
+    ntt.ntt_uniform_init(seed, 0, 0, 0, Wd)
+    ntt.ntt_uniform_init(seed, 0, 0, 1, Hd)
+    ntt.nmf_mu_step(Xd, Wd, Hd, 1)
+    torch.cuda.synchronize()
+    W0 = oracle.uniform01(oracle.stream_key(seed, 0, 0, 0), np.arange(m * r, dtype=np.uint64)).reshape(m, r)
+    G = W0.T @ W0
+    # oracle H1 and P, Q in column chunks (FP64)
+    P = np.zeros((m, r))
+    Q = np.zeros((r, r))
+    rng = np.random.Generator(np.random.PCG64(0))
+    sample = np.sort(rng.choice(n, size=4096, replace=False))
+    Hg = Hd.cpu().numpy()
+    chunk = 1 << 21
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        Xc = X[:, c0:c1].astype(np.float64)
+        H0c = oracle.init_columns_H(n, r, seed, 0, np.arange(c0, c1))
+        H1c = np.maximum(0.0, H0c * (W0.T @ Xc) / (G @ H0c + 1e-12))
+        P += Xc @ H1c.T
+        Q += H1c @ H1c.T
+        sel = sample[(sample >= c0) & (sample < c1)]
+        if sel.size:
+            assert np.allclose(Hg[:, sel], H1c[:, sel - c0], rtol=1e-5, atol=1e-7 * H1c.max())
+    W1 = np.maximum(0.0, W0 * P / (W0 @ Q + 1e-12))
+    assert _fro_rel(Wd.cpu().numpy(), W1) <= REL_ITERATE
+
+
+def test_c2_full_size_decompose_properties(ntt, c2_full):
+    """The whole 32^6 decomposition as the benchmark runs it: non-negative
+    cores, non-increasing objective traces, Gram-form objective consistent
+    with the direct FP64 residual, and a relative error near the noise level."""
+    c, A = c2_full
+    plan = ntt.ntt_plan_create(c["dims"], c["ranks"], c["iters"], 1e-12, "f32", 0, c["init_seed"])
+    ws = ntt.empty_workspace(plan.workspace_size())
+    cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
+    Ad = torch.from_numpy(A.ravel()).cuda()
+    ntt.ntt_decompose(plan, Ad, cores, ws)
+    stats = ntt.ntt_plan_get_stats(plan)
+    assert stats["status"] == "NTT_OK"
+    for cc in cores:
+        assert bool(torch.all(cc >= 0)) and bool(torch.all(torch.isfinite(cc)))
+    for s, st in enumerate(stats["stages"]):
+        # expanded Gram form at the last iteration vs direct residual (1% noise: f ~ 1e-4 ||X||^2)
+        assert abs(st["obj_last"] - st["resid"]) <= 2e-2 * st["resid"] + 1e-7 * st["xnorm2"]
+    err = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ntt.ntt_rel_error(c["dims"], c["ranks"], cores, Ad, err)
+    e = err[0].item()
+    print(f"32^6 relative error {e:.5f}, total {stats['total_ms']:.1f} ms")
+    assert 0.0 < e < 0.05
