@@ -249,8 +249,11 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
   NTT_CUDA_TRY(cudaMemsetAsync(tickets, 0, 64, st));
   const int d = p->d;
   int64_t launches = 0;
+  // External event nodes: a plain record on a capturing stream would only
+  // mark a capture dependency and put no timing node into the graph.
   auto rec = [&](int i) -> cudaError_t {
-    return p->ev.empty() ? cudaSuccess : cudaEventRecord(p->ev[i], st);
+    return p->ev.empty() ? cudaSuccess
+                         : cudaEventRecordWithFlags(p->ev[i], st, cudaEventRecordExternal);
   };
   NTT_CUDA_TRY(rec(4 * d));
   for (int s = 0; s < d - 1; ++s) {
