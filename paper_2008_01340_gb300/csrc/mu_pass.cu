@@ -1,6 +1,8 @@
 // Host side of the fused MU pass: bucket choice, TMA tensor maps, dispatch.
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "ntt_internal.cuh"
@@ -77,9 +79,38 @@ ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, M
   if (grid > kMaxPassCtas) grid = kMaxPassCtas;
   if (grid > ntiles) grid = ntiles;
   s.grid = (int)grid;
+  int64_t cap = num_sms > 0 ? num_sms : 152;
+  if (cap > kMaxPassCtas) cap = kMaxPassCtas;
+  if (cap > (n + 15) / 16) cap = (n + 15) / 16;   // every pass tile is >= 16 columns
+  s.grid_cap = (int)(cap > grid ? cap : grid);
   s.tma = 0;
+  s.tc = 0;
   *out = s;
   return NTT_OK;
+}
+
+// The tensor-core pass (FP32 X, m <= 32, r <= 16, TMA-aligned tiles) is
+// selected with NTT_PASS=tc in the environment; the packed-FMA pass is the
+// default.  Measured on GB300: a kind::tf32 M=128 K=8 MMA costs ~56 cycles for
+// any N <= 64, so the 3xTF32 form needs >= 10.5 tensor-pipe cycles per column
+// of a 32-row unfolding against a 9-cycle HBM budget, and the FMA pass is faster.
+static bool tc_enabled() {
+  const char* e = std::getenv("NTT_PASS");
+  return e && std::strcmp(e, "tc") == 0;
+}
+
+void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
+  s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
+  s->tc = 0;
+  if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled()) {
+    s->tc = 1;
+    s->T = 128;
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+  }
 }
 
 bool mu_tma_ok(const MuShape& s, const void* X, const float* H) {
@@ -113,12 +144,13 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.m};
     cuuint64_t strides[1] = {(cuuint64_t)(s.n * xb)};
-    cuuint32_t box[2] = {(cuuint32_t)s.T, (cuuint32_t)br};
+    // tensor-core pass: 32-column boxes (128 bytes), 128-byte swizzle of 32-byte chunks
+    cuuint32_t box[2] = {(cuuint32_t)(s.tc ? 32 : s.T), (cuuint32_t)br};
     cuuint32_t es[2] = {1, 1};
     CUresult e = fn(mx, s.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     2, const_cast<void*>(X), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    s.tc ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
   }
   {
@@ -136,6 +168,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st) {
+  if (s.tc) return launch_mu_pass_tc(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \
   case MPV:                                                                 \
     return s.bf16 ? launch_pass_bf16_m##MPV(s.R, s, d, eps, mx, mh, st)    \

@@ -31,9 +31,11 @@ namespace ntt {
 
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
-__host__ __device__ constexpr int pick_nrg(int ms) {
+// Row groups of phase B: the fewest (power of two >= 8) that keep <= 5
+// stacked rows per thread, capped so that groups x rank blocks <= threads.
+__host__ __device__ constexpr int pick_nrg(int ms, int kbb, int nt) {
   int g = 8;
-  while ((ms + g - 1) / g > 9) g *= 2;
+  while ((ms + g - 1) / g > 5 && g * 2 * kbb <= nt) g *= 2;
   return g;
 }
 
@@ -44,17 +46,18 @@ struct PassCfg {
   static constexpr bool BF16 = BF16_;
   static constexpr int XB = BF16 ? 2 : 4;          // bytes per X element
   static constexpr int NT = kPassThreads;
-  static constexpr int T = cmax(16, cmin(256, 8192 / MP));
+  static constexpr int T = cmax(16, cmin(cmin(256, 8192 / MP), 4096 / R));
   static constexpr int CH = T / 4;                 // 4-column chunks per tile
   static constexpr int KBA = R / 8;                // 8-rank blocks (phase A)
   static constexpr int SA = NT / (CH * KBA);       // row splits (phase A)
   static constexpr int RPS = MP / SA;              // rows per split
   static constexpr int MS = MP + R;                // stacked rows [X ; H_new]
-  static constexpr int NRG = pick_nrg(MS);         // row groups (phase B)
+  static constexpr int KBB = R / 8;                // 8-rank blocks (phase B)
+  static constexpr int NRG = pick_nrg(MS, R / 8, NT);  // row groups (phase B)
   static constexpr int RB = (MS + NRG - 1) / NRG;  // rows per group
   static constexpr int MSP = NRG * RB;
-  static constexpr int KBB = R / 8;                // 8-rank blocks (phase B)
   static constexpr int CG = NT / (NRG * KBB);      // column groups (phase B)
+  static constexpr bool PAIRB = RB <= 5;           // packed column-pair accumulators
   static constexpr int CPT = T / CG;               // columns per thread per tile
   static constexpr int HKG = cmax(1, NT / T);      // threads per column (H update)
   static constexpr int KPT = cmax(1, R / HKG);     // ranks per thread (H update)
@@ -69,7 +72,8 @@ struct PassCfg {
   static constexpr int W_BYTES = MP * R * 4;
   static constexpr int G_BYTES = R * R * 4;
   static constexpr int BAR_BYTES = 64;
-  static constexpr int FIXED = HN_BYTES + Y_BYTES + W_BYTES + G_BYTES + BAR_BYTES + 1024;
+  static constexpr int HN_BUF = (HN_BYTES + 1023) / 1024 * 1024;   // one H_new buffer
+  static constexpr int FIXED = 2 * HN_BUF + Y_BYTES + W_BYTES + G_BYTES + BAR_BYTES + 1024;
   static constexpr int SMEM_CAP = 227 * 1024 - 256;
   static constexpr int STAGES = cmin(4, (SMEM_CAP - FIXED) / STAGE_BYTES);
   static constexpr int SMEM = STAGES * STAGE_BYTES + FIXED;
@@ -80,7 +84,7 @@ struct PassCfg {
   static_assert(CH * KBA * SA == NT && SA * RPS == MP, "phase A mapping");
   static_assert(NRG * KBB * CG == NT && CPT % 4 == 0 && CPT >= 4, "phase B mapping");
   static_assert(STAGES >= 2 && STAGES <= 4, "pipeline depth");
-  static_assert(RED_BYTES <= STAGES * STAGE_BYTES + HN_BYTES + Y_BYTES, "reduction scratch");
+  static_assert(RED_BYTES <= STAGES * STAGE_BYTES + 2 * HN_BUF + Y_BYTES, "reduction scratch");
   static_assert(SMEM <= SMEM_CAP, "shared memory");
   static_assert(MP % BR == 0 && T <= 256 && R <= 256, "TMA box");
 };
@@ -132,13 +136,14 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
                const PassParams p) {
   using XT = typename XLoad<C::BF16>::T;
   constexpr int T = C::T, R = C::R, MP = C::MP, NT = C::NT;
+  constexpr int HNF = C::HN_BUF / 4;   // floats per H_new buffer
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   uint8_t* stage_base = smem;
-  float* Hn = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES);
-  float* Ysm = Hn + C::HN_ROWS * T;
+  float* HnBuf = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES);  // 2 buffers
+  float* Ysm = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES + 2 * C::HN_BUF);
   float* Ws = Ysm + C::SA * R * T;
   float* Gs = Ws + MP * R;
   uint64_t* bars = reinterpret_cast<uint64_t*>(Gs + R * R);
@@ -147,23 +152,25 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   const int tid = threadIdx.x;
   const int m = p.m, r = p.r;
   const int64_t n = p.n;
+  const bool tma = p.use_tma != 0;
 
   if (tid == 0) {
     s_err = 0;
-    if (p.use_tma) {
+    if (tma) {
       prefetch_tensormap(&tmX);
       prefetch_tensormap(&tmH);
       for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
       fence_mbar_init();
     }
   }
-  // W (zero padded to MP x R), G (R x R), zero padding rows of the H_new stack
+  // W (zero padded to MP x R), G (R x R), zero padding rows of both H_new stacks
   for (int idx = tid; idx < MP * R; idx += NT) {
     const int i = idx / R, k = idx % R;
     Ws[idx] = (i < m && k < r) ? p.W[i * r + k] : 0.0f;
   }
   for (int idx = tid; idx < R * R; idx += NT) Gs[idx] = p.G[idx];
-  for (int idx = R * T + tid; idx < C::HN_ROWS * T; idx += NT) Hn[idx] = 0.0f;
+  for (int b = 0; b < 2; ++b)
+    for (int idx = R * T + tid; idx < C::HN_ROWS * T; idx += NT) HnBuf[b * HNF + idx] = 0.0f;
   __syncthreads();
 
   auto issue = [&](int stage, int tile) {
@@ -177,7 +184,7 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   };
 
   int issued = 0;  // tiles issued by thread 0 (TMA mode)
-  if (p.use_tma && tid == 0) {
+  if (tma && tid == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       const int tile = blockIdx.x + s * gridDim.x;
       if (tile < p.ntiles) {
@@ -187,25 +194,30 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     }
   }
 
-  // phase B accumulators (persistent over tiles): rows g*RB.., ranks kbb*8..
+  // phase B accumulators (persistent over tiles): stacked rows gB*RB.., ranks kbB*8..
   const int qB = tid % C::CG;
   const int kbB = (tid / C::CG) % C::KBB;
   const int gB = tid / (C::CG * C::KBB);
-  float accB[C::RB][8];
+  constexpr int NACC = C::PAIRB ? 2 : 1;
+  float accB[C::RB][8][NACC];
 #pragma unroll
   for (int i = 0; i < C::RB; ++i)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) accB[i][k] = 0.0f;
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int e = 0; e < NACC; ++e) accB[i][k][e] = 0.0f;
 
   int consumed = 0;
-  for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++consumed) {
+  int cur = 0;  // H_new buffer of this tile
+  for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++consumed, cur ^= 1) {
     const int stage = consumed % C::STAGES;
     const XT* Xs = reinterpret_cast<const XT*>(stage_base + stage * C::STAGE_BYTES);
     const float* Hs = reinterpret_cast<const float*>(stage_base + stage * C::STAGE_BYTES +
                                                      C::XS_BYTES);
+    float* Hn = HnBuf + cur * HNF;
     const int64_t col0 = (int64_t)tile * T;
 
-    if (p.use_tma) {
+    if (tma) {
       if (!mbar_wait_bounded(smem_u32(&bars[stage]), (consumed / C::STAGES) & 1)) s_err = 1;
     } else {
       XT* Xw = const_cast<XT*>(Xs);
@@ -224,35 +236,36 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       __syncthreads();
     }
 
-    // ---------------- phase A: partial Y = W^T X over this thread's rows
+    // ---------------- phase A: partial Y = W^T X over this thread's rows (packed FMA)
     {
       const int cq = tid % C::CH;
       const int kb = (tid / C::CH) % C::KBA;
       const int sa = tid / (C::CH * C::KBA);
-      float acc[8][4];
+      float2 acc[8][2];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
+      for (int k = 0; k < 8; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
       const XT* xp = Xs + (sa * C::RPS) * T + 4 * cq;
       const float* wp = Ws + (sa * C::RPS) * R + kb * 8;
 #pragma unroll 4
       for (int ii = 0; ii < C::RPS; ++ii) {
         const float4 x = XLoad<C::BF16>::ld4(xp + ii * T);
+        const float2 x01 = make_float2(x.x, x.y), x23 = make_float2(x.z, x.w);
         const float4 w0 = *reinterpret_cast<const float4*>(wp + ii * R);
         const float4 w1 = *reinterpret_cast<const float4*>(wp + ii * R + 4);
         const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          acc[k][0] = fmaf(w[k], x.x, acc[k][0]);
-          acc[k][1] = fmaf(w[k], x.y, acc[k][1]);
-          acc[k][2] = fmaf(w[k], x.z, acc[k][2]);
-          acc[k][3] = fmaf(w[k], x.w, acc[k][3]);
+          const float2 wk = make_float2(w[k], w[k]);
+          acc[k][0] = __ffma2_rn(wk, x01, acc[k][0]);
+          acc[k][1] = __ffma2_rn(wk, x23, acc[k][1]);
         }
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         *reinterpret_cast<float4*>(Ysm + (sa * R + kb * 8 + k) * T + 4 * cq) =
-            make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+            make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
     }
+    if (tma && tid == 0) bulk_wait_read<1>();  // the store of two tiles ago has read Hn[cur]
     __syncthreads();
     if (s_err) break;
 
@@ -260,37 +273,69 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     {
       const int c = tid % T;
       const int kg = tid / T;
-      if (kg < C::HKG && kg * C::KPT < R) {
+      if (kg * C::KPT < R) {
         float h[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) h[j] = Hs[j * T + c];
         const int64_t col = col0 + c;
+        if constexpr (C::HKG == 1) {
+          // one thread per column, all ranks: packed G H with G symmetric (row j = column j)
+          float2 gh[R / 2];
 #pragma unroll
-        for (int kk = 0; kk < C::KPT; ++kk) {
-          const int k = kg * C::KPT + kk;
-          float y = 0.0f;
+          for (int q = 0; q < R / 2; ++q) gh[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
-          for (int s = 0; s < C::SA; ++s) y += Ysm[(s * R + k) * T + c];
-          float gh = 0.0f;
+          for (int j = 0; j < R; ++j) {
+            const float2 hj = make_float2(h[j], h[j]);
 #pragma unroll
-          for (int j = 0; j < R; j += 4) {
-            const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + j);
-            gh = fmaf(g.x, h[j], gh);
-            gh = fmaf(g.y, h[j + 1], gh);
-            gh = fmaf(g.z, h[j + 2], gh);
-            gh = fmaf(g.w, h[j + 3], gh);
+            for (int q = 0; q < R / 4; ++q) {
+              const float4 g4 = *reinterpret_cast<const float4*>(Gs + j * R + 4 * q);
+              gh[2 * q] = __ffma2_rn(make_float2(g4.x, g4.y), hj, gh[2 * q]);
+              gh[2 * q + 1] = __ffma2_rn(make_float2(g4.z, g4.w), hj, gh[2 * q + 1]);
+            }
           }
-          float hk = 0.0f;
 #pragma unroll
-          for (int j = 0; j < R; ++j)
-            if (j == k) hk = h[j];
-          const float hn = fmaxf(0.0f, __fdividef(hk * y, gh + p.eps));
-          Hn[k * T + c] = hn;
-          if (k < r && col < n) p.H[(int64_t)k * n + col] = hn;
+          for (int k = 0; k < R; ++k) {
+            float y = 0.0f;
+#pragma unroll
+            for (int s = 0; s < C::SA; ++s) y += Ysm[(s * R + k) * T + c];
+            const float den = ((k & 1) ? gh[k / 2].y : gh[k / 2].x) + p.eps;
+            const float hn = fmaxf(0.0f, __fdividef(h[k] * y, den));
+            Hn[k * T + c] = hn;
+            if (!tma && k < r && col < n) p.H[(int64_t)k * n + col] = hn;
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < C::KPT; ++kk) {
+            const int k = kg * C::KPT + kk;
+            float y = 0.0f;
+#pragma unroll
+            for (int s = 0; s < C::SA; ++s) y += Ysm[(s * R + k) * T + c];
+            float gh = 0.0f;
+#pragma unroll
+            for (int j = 0; j < R; j += 4) {
+              const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + j);
+              gh = fmaf(g.x, h[j], gh);
+              gh = fmaf(g.y, h[j + 1], gh);
+              gh = fmaf(g.z, h[j + 2], gh);
+              gh = fmaf(g.w, h[j + 3], gh);
+            }
+            float hk = 0.0f;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+              if (j == k) hk = h[j];
+            const float hn = fmaxf(0.0f, __fdividef(hk * y, gh + p.eps));
+            Hn[k * T + c] = hn;
+            if (!tma && k < r && col < n) p.H[(int64_t)k * n + col] = hn;
+          }
         }
       }
     }
+    if (tma) fence_proxy_async_smem();   // H_new visible to the TMA store
     __syncthreads();
+    if (tma && tid == 0) {
+      tma_store_2d(&tmH, smem_u32(Hn), (int)col0, 0);
+      bulk_commit();
+    }
 
     // ---------------- phase B: [P ; Q] += [X_tile ; H_new] H_new^T
     {
@@ -309,21 +354,33 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             x = XLoad<C::BF16>::ld4(Xs + row * T + c);
           else
             x = *reinterpret_cast<const float4*>(Hn + (row - MP) * T + c);
+          if constexpr (C::PAIRB) {
+            const float2 x01 = make_float2(x.x, x.y), x23 = make_float2(x.z, x.w);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            float a = accB[i][k];
-            a = fmaf(x.x, h[k].x, a);
-            a = fmaf(x.y, h[k].y, a);
-            a = fmaf(x.z, h[k].z, a);
-            a = fmaf(x.w, h[k].w, a);
-            accB[i][k] = a;
+            for (int k = 0; k < 8; ++k) {
+              float2 a = make_float2(accB[i][k][0], accB[i][k][NACC - 1]);
+              a = __ffma2_rn(x01, make_float2(h[k].x, h[k].y), a);
+              a = __ffma2_rn(x23, make_float2(h[k].z, h[k].w), a);
+              accB[i][k][0] = a.x;
+              accB[i][k][NACC - 1] = a.y;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              float a = accB[i][k][0];
+              a = fmaf(x.x, h[k].x, a);
+              a = fmaf(x.y, h[k].y, a);
+              a = fmaf(x.z, h[k].z, a);
+              a = fmaf(x.w, h[k].w, a);
+              accB[i][k][0] = a;
+            }
           }
         }
       }
     }
     __syncthreads();
 
-    if (p.use_tma && tid == 0) {
+    if (tma && tid == 0) {
       const int next = tile + C::STAGES * gridDim.x;
       if (next < p.ntiles) {
         fence_proxy_async_smem();
@@ -335,13 +392,16 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 
   if (s_err) {
     // Drain copies still in flight (bounded) before the CTA exits.
-    if (p.use_tma && tid == 0) {
+    if (tma && tid == 0) {
       for (int c = consumed; c < issued; ++c)
         (void)mbar_wait_bounded(smem_u32(&bars[c % C::STAGES]), (c / C::STAGES) & 1);
+      bulk_wait<0>();
       atomicExch(p.status, kStatusTimeout);
     }
     return;
   }
+  if (tma && tid == 0) bulk_wait<0>();   // H stores complete before smem is reused
+  __syncthreads();
 
   // ---------------- CTA reduction of phase-B accumulators over column groups
   float* red = reinterpret_cast<float*>(smem);
@@ -349,7 +409,8 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   for (int i = 0; i < C::RB; ++i)
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      red[((gB * C::RB + i) * R + kbB * 8 + k) * C::CG + qB] = accB[i][k];
+      red[((gB * C::RB + i) * R + kbB * 8 + k) * C::CG + qB] =
+          C::PAIRB ? accB[i][k][0] + accB[i][k][NACC - 1] : accB[i][k][0];
   __syncthreads();
   float* out = p.part + (size_t)blockIdx.x * (C::MS * R);
   for (int e = tid; e < C::MS * R; e += NT) {

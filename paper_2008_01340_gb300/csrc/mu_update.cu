@@ -48,12 +48,20 @@ __device__ double block_sum_f64(double v, double* sh) {
 }
 
 // G = W^T W (R x R, zero outside r x r) from W (m x r) by the whole block.
+// Eight independent partial sums per entry (fixed order) keep the FMA chain short.
 __device__ void gram_block(const float* W, int m, int r, int R, float* G, float* Gs) {
   for (int kl = threadIdx.x; kl < R * R; kl += blockDim.x) {
     const int k = kl / R, l = kl % R;
     float g = 0.0f;
-    if (k < r && l < r)
-      for (int i = 0; i < m; ++i) g = fmaf(W[i * r + k], W[i * r + l], g);
+    if (k < r && l < r) {
+      float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      int i = 0;
+      for (; i + 8 <= m; i += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fmaf(W[(i + u) * r + k], W[(i + u) * r + l], a[u]);
+      for (; i < m; ++i) a[0] = fmaf(W[i * r + k], W[i * r + l], a[0]);
+      g = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
     G[kl] = g;
     if (Gs) Gs[kl] = g;
   }

@@ -237,12 +237,23 @@ __global__ void handoff_w_kernel(float* W, int64_t m, int r, float* s_out) {
   }
 }
 
+// grid.y = row k of H; 4-wide accesses when rows are 16-byte aligned.
 __global__ void handoff_h_kernel(float* H, int64_t n, int r, const float* s) {
-  const int64_t total = (int64_t)r * n;
+  const int k = blockIdx.y;
+  const float sk = s[k];
+  if (!(sk > 0.0f)) return;
+  float* row = H + (int64_t)k * n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const float sk = s[e / n];
-    if (sk > 0.0f) H[e] *= sk;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0) {
+    float4* r4 = reinterpret_cast<float4*>(row);
+    for (int64_t e = t0; e < n / 4; e += stride) {
+      float4 v = r4[e];
+      v.x *= sk; v.y *= sk; v.z *= sk; v.w *= sk;
+      r4[e] = v;
+    }
+  } else {
+    for (int64_t e = t0; e < n; e += stride) row[e] *= sk;
   }
 }
 
@@ -303,8 +314,10 @@ cudaError_t launch_handoff(float* W, float* H, int64_t m, int64_t n, int r, floa
   handoff_w_kernel<<<1, kAuxThreads, 0, st>>>(W, m, r, s_scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  handoff_h_kernel<<<grid_for((int64_t)r * n, kAuxThreads * 8), kAuxThreads, 0, st>>>(H, n, r,
-                                                                                     s_scratch);
+  int gx = grid_for(n / 4 + 1, kAuxThreads * 4);
+  const int cap = (device_sms() * 8 + r - 1) / r;
+  if (gx > cap) gx = cap;
+  handoff_h_kernel<<<dim3(gx, r), kAuxThreads, 0, st>>>(H, n, r, s_scratch);
   return cudaGetLastError();
 }
 

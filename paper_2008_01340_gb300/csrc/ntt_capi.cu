@@ -52,7 +52,7 @@ struct MuWs {
   size_t status, tickets, scal, G, red, part, part64;
 };
 
-size_t mu_partial_floats(const MuShape& s) { return (size_t)s.grid * s.part_stride(); }
+size_t mu_partial_floats(const MuShape& s) { return (size_t)s.grid_cap * s.part_stride(); }
 
 // Launch the gram and `iters` (pass, combine) pairs of one NMF.
 ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
@@ -61,7 +61,7 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
   std::memset(&mx, 0, sizeof(mx));
   std::memset(&mh, 0, sizeof(mh));
   MuShape s = shp;
-  s.tma = mu_tma_ok(s, dev.X, dev.H) ? 1 : 0;
+  mu_finalize_shape(&s, dev.X, dev.H, device_sms());
   if (s.tma) NTT_TRY(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
   for (int t = 0; t < iters; ++t) {
     NTT_CUDA_TRY(launch_mu_pass(s, dev, eps, mx, mh, st));

@@ -354,3 +354,21 @@ def test_c2_full_size_decompose_properties(ntt, c2_full):
     e = err[0].item()
     print(f"32^6 relative error {e:.5f}, total {stats['total_ms']:.1f} ms")
     assert 0.0 < e < 0.05
+
+
+@pytest.mark.parametrize("m,n,r", [(32, 70000, 8), (16, 20000, 16), (24, 9000, 8), (32, 8192, 12),
+                                   (32, 9000 * 128, 8)])
+def test_tensor_core_and_fma_passes_agree(ntt, m, n, r, monkeypatch):
+    """The tcgen05 pass (m <= 32, r <= 16, selected by NTT_PASS=tc) and the
+    default FMA pass both match the oracle's iterates within the FP32 tolerance."""
+    X = _x_matrix("lowrank", m, n, 77 + m)
+    W0 = synth.uniform_matrix((m, r), 78)
+    H0 = synth.uniform_matrix((r, n), 79)
+    monkeypatch.setenv("NTT_PASS", "tc")
+    Wt, Ht, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    monkeypatch.delenv("NTT_PASS")
+    Wf, Hf, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    Wo, Ho, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
+    for Wg, Hg in ((Wt, Ht), (Wf, Hf)):
+        assert _fro_rel(Wg, Wo) <= REL_ITERATE
+        assert _fro_rel(Hg, Ho) <= REL_ITERATE
