@@ -150,6 +150,26 @@ ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_d
                        float* W, float* H, int iters, float eps_mu, double* obj_dev,
                        void* ws, void* stream);
 
+/* nmf_mu_step without a workspace argument, for callers that cannot allocate
+ * device memory (for instance a plugin running inside a host process whose own
+ * runtime owns every device allocation, or a control loop that must not take
+ * the implicit synchronisation of cudaMalloc).  The paper has no counterpart:
+ * this is an interface convenience of the library.
+ *   Scratch: one file-scope device array of 8 MiB (8 << 20 bytes), held by
+ *   every GPU that loads the library until the process exits.  Shapes whose
+ *   nmf_mu_workspace_size exceeds 8 MiB return NTT_ERR_OOM and launch nothing
+ *   (m <= 512 with r <= 16 always fit; m = 512 with r = 32 does not).
+ *   All calls on a device share the array and it keeps the last call's
+ *   contents; each call clears the words that must start at zero.  Calls whose
+ *   device work overlaps (different streams or host threads) race: serialise
+ *   them.  The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  No allocation of any kind is made.
+ * Other arguments and results as for nmf_mu_step. */
+ntt_status nmf_mu_step_noalloc(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
+                               float* W, float* H, int iters, float eps_mu, double* obj_dev,
+                               void* stream);
+
 /* Device status word left in an nmf_mu_step workspace (sync first). */
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out);
 

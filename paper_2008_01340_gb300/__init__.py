@@ -42,7 +42,7 @@ EXPORTS = (
     "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
-    "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio",
+    "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
 )
 
 
@@ -112,6 +112,7 @@ def lib():
     L.ntt_plan_destroy.argtypes = [vp]
     L.nmf_mu_workspace_size.argtypes = [i64, i64, i32, i32, psz]
     L.nmf_mu_step.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.nmf_mu_step_noalloc.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp]
     L.ntt_status_of_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ntt_uniform_init.argtypes = [ctypes.c_uint64, i32, i32, i32, i64, vp, vp]
     L.ntt_reconstruct_workspace_size.argtypes = [i32, p64, p64, psz]
@@ -291,6 +292,25 @@ def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=N
                              int(iters), float(eps_mu), optr, _dev_ptr(workspace, None, "ws"),
                              _stream_ptr(stream)), "nmf_mu_step")
     return workspace
+
+
+def nmf_mu_step_noalloc(X, W, H, iters, eps_mu=1e-12, obj=None, stream=None):
+    """nmf_mu_step for callers that cannot allocate device memory: the scratch is
+    the library's own 8 MiB device array (see include/ntt.h); shapes that need
+    more raise NTTError (NTT_ERR_OOM).  Calls on one device must not overlap."""
+    import torch
+    if X.dim() != 2 or W.dim() != 2 or H.dim() != 2:
+        raise ValueError("X, W, H must be matrices")
+    m, n = X.shape
+    r = W.shape[1]
+    if W.shape[0] != m or H.shape != (r, n):
+        raise ValueError("shape mismatch")
+    xd = NTT_BF16 if X.dtype == torch.bfloat16 else NTT_F32
+    optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
+    _check(lib().nmf_mu_step_noalloc(m, n, r, _dev_ptr(X, None, "X"), xd,
+                                     _dev_ptr(W, torch.float32, "W"),
+                                     _dev_ptr(H, torch.float32, "H"), int(iters), float(eps_mu),
+                                     optr, _stream_ptr(stream)), "nmf_mu_step_noalloc")
 
 
 def ntt_status_of_workspace(workspace):
