@@ -199,6 +199,40 @@ ntt_status ntt_rel_error(int d, const int64_t* dims, const int64_t* ranks,
                          const float* const* cores, const float* A, double* err_dev,
                          void* ws, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: B independent nTTs, each stage solved from `restarts` random
+ * initialisations (restart j of stage s of instance i uses the init streams
+ * (seed + i, s, j, 0/1)); the restart with the lowest final 1/2||X - WH||^2
+ * is kept (ties: lowest index), hand-off normalised, and its H becomes the
+ * next unfolding (Algorithm 2 per instance).  Small unfoldings are solved one
+ * NMF per CTA in shared memory; large ones run several restarts side by side
+ * in one streaming pass (restarts are independent blocks of one NMF).
+ * ------------------------------------------------------------------------ */
+typedef struct ntt_batch_s* ntt_batch;
+
+/* d[i] (B entries), dims (sum d[i] entries), ranks (sum (d[i]+1) entries),
+ * all host arrays, instance after instance.  Validates like ntt_plan_create. */
+ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int64_t* ranks,
+                            int iters, int restarts, float eps_mu, uint64_t seed, ntt_batch* out);
+
+/* Sizes of the packed input (floats), packed cores (floats) and workspace (bytes). */
+ntt_status ntt_batch_sizes(ntt_batch b, size_t* input_floats, size_t* core_floats,
+                           size_t* workspace_bytes);
+
+/* Offsets (in floats) of each instance's tensor in the packed input (B entries)
+ * and of each core in the packed cores (sum d[i] entries, instance after instance). */
+ntt_status ntt_batch_offsets(ntt_batch b, int64_t* input_off, int64_t* core_off);
+
+/* Decompose all instances.  A: device packed tensors (C order each); cores:
+ * device packed cores (core k of instance i is r_k x n_{k+1} x r_{k+1});
+ * workspace: device, ntt_batch_sizes bytes, 256-byte aligned.  Returns after
+ * the stream has finished the work (synchronises `stream`), with the device
+ * status word. */
+ntt_status ntt_decompose_batched(ntt_batch b, const float* A, float* cores, void* workspace,
+                                 void* stream);
+
+ntt_status ntt_batch_destroy(ntt_batch b);
+
 /* Eq. (4): prod n_i / sum n_i r_{i-1} r_i (host arithmetic). */
 double ntt_compression_ratio(int d, const int64_t* dims, const int64_t* ranks);
 

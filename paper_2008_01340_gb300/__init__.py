@@ -43,6 +43,8 @@ EXPORTS = (
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
+    "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
+    "ntt_batch_destroy",
 )
 
 
@@ -118,6 +120,13 @@ def lib():
     L.ntt_reconstruct_workspace_size.argtypes = [i32, p64, p64, psz]
     L.ntt_reconstruct.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp]
     L.ntt_rel_error.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp, vp]
+    psz_ = ctypes.POINTER(ctypes.c_size_t)
+    L.ntt_batch_create.argtypes = [i32, ctypes.POINTER(ctypes.c_int), p64, p64, i32, i32,
+                                   ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.ntt_batch_sizes.argtypes = [vp, psz_, psz_, psz_]
+    L.ntt_batch_offsets.argtypes = [vp, p64, p64]
+    L.ntt_decompose_batched.argtypes = [vp, vp, vp, vp, vp]
+    L.ntt_batch_destroy.argtypes = [vp]
     L.ntt_compression_ratio.restype = ctypes.c_double
     L.ntt_compression_ratio.argtypes = [i32, p64, p64]
     for name in EXPORTS:
@@ -357,6 +366,67 @@ def ntt_rel_error(dims, ranks, cores, A, err, workspace=None, stream=None):
                                _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)),
            "ntt_rel_error")
     return workspace
+
+
+class Batch:
+    """Plan of the batched form: B instances (dims, ranks), restarts per stage."""
+
+    def __init__(self, instances, iters, restarts, eps_mu=1e-12, seed=0):
+        self.instances = [(tuple(int(x) for x in d), tuple(int(x) for x in r)) for d, r in instances]
+        B = len(self.instances)
+        d_arr = (ctypes.c_int * B)(*[len(d) for d, _ in self.instances])
+        dims = _i64arr([x for d, _ in self.instances for x in d])
+        ranks = _i64arr([x for _, r in self.instances for x in r])
+        h = ctypes.c_void_p()
+        _check(lib().ntt_batch_create(B, d_arr, dims, ranks, int(iters), int(restarts),
+                                      float(eps_mu), int(seed), ctypes.byref(h)), "ntt_batch_create")
+        self.handle = h
+        a, c, w = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().ntt_batch_sizes(h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(w)),
+               "ntt_batch_sizes")
+        self.input_floats, self.core_floats, self.workspace_bytes = a.value, c.value, w.value
+        io = (ctypes.c_int64 * B)()
+        co = (ctypes.c_int64 * sum(len(d) for d, _ in self.instances))()
+        _check(lib().ntt_batch_offsets(h, io, co), "ntt_batch_offsets")
+        self.input_off = list(io)
+        self.core_off = list(co)
+
+    def core_views(self, cores_packed):
+        """Per instance, the list of its cores as views of the packed buffer."""
+        out, c = [], 0
+        for dims, ranks in self.instances:
+            lst = []
+            for k, n in enumerate(dims):
+                size = ranks[k] * n * ranks[k + 1]
+                lst.append(cores_packed[self.core_off[c]:self.core_off[c] + size]
+                           .view(ranks[k], n, ranks[k + 1]))
+                c += 1
+            out.append(lst)
+        return out
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().ntt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ntt_batch_create(instances, iters, restarts, eps_mu=1e-12, seed=0):
+    return Batch(instances, iters, restarts, eps_mu, seed)
+
+
+def ntt_decompose_batched(batch, A_packed, cores_packed, workspace, stream=None):
+    """A_packed / cores_packed: CUDA float32 tensors laid out by batch.input_off / core_off."""
+    import torch
+    _check(lib().ntt_decompose_batched(batch.handle, _dev_ptr(A_packed, torch.float32, "A"),
+                                       _dev_ptr(cores_packed, torch.float32, "cores"),
+                                       _dev_ptr(workspace, None, "workspace"), _stream_ptr(stream)),
+           "ntt_decompose_batched")
 
 
 def ntt_compression_ratio(dims, ranks):

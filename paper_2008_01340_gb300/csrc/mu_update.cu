@@ -31,6 +31,7 @@ struct CombineParams {
   int t;
   const double* xnorm2;
   float eps;
+  int blk;   // > 0: W^T W and H H^T masked to diagonal blocks of this size
 };
 
 // Deterministic FP64 block sum of one value per thread (tree over smem).
@@ -49,11 +50,14 @@ __device__ double block_sum_f64(double v, double* sh) {
 
 // G = W^T W (R x R, zero outside r x r) from W (m x r) by the whole block.
 // Eight independent partial sums per entry (fixed order) keep the FMA chain short.
-__device__ void gram_block(const float* W, int m, int r, int R, float* G, float* Gs) {
+// blk > 0 keeps only the diagonal blk x blk blocks: the columns of W are then
+// independent restarts of rank blk solved side by side (their updates only
+// ever couple through these Gram matrices).
+__device__ void gram_block(const float* W, int m, int r, int R, float* G, float* Gs, int blk) {
   for (int kl = threadIdx.x; kl < R * R; kl += blockDim.x) {
     const int k = kl / R, l = kl % R;
     float g = 0.0f;
-    if (k < r && l < r) {
+    if (k < r && l < r && (blk <= 0 || k / blk == l / blk)) {
       float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       int i = 0;
       for (; i + 8 <= m; i += 8)
@@ -121,14 +125,15 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
         float wq = 0.0f;
 #pragma unroll
         for (int j = 0; j < NTT_MAX_RANK; ++j)
-          if (j < r) wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
+          if (j < r && (p.blk <= 0 || j / p.blk == k / p.blk))
+            wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
         Wn[i * r + k] = fmaxf(0.0f, __fdiv_rn(w[k] * red_s[i * R + k], wq + p.eps));
       }
     }
   }
   __syncthreads();
   for (int e = tid; e < m * r; e += blockDim.x) p.W[e] = Wn[e];
-  gram_block(Wn, m, r, R, p.G, Gs);
+  gram_block(Wn, m, r, R, p.G, Gs, p.blk);
   __syncthreads();
   if (p.obj) {
     double a = 0.0, b = 0.0;
@@ -138,7 +143,8 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
     }
     for (int kl = tid; kl < r * r; kl += blockDim.x) {
       const int k = kl / r, l = kl % r;
-      b += (double)Gs[k * R + l] * (double)red_s[(MP + k) * R + l];
+      if (p.blk <= 0 || k / p.blk == l / p.blk)
+        b += (double)Gs[k * R + l] * (double)red_s[(MP + k) * R + l];
     }
     const double A = block_sum_f64(a, dsh);
     const double B = block_sum_f64(b, dsh);
@@ -148,8 +154,8 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
 }
 
 __global__ void __launch_bounds__(kAuxThreads) gram_kernel(const float* W, int m, int r, int R,
-                                                           float* G) {
-  gram_block(W, m, r, R, G, nullptr);
+                                                           float* G, int blk) {
+  gram_block(W, m, r, R, G, nullptr, blk);
 }
 
 }  // namespace
@@ -177,6 +183,7 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
   p.t = t;
   p.xnorm2 = d.xnorm2;
   p.eps = eps;
+  p.blk = d.blk;
   const int E = s.part_stride();
   const int blocks = (E + kEntriesPerBlock - 1) / kEntriesPerBlock;
   const size_t smem = (size_t)(E + s.m * s.r + s.R * s.R) * sizeof(float);
@@ -185,7 +192,7 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
 }
 
 cudaError_t launch_gram(const MuShape& s, const MuDev& d, cudaStream_t st) {
-  gram_kernel<<<1, kAuxThreads, 0, st>>>(d.W, (int)s.m, s.r, s.R, d.G);
+  gram_kernel<<<1, kAuxThreads, 0, st>>>(d.W, (int)s.m, s.r, s.R, d.G, d.blk);
   return cudaGetLastError();
 }
 

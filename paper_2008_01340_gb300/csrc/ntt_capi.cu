@@ -9,11 +9,69 @@
 
 #include "ntt_internal.cuh"
 
+#define NTT_CUDA_TRY_NS(expr)                      \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) {                       \
+      cudaGetLastError();                          \
+      return NTT_ERR_CUDA;                         \
+    }                                              \
+  } while (0)
+#define NTT_TRY_NS(expr)             \
+  do {                               \
+    ntt_status s_ = (expr);          \
+    if (s_ != NTT_OK) return s_;     \
+  } while (0)
+
 using namespace ntt;
+
+namespace ntt {
+
+// Launch the gram and `iters` (pass, combine) pairs of one NMF.
+ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
+                        cudaStream_t st) {
+  CUtensorMap mx, mh;
+  std::memset(&mx, 0, sizeof(mx));
+  std::memset(&mh, 0, sizeof(mh));
+  MuShape s = shp;
+  mu_finalize_shape(&s, dev.X, dev.H, device_sms());
+  if (s.tma) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
+  for (int t = 0; t < iters; ++t) {
+    NTT_CUDA_TRY_NS(launch_mu_pass(s, dev, eps, mx, mh, st));
+    MuDev d2 = dev;
+    NTT_CUDA_TRY_NS(launch_mu_combine(s, d2, eps, t0 + t, st));
+  }
+  return NTT_OK;
+}
+
+ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
+                      int64_t N, int r, int mode, double scale, double* acc, double* rel,
+                      double* part64, unsigned* ticket, cudaStream_t st) {
+  ResidArgs a;
+  a.X = X;
+  a.xbf16 = xbf16;
+  a.L = L;
+  a.Rm = Rm;
+  a.M = M;
+  a.N = N;
+  a.r = r;
+  a.mode = mode;
+  a.part64 = part64;
+  a.ticket = ticket;
+  a.acc = acc;
+  a.rel = rel;
+  a.scale = scale;
+  int blocks = resid_blocks(device_sms());
+  if (blocks > kMaxResidBlocks) blocks = kMaxResidBlocks;
+  NTT_CUDA_TRY_NS(launch_resid(a, blocks, st));
+  return NTT_OK;
+}
+
+
+}  // namespace ntt
 
 namespace {
 
-constexpr int kMaxResidBlocks = 4096;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
@@ -53,46 +111,6 @@ struct MuWs {
 };
 
 size_t mu_partial_floats(const MuShape& s) { return (size_t)s.grid_cap * s.part_stride(); }
-
-// Launch the gram and `iters` (pass, combine) pairs of one NMF.
-ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
-                        cudaStream_t st) {
-  CUtensorMap mx, mh;
-  std::memset(&mx, 0, sizeof(mx));
-  std::memset(&mh, 0, sizeof(mh));
-  MuShape s = shp;
-  mu_finalize_shape(&s, dev.X, dev.H, device_sms());
-  if (s.tma) NTT_TRY(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
-  for (int t = 0; t < iters; ++t) {
-    NTT_CUDA_TRY(launch_mu_pass(s, dev, eps, mx, mh, st));
-    MuDev d2 = dev;
-    NTT_CUDA_TRY(launch_mu_combine(s, d2, eps, t0 + t, st));
-  }
-  return NTT_OK;
-}
-
-ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
-                      int64_t N, int r, int mode, double scale, double* acc, double* rel,
-                      double* part64, unsigned* ticket, cudaStream_t st) {
-  ResidArgs a;
-  a.X = X;
-  a.xbf16 = xbf16;
-  a.L = L;
-  a.Rm = Rm;
-  a.M = M;
-  a.N = N;
-  a.r = r;
-  a.mode = mode;
-  a.part64 = part64;
-  a.ticket = ticket;
-  a.acc = acc;
-  a.rel = rel;
-  a.scale = scale;
-  int blocks = resid_blocks(device_sms());
-  if (blocks > kMaxResidBlocks) blocks = kMaxResidBlocks;
-  NTT_CUDA_TRY(launch_resid(a, blocks, st));
-  return NTT_OK;
-}
 
 int split_point(int d, const int64_t* dims) {
   double total = 0.0;

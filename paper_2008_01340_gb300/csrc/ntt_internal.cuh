@@ -297,6 +297,7 @@ struct MuDev {
   double* obj = nullptr;         // objective trace or nullptr
   const double* xnorm2 = nullptr;
   int* status = nullptr;
+  int blk = 0;                   // > 0: independent restarts of rank blk side by side
 };
 
 // Pick template bucket, tile width and grid for an m x n x r problem.
@@ -357,5 +358,15 @@ cudaError_t launch_handoff(float* W, float* H, int64_t m, int64_t n, int r, floa
 
 // Number of SMs of the current device (cached; 152 when no device).
 int device_sms();
+
+constexpr int kMaxResidBlocks = 4096;
+// Enqueue the gram and `iters` (pass, combine) pairs of one NMF (t0 = index of
+// the first objective entry).
+ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
+                        cudaStream_t st);
+// Enqueue one residual / norm pass (see ResidArgs); part64 holds 2 * kMaxResidBlocks doubles.
+ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
+                      int64_t N, int r, int mode, double scale, double* acc, double* rel,
+                      double* part64, unsigned* ticket, cudaStream_t st);
 
 }  // namespace ntt

@@ -1,0 +1,90 @@
+"""Batched form (restarts per stage, best restart kept) against the oracle's
+Algorithm 2 with the same restart rule, per instance.
+
+Tolerances: per-iterate relative Frobenius difference of every core <= 1e-4
+times the stage index (errors of earlier stages propagate) after 10 updates per
+stage; after a longer run, the relative error (Eq. 3) within 1e-3 absolute."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ntt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2008_01340_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+INSTANCES = [
+    ((6, 7, 8), (1, 3, 4, 1)),                 # all stages in shared memory
+    ((10, 9, 8, 7), (1, 4, 5, 3, 1)),          # small stages, d = 4
+    ((16, 12, 20, 24), (1, 8, 12, 6, 1)),      # stage 1 large: restarts side by side (r=8, 4 per pass)
+    ((24, 20, 16, 12), (1, 12, 10, 6, 1)),     # stages 1-2 large, r = 12 and 10 (2 and 3 restarts per pass)
+    ((8, 8), (1, 2, 1)),                       # d = 2
+]
+
+
+def _run(ntt, instances, iters, restarts, seed):
+    b = ntt.ntt_batch_create(instances, iters, restarts, 1e-12, seed)
+    A = torch.zeros(b.input_floats, dtype=torch.float32)
+    tensors = []
+    for i, (dims, ranks) in enumerate(instances):
+        T, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=700 + i)
+        tensors.append(T)
+        A[b.input_off[i]:b.input_off[i] + T.size] = torch.from_numpy(T.ravel())
+    Ad = A.cuda()
+    cores = torch.zeros(b.core_floats, dtype=torch.float32, device="cuda")
+    ws = ntt.empty_workspace(b.workspace_bytes)
+    ntt.ntt_decompose_batched(b, Ad, cores, ws)
+    views = [[c.cpu().numpy() for c in lst] for lst in b.core_views(cores)]
+    return tensors, views
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_batched_per_iterate_matches_oracle(ntt):
+    seed, restarts, iters = 4000, 4, 10
+    tensors, views = _run(ntt, INSTANCES, iters, restarts, seed)
+    for i, ((dims, ranks), T) in enumerate(zip(INSTANCES, tensors)):
+        ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
+        for k, (g, o) in enumerate(zip(views[i], ref)):
+            assert _rel(g, o) <= 1e-4 * (k + 1), f"instance {i} core {k}: {_rel(g, o):.2e}"
+            assert np.all(g >= 0)
+
+
+def test_batched_final_error_matches_oracle(ntt):
+    seed, restarts, iters = 99, 3, 150
+    inst = INSTANCES[:3]
+    tensors, views = _run(ntt, inst, iters, restarts, seed)
+    for i, ((dims, ranks), T) in enumerate(zip(inst, tensors)):
+        ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
+        eg, eo = oracle.rel_error(T, views[i]), oracle.rel_error(T, ref)
+        assert abs(eg - eo) <= 1e-3, f"instance {i}: {eg} vs {eo}"
+
+
+def test_batched_equals_single_instance_plan_with_one_restart(ntt):
+    # with one restart the batched form is Algorithm 2 of each instance alone
+    seed = 7
+    inst = [INSTANCES[1], INSTANCES[2]]
+    tensors, views = _run(ntt, inst, 12, 1, seed)
+    for i, ((dims, ranks), T) in enumerate(zip(inst, tensors)):
+        plan = ntt.ntt_plan_create(dims, ranks, 12, 1e-12, "f32", 0, seed + i)
+        ws = ntt.empty_workspace(plan.workspace_size())
+        cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
+        ntt.ntt_decompose(plan, torch.from_numpy(T).cuda(), cores, ws)
+        torch.cuda.synchronize()
+        for k, (g, c) in enumerate(zip(views[i], cores)):
+            assert _rel(g, c.cpu().numpy()) <= 1e-4 * (k + 1)
