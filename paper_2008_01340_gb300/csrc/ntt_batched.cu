@@ -37,6 +37,7 @@ constexpr int kSmallThreads = 256;
 constexpr int kSmallMaxR = 16;
 constexpr size_t kSmallSmemCap = 200 * 1024;
 constexpr int kMaxRestarts = 16;
+constexpr int kStreams = 16;
 
 struct SmallTask {
   const float* X;
@@ -258,18 +259,34 @@ struct ntt_batch_s {
     uint64_t seed;
   };
   std::vector<Inst> inst;
+  // large stages run on kStreams streams, instance i on stream i % kStreams,
+  // each stream with its own scratch slice
+  struct Lane {
+    size_t G, red, part, part64, tickets, scal, rtmp, lW, lH, lWg, job;
+  };
+  std::vector<Lane> lane;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
   int iters = 0, restarts = 1;
   float eps = 1e-12f;
   size_t a_total = 0, cores_total = 0;
   // workspace layout (bytes)
-  size_t off_status, off_tickets, off_scal, off_G, off_red, off_part, off_part64, off_obj,
-      off_rtmp, off_tasks, off_jobs, off_small, off_lW, off_lH, off_lWg, off_x, bytes;
+  size_t off_status, off_tickets, off_scal, off_obj, off_tasks, off_jobs, off_small, off_x, bytes;
   size_t max_tasks = 0, max_jobs = 0;
   int max_stages = 0;
   std::vector<SmallTask> h_tasks;
   std::vector<SelectJob> h_jobs;
   cudaStream_t last_stream = nullptr;
   void* last_ws = nullptr;
+  ~ntt_batch_s() {
+    for (auto st : streams)
+      if (st) cudaStreamDestroy(st);
+    for (auto e : ev_join)
+      if (e) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    cudaGetLastError();
+  }
 };
 
 namespace {
@@ -285,6 +302,17 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
   double* obj = reinterpret_cast<double*>(ws + b->off_obj);
   if (cudaMemsetAsync(status, 0, 64, st) != cudaSuccess || cudaMemsetAsync(tickets, 0, 64, st) != cudaSuccess)
     return NTT_ERR_CUDA;
+  if (b->streams.empty()) {
+    b->streams.assign(kStreams, nullptr);
+    b->ev_join.assign(kStreams, nullptr);
+    for (int l = 0; l < kStreams; ++l)
+      if (cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[l], cudaEventDisableTiming) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) return NTT_ERR_CUDA;
+  }
+  for (const auto& L : b->lane)
+    if (cudaMemsetAsync(ws + L.tickets, 0, 64, st) != cudaSuccess) return NTT_ERR_CUDA;
   const int R = b->restarts;
   const int sms = device_sms();
   for (int s = 0; s < b->max_stages; ++s) {
@@ -338,19 +366,28 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
                                                           b->eps);
       if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
     }
-    // ---- large tasks, one instance at a time, g restarts side by side
+    // ---- large tasks: instance i on lane i % kStreams, g restarts side by side
+    if (!large.empty()) {
+      if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return NTT_ERR_CUDA;
+      for (int l = 0; l < kStreams; ++l)
+        if (cudaStreamWaitEvent(b->streams[l], b->ev_fork, 0) != cudaSuccess) return NTT_ERR_CUDA;
+    }
     for (int i : large) {
       auto& I = b->inst[i];
+      const int lid = i % kStreams;
+      const auto& L = b->lane[lid];
+      cudaStream_t ls = b->streams[lid];
       const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
       const int r = (int)I.ranks[s + 1];
       const float* X = (s == 0) ? A + I.a_off
                                 : reinterpret_cast<const float*>(ws + b->off_x) + I.x_off[(s - 1) & 1];
-      float* Wall = reinterpret_cast<float*>(ws + b->off_lW);
-      float* Hall = reinterpret_cast<float*>(ws + b->off_lH);
-      float* Wg = reinterpret_cast<float*>(ws + b->off_lWg);
-      double* xn2 = scal;
-      NTT_TRY_B(resid_into(X, 0, nullptr, nullptr, m, n, 0, 0, 1.0, xn2, nullptr,
-                           reinterpret_cast<double*>(ws + b->off_part64), tickets + 1, st));
+      float* Wall = reinterpret_cast<float*>(ws + L.lW);
+      float* Hall = reinterpret_cast<float*>(ws + L.lH);
+      float* Wg = reinterpret_cast<float*>(ws + L.lWg);
+      unsigned* lt = reinterpret_cast<unsigned*>(ws + L.tickets);
+      double* xn2 = reinterpret_cast<double*>(ws + L.scal);
+      double* part64 = reinterpret_cast<double*>(ws + L.part64);
+      NTT_TRY_B(resid_into(X, 0, nullptr, nullptr, m, n, 0, 0, 1.0, xn2, nullptr, part64, lt + 1, ls));
       const int g = std::max(1, std::min(R, NTT_MAX_RANK / r));
       for (int j0 = 0; j0 < R; j0 += g) {
         const int gj = std::min(g, R - j0);
@@ -361,7 +398,7 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
           keys.h[q] = stream_key(I.seed, s, j0 + q, 1);
         }
         float* Hg = Hall + (size_t)j0 * r * n;
-        init_group_kernel<<<sms * 4, 256, 0, st>>>(Wg, Hg, (int)m, n, r, gj, keys);
+        init_group_kernel<<<sms * 2, 256, 0, ls>>>(Wg, Hg, (int)m, n, r, gj, keys);
         if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
         MuShape shp;
         NTT_TRY_B(mu_choose_shape(m, n, gj * r, 0, sms, &shp));
@@ -369,29 +406,27 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
         dev.X = X;
         dev.W = Wg;
         dev.H = Hg;
-        dev.G = reinterpret_cast<float*>(ws + b->off_G);
-        dev.part = reinterpret_cast<float*>(ws + b->off_part);
-        dev.red = reinterpret_cast<float*>(ws + b->off_red);
-        dev.ticket = tickets;
+        dev.G = reinterpret_cast<float*>(ws + L.G);
+        dev.part = reinterpret_cast<float*>(ws + L.part);
+        dev.red = reinterpret_cast<float*>(ws + L.red);
+        dev.ticket = lt;
         dev.obj = nullptr;
         dev.xnorm2 = xn2;
         dev.status = status;
         dev.blk = r;
-        if (launch_gram(shp, dev, st) != cudaSuccess) return NTT_ERR_CUDA;
-        NTT_TRY_B(run_mu_iters(shp, dev, b->eps, b->iters, 0, st));
-        split_group_w_kernel<<<64, 256, 0, st>>>(Wg, Wall + (size_t)j0 * m * r, (int)m, r, gj);
+        if (launch_gram(shp, dev, ls) != cudaSuccess) return NTT_ERR_CUDA;
+        NTT_TRY_B(run_mu_iters(shp, dev, b->eps, b->iters, 0, ls));
+        split_group_w_kernel<<<64, 256, 0, ls>>>(Wg, Wall + (size_t)j0 * m * r, (int)m, r, gj);
         if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-        double* rtmp = reinterpret_cast<double*>(ws + b->off_rtmp);
+        double* rtmp = reinterpret_cast<double*>(ws + L.rtmp);
         for (int q = 0; q < gj; ++q) {
           NTT_TRY_B(resid_into(X, 0, Wall + (size_t)(j0 + q) * m * r, Hg + (size_t)q * r * n, m, n, r, 1,
-                               0.5, rtmp + 2 * q, nullptr,
-                               reinterpret_cast<double*>(ws + b->off_part64), tickets + 1, st));
+                               0.5, rtmp + 2 * q, nullptr, part64, lt + 1, ls));
           if (cudaMemcpyAsync(obj + (size_t)i * R + j0 + q, rtmp + 2 * q, sizeof(double),
-                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                              cudaMemcpyDeviceToDevice, ls) != cudaSuccess)
             return NTT_ERR_CUDA;
         }
       }
-      // select now (the large scratch is reused by the next instance)
       SelectJob jb;
       jb.Wc = Wall;
       jb.Hc = Hall;
@@ -406,13 +441,19 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
       jb.r = r;
       jb.restarts = R;
       jb.pad = 0;
-      SelectJob* dj = reinterpret_cast<SelectJob*>(ws + b->off_jobs) + b->max_jobs;  // private slot
-      if (cudaMemcpyAsync(dj, &jb, sizeof(jb), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      SelectJob* dj = reinterpret_cast<SelectJob*>(ws + L.job);
+      if (cudaMemcpyAsync(dj, &jb, sizeof(jb), cudaMemcpyHostToDevice, ls) != cudaSuccess)
         return NTT_ERR_CUDA;
       select_kernel<<<dim3(std::max<int64_t>(1, std::min<int64_t>(sms * 4, (r * n + 1023) / 1024)), 1),
-                      256, 0, st>>>(dj, 1);
+                      256, 0, ls>>>(dj, 1);
       if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
     }
+    if (!large.empty())
+      for (int l = 0; l < kStreams; ++l) {
+        if (cudaEventRecord(b->ev_join[l], b->streams[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, b->ev_join[l], 0) != cudaSuccess)
+          return NTT_ERR_CUDA;
+      }
     // ---- selection for the small instances of this stage
     b->h_jobs.clear();
     {
@@ -471,7 +512,9 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
   b->restarts = restarts;
   b->eps = eps_mu;
   size_t dpos = 0, rpos = 0, a_total = 0, c_total = 0, x_total = 0;
-  size_t small_max = 0, lW = 1, lH = 1, lWg = 1, part_max = 1, red_max = 1;
+  size_t small_max = 0;
+  std::vector<size_t> lW(kStreams, 1), lH(kStreams, 1), lWg(kStreams, 1), part_max(kStreams, 1),
+      red_max(kStreams, 1);
   std::vector<size_t> small_per_stage(NTT_MAX_D, 0), tasks_per_stage(NTT_MAX_D, 0),
       jobs_per_stage(NTT_MAX_D, 0);
   const int sms = device_sms();
@@ -514,17 +557,18 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
         small_per_stage[s] += (size_t)restarts * (m * r + r * n);
         tasks_per_stage[s] += restarts;
       } else {
-        lW = std::max(lW, (size_t)restarts * m * r);
-        lH = std::max(lH, (size_t)restarts * r * n);
+        const int l = i % kStreams;
+        lW[l] = std::max(lW[l], (size_t)restarts * m * r);
+        lH[l] = std::max(lH[l], (size_t)restarts * r * n);
         const int g = std::max(1, std::min(restarts, NTT_MAX_RANK / r));
-        lWg = std::max(lWg, (size_t)m * g * r);
+        lWg[l] = std::max(lWg[l], (size_t)m * g * r);
         MuShape shp;
         if (mu_choose_shape(m, n, g * r, 0, sms, &shp) != NTT_OK) {
           delete b;
           return NTT_ERR_UNSUPPORTED;
         }
-        part_max = std::max(part_max, (size_t)shp.grid_cap * shp.part_stride());
-        red_max = std::max(red_max, (size_t)shp.part_stride());
+        part_max[l] = std::max(part_max[l], (size_t)shp.grid_cap * shp.part_stride());
+        red_max[l] = std::max(red_max[l], (size_t)shp.part_stride());
       }
       jobs_per_stage[s] += 1;
     }
@@ -551,19 +595,26 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
   b->off_status = take(64);
   b->off_tickets = take(64);
   b->off_scal = take(8 * sizeof(double));
-  b->off_G = take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
-  b->off_red = take(red_max * 4);
-  b->off_part = take(part_max * 4);
-  b->off_part64 = take(2 * kMaxResidBlocks * sizeof(double));
   b->off_obj = take((size_t)B * restarts * sizeof(double));
-  b->off_rtmp = take(2 * kMaxRestarts * sizeof(double));
   b->off_tasks = take(std::max<size_t>(1, b->max_tasks) * sizeof(SmallTask));
   b->off_jobs = take((b->max_jobs + 1) * sizeof(SelectJob));
   b->off_small = take(small_max * 4);
-  b->off_lW = take(lW * 4);
-  b->off_lH = take(lH * 4);
-  b->off_lWg = take(lWg * 4);
   b->off_x = take(x_total * 4);
+  b->lane.resize(kStreams);
+  for (int l = 0; l < kStreams; ++l) {
+    auto& L = b->lane[l];
+    L.tickets = take(64);
+    L.scal = take(8 * sizeof(double));
+    L.G = take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
+    L.red = take(red_max[l] * 4);
+    L.part = take(part_max[l] * 4);
+    L.part64 = take(2 * kMaxResidBlocks * sizeof(double));
+    L.rtmp = take(2 * kMaxRestarts * sizeof(double));
+    L.lW = take(lW[l] * 4);
+    L.lH = take(lH[l] * 4);
+    L.lWg = take(lWg[l] * 4);
+    L.job = take(sizeof(SelectJob));
+  }
   b->bytes = off;
   *out = b;
   return NTT_OK;

@@ -88,3 +88,16 @@ def test_batched_equals_single_instance_plan_with_one_restart(ntt):
         torch.cuda.synchronize()
         for k, (g, c) in enumerate(zip(views[i], cores)):
             assert _rel(g, c.cpu().numpy()) <= 1e-4 * (k + 1)
+
+
+def test_batched_recipe_subsample_matches_oracle(ntt):
+    """The batched recipe (d 3-6, ranks 2-12 clamped, 8 restarts) on 12 instances
+    with mode sizes 8-11 so that the oracle finishes: final Eq. (3) within 1e-3."""
+    inst = synth.batched_instances(12, seed=41, n_range=(8, 11))
+    instances = [(i["dims"], i["ranks"]) for i in inst]
+    seed, restarts, iters = 5, 8, 40
+    tensors, views = _run(ntt, instances, iters, restarts, seed)
+    for i, ((dims, ranks), T) in enumerate(zip(instances, tensors)):
+        ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
+        eg, eo = oracle.rel_error(T, views[i]), oracle.rel_error(T, ref)
+        assert abs(eg - eo) <= 1e-3, f"instance {i} {dims}: {eg} vs {eo}"
