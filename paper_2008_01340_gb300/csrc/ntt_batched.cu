@@ -12,17 +12,21 @@
 //     stage; one CTA owns one NMF for all of its iterations, X read from HBM
 //     once per task;
 //   * large unfoldings: the restarts run side by side as one NMF of rank
-//     g*r with W^T W and H H^T masked to diagonal r x r blocks (the only
-//     coupling between columns of W), g = floor(32 / r), through the streaming
-//     pass -- one read of X serves g restarts;
+//     g*r with W^T W and H H^T kept on the diagonal r x r blocks (the only
+//     coupling between columns of W), g = floor(32 / r), and every group of
+//     every large instance of the stage advances together in the grouped MU
+//     engine -- one pass launch per shape bucket and one combine launch per
+//     iteration for all of them, one read of X serving g restarts;
+//   * per-restart objectives by one grouped FP64 residual pass;
 //   * select_kernel: best restart, column-L1 hand-off into the core and the
 //     next unfolding, for all instances of the stage at once.
+// The small-unfolding launch runs on a second stream, beside the large work.
 #include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "ntt_internal.cuh"
+#include "group_engine.cuh"
 
 namespace ntt {
 namespace {
@@ -37,7 +41,6 @@ constexpr int kSmallThreads = 256;
 constexpr int kSmallMaxR = 16;
 constexpr size_t kSmallSmemCap = 200 * 1024;
 constexpr int kMaxRestarts = 16;
-constexpr int kStreams = 16;
 
 struct SmallTask {
   const float* X;
@@ -159,32 +162,103 @@ __global__ void __launch_bounds__(kSmallThreads) small_nmf_kernel(const SmallTas
   }
 }
 
-// Initial factors of g side-by-side restarts: W_group (m x g r, restart j in
-// columns j r .. j r + r - 1) and H rows j r .. of H_group, from each restart's stream.
-struct GroupKeys {
-  uint64_t w[kMaxRestarts], h[kMaxRestarts];
+
+// Initial factors of one group of g side-by-side restarts: W_group (m x g r,
+// restart q in columns q r .. q r + r - 1) and H rows q r .. of the group,
+// each restart from its own stream.  One table entry per group.
+struct InitJob {
+  float* W;
+  float* H;
+  int64_t n;
+  int m, r, g, pad;
+  uint64_t kw[kMaxRestarts], kh[kMaxRestarts];
 };
-__global__ void init_group_kernel(float* Wg, float* Hg, int m, int64_t n, int r, int g,
-                                  GroupKeys keys) {
+
+__global__ void init_groups_kernel(const InitJob* jobs) {
+  const InitJob& J = jobs[blockIdx.y];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int re = g * r;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)m * re; e += stride) {
-    const int i = (int)(e / re), q = (int)(e % re), j = q / r, k = q % r;
-    Wg[e] = uniform24(keys.w[j], (uint64_t)(i * r + k));
+  const int re = J.g * J.r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)J.m * re; e += stride) {
+    const int i = (int)(e / re), q = (int)(e % re), j = q / J.r, k = q % J.r;
+    J.W[e] = uniform24(J.kw[j], (uint64_t)(i * J.r + k));
   }
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)re * n; e += stride) {
-    const int j = (int)(e / ((int64_t)r * n));
-    Hg[e] = uniform24(keys.h[j], (uint64_t)(e - (int64_t)j * r * n));
+  const int64_t rn = (int64_t)J.r * J.n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)re * J.n; e += stride) {
+    const int j = (int)(e / rn);
+    J.H[e] = uniform24(J.kh[j], (uint64_t)(e - (int64_t)j * rn));
   }
 }
 
-// W_j (m x r, contiguous) <- columns j r .. of W_group, for all g restarts.
-__global__ void split_group_w_kernel(const float* Wg, float* Wall, int m, int r, int g) {
-  const int re = g * r;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * re; e += gridDim.x * blockDim.x) {
-    const int i = e / re, q = e % re, j = q / r, k = q % r;
-    Wall[(size_t)j * m * r + i * r + k] = Wg[e];
+// W_j (m x r, contiguous) <- columns j r .. of W_group, for the g restarts of a group.
+struct SplitJob {
+  const float* Wg;
+  float* Wall;
+  int m, r, g, pad;
+};
+
+__global__ void split_groups_kernel(const SplitJob* jobs) {
+  const SplitJob J = jobs[blockIdx.y];
+  const int re = J.g * J.r;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J.m * re; e += gridDim.x * blockDim.x) {
+    const int i = e / re, q = e % re, j = q / J.r, k = q % J.r;
+    J.Wall[(size_t)j * J.m * J.r + i * J.r + k] = J.Wg[e];
   }
+}
+
+// 1/2 ||X - W H||_F^2 of one restart: FP32 products, FP64 sums in a fixed
+// order.  Blocks cover kResCols columns each; block partials are summed in
+// block order by resid_reduce_kernel.
+constexpr int kResCols = 2048;
+struct ResJob {
+  const float* X;
+  const float* W;   // m x r
+  const float* H;   // r x n
+  double* out;
+  int64_t n;
+  int m, r, blk0, nblk;
+};
+
+__global__ void __launch_bounds__(256) resid_groups_kernel(const ResJob* __restrict__ jobs,
+                                                           const int* __restrict__ blk_job,
+                                                           double* __restrict__ partial) {
+  extern __shared__ float wsm[];
+  __shared__ double dred[256];
+  const ResJob J = jobs[blk_job[blockIdx.x]];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < J.m * J.r; e += blockDim.x) wsm[e] = J.W[e];
+  __syncthreads();
+  const int64_t c0 = (int64_t)(blockIdx.x - J.blk0) * kResCols;
+  const int64_t c1 = c0 + kResCols < J.n ? c0 + kResCols : J.n;
+  double acc = 0.0;
+  for (int64_t c = c0 + tid; c < c1; c += blockDim.x) {
+    float h[NTT_MAX_RANK];
+#pragma unroll
+    for (int k = 0; k < NTT_MAX_RANK; ++k) h[k] = k < J.r ? J.H[(int64_t)k * J.n + c] : 0.0f;
+    for (int i = 0; i < J.m; ++i) {
+      float v = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NTT_MAX_RANK; ++k)
+        if (k < J.r) v = fmaf(wsm[i * J.r + k], h[k], v);
+      const float d = J.X[(int64_t)i * J.n + c] - v;
+      acc += (double)(d * d);
+    }
+  }
+  dred[tid] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) dred[tid] += dred[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) partial[blockIdx.x] = dred[0];
+}
+
+__global__ void resid_reduce_kernel(const ResJob* jobs, int njobs, const double* partial) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= njobs) return;
+  const ResJob J = jobs[j];
+  double s = 0.0;
+  for (int b = 0; b < J.nblk; ++b) s += partial[J.blk0 + b];
+  *J.out = 0.5 * s;
 }
 
 struct SelectJob {
@@ -198,9 +272,10 @@ struct SelectJob {
   int m, r, restarts, pad;
 };
 
-// grid = (column chunks, jobs): every block picks the same restart, computes
-// the column norms, block x == 0 writes the core, all blocks scale their chunk of H.
-__global__ void select_kernel(const SelectJob* jobs, int njobs) {
+// One select job on the calling block: every block picks the same restart,
+// computes the column norms, block x == 0 writes the core, all blocks scale
+// their chunk of H.
+__global__ void select_kernel(const SelectJob* jobs) {
   __shared__ float snorm[NTT_MAX_RANK];
   __shared__ int sbest;
   const SelectJob jb = jobs[blockIdx.y];
@@ -238,10 +313,15 @@ __global__ void select_kernel(const SelectJob* jobs, int njobs) {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+size_t align64f(size_t x) { return (x + 63) / 64 * 64; }   // floats, 256-byte steps
 int64_t prod64(const std::vector<int64_t>& v, int a, int b) {
   int64_t p = 1;
   for (int i = a; i < b; ++i) p *= v[i];
   return p;
+}
+
+bool is_small(int64_t m, int64_t n, int r) {
+  return r <= kSmallMaxR && n < (1 << 20) && small_smem_bytes((int)m, (int)n, r) <= kSmallSmemCap;
 }
 
 }  // namespace
@@ -258,241 +338,258 @@ struct ntt_batch_s {
     size_t x_off[2];                 // floats into the workspace (next-unfolding ping-pong)
     uint64_t seed;
   };
-  std::vector<Inst> inst;
-  // large stages run on kStreams streams, instance i on stream i % kStreams,
-  // each stream with its own scratch slice
-  struct Lane {
-    size_t G, red, part, part64, tickets, scal, rtmp, lW, lH, lWg, job;
+  // Large unfoldings of one stage: per instance its restart factors, per
+  // group of g restarts one problem of the grouped engine.
+  struct Stage {
+    std::vector<int> large;                       // instances
+    std::vector<size_t> wall_off, hall_off;       // per large instance, bytes
+    std::vector<int> prob_inst, prob_j0, prob_g;  // per problem
+    std::vector<size_t> wg_off;                   // per problem, bytes
+    ntt::GroupPlan gp;
+    int nres = 0, res_blocks = 0, res_smem = 0;
+    size_t off_init, off_split, off_res, off_resmap, off_respart, off_sel;   // bytes, device tables
+    size_t tab_bytes = 0;                          // bytes of those tables (one copy)
+    size_t host_off = 0;                           // pinned host offset of this stage
+    int sel_grid = 1;
+    // small tasks and their select jobs
+    size_t task_base = 0, ntasks = 0, job_base = 0, njobs = 0, small_floats = 0;
+    size_t small_smem = 0;
   };
-  std::vector<Lane> lane;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> ev_join;
-  cudaEvent_t ev_fork = nullptr;
+  std::vector<Inst> inst;
+  std::vector<Stage> stage;
   int iters = 0, restarts = 1;
   float eps = 1e-12f;
   size_t a_total = 0, cores_total = 0;
   // workspace layout (bytes)
-  size_t off_status, off_tickets, off_scal, off_obj, off_tasks, off_jobs, off_small, off_x, bytes;
-  size_t max_tasks = 0, max_jobs = 0;
+  size_t off_status, off_obj, off_tasks, off_jobs, off_small, off_x, off_stage, bytes;
+  size_t n_tasks = 0, n_jobs = 0;
   int max_stages = 0;
-  std::vector<SmallTask> h_tasks;
-  std::vector<SelectJob> h_jobs;
-  cudaStream_t last_stream = nullptr;
-  void* last_ws = nullptr;
+  // pinned host tables: small tasks, small select jobs, per-stage tables
+  char* h_pinned = nullptr;
+  size_t h_bytes = 0, h_tasks_off = 0, h_jobs_off = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tables = nullptr;
+  bool tables_pending = false;
   ~ntt_batch_s() {
-    for (auto st : streams)
-      if (st) cudaStreamDestroy(st);
-    for (auto e : ev_join)
-      if (e) cudaEventDestroy(e);
+    if (ev_tables && tables_pending) cudaEventSynchronize(ev_tables);
+    if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_tables) cudaEventDestroy(ev_tables);
+    if (h_pinned) cudaFreeHost(h_pinned);
     cudaGetLastError();
   }
 };
 
 namespace {
 
-bool is_small(int64_t m, int64_t n, int r) {
-  return r <= kSmallMaxR && n < (1 << 20) && small_smem_bytes((int)m, (int)n, r) <= kSmallSmemCap;
+const float* stage_input(ntt_batch b, int i, int s, const float* A, char* ws) {
+  const auto& I = b->inst[i];
+  return (s == 0) ? A + I.a_off : reinterpret_cast<const float*>(ws + b->off_x) + I.x_off[(s - 1) & 1];
+}
+
+float* stage_next(ntt_batch b, int i, int s, float* cores, char* ws) {
+  const auto& I = b->inst[i];
+  return (s == I.d - 2) ? cores + I.core_off[I.d - 1]
+                        : reinterpret_cast<float*>(ws + b->off_x) + I.x_off[s & 1];
+}
+
+// Host tables of stage s's small tasks and their selection jobs.
+void fill_small_tables(ntt_batch b, int s, const float* A, float* cores, char* ws) {
+  const auto& S = b->stage[s];
+  const int R = b->restarts;
+  double* obj = reinterpret_cast<double*>(ws + b->off_obj);
+  SmallTask* tasks = reinterpret_cast<SmallTask*>(b->h_pinned + b->h_tasks_off);
+  SelectJob* jobs = reinterpret_cast<SelectJob*>(b->h_pinned + b->h_jobs_off);
+  size_t t = S.task_base, jn = S.job_base, off = 0;
+  for (int i = 0; i < (int)b->inst.size(); ++i) {
+    auto& I = b->inst[i];
+    if (s >= I.d - 1) continue;
+    const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
+    const int r = (int)I.ranks[s + 1];
+    if (!is_small(m, n, r)) continue;
+    const float* X = stage_input(b, i, s, A, ws);
+    float* base = reinterpret_cast<float*>(ws + b->off_small) + off;
+    for (int j = 0; j < R; ++j) {
+      SmallTask& tk = tasks[t++];
+      tk.X = X;
+      tk.W = base + (size_t)j * (m * r + r * n);
+      tk.H = tk.W + m * r;
+      tk.obj = obj + (size_t)i * R + j;
+      tk.keyW = stream_key(I.seed, s, j, 0);
+      tk.keyH = stream_key(I.seed, s, j, 1);
+      tk.m = (int)m;
+      tk.n = (int)n;
+      tk.r = r;
+      tk.pad = 0;
+    }
+    SelectJob& jb = jobs[jn++];
+    jb.Wc = base;
+    jb.Hc = base + m * r;
+    jb.w_stride = m * r + r * n;
+    jb.h_stride = m * r + r * n;
+    jb.obj = obj + (size_t)i * R;
+    jb.core = cores + I.core_off[s];
+    jb.next = stage_next(b, i, s, cores, ws);
+    jb.n = n;
+    jb.m = (int)m;
+    jb.r = r;
+    jb.restarts = R;
+    jb.pad = 0;
+    off += (size_t)R * (m * r + r * n);
+  }
+}
+
+// Large unfoldings of stage s: init tables, grouped iterations, split,
+// residuals, selection -- all on stream st.
+ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores, char* ws, cudaStream_t st,
+                               int sms) {
+  auto& S = b->stage[s];
+  if (S.large.empty()) return NTT_OK;
+  const int R = b->restarts;
+  double* obj = reinterpret_cast<double*>(ws + b->off_obj);
+  char* h = b->h_pinned + S.host_off;
+  InitJob* hi = reinterpret_cast<InitJob*>(h + (S.off_init - b->off_stage));
+  SplitJob* hs = reinterpret_cast<SplitJob*>(h + (S.off_split - b->off_stage));
+  ResJob* hr = reinterpret_cast<ResJob*>(h + (S.off_res - b->off_stage));
+  int* hrm = reinterpret_cast<int*>(h + (S.off_resmap - b->off_stage));
+  SelectJob* hsel = reinterpret_cast<SelectJob*>(h + (S.off_sel - b->off_stage));
+  const int np = (int)S.prob_inst.size();
+  std::vector<GroupPtrs> ptrs(np);
+  int rj = 0, rb = 0;
+  for (int li = 0; li < (int)S.large.size(); ++li) {
+    const int i = S.large[li];
+    const auto& I = b->inst[i];
+    const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
+    const int r = (int)I.ranks[s + 1];
+    const float* X = stage_input(b, i, s, A, ws);
+    float* Wall = reinterpret_cast<float*>(ws + S.wall_off[li]);
+    float* Hall = reinterpret_cast<float*>(ws + S.hall_off[li]);
+    for (int j = 0; j < R; ++j, ++rj) {
+      ResJob& J = hr[rj];
+      J.X = X;
+      J.W = Wall + (size_t)j * m * r;
+      J.H = Hall + (size_t)j * r * n;
+      J.out = obj + (size_t)i * R + j;
+      J.n = n;
+      J.m = (int)m;
+      J.r = r;
+      J.nblk = (int)((n + kResCols - 1) / kResCols);
+      J.blk0 = rb;
+      for (int q = 0; q < J.nblk; ++q) hrm[rb + q] = rj;
+      rb += J.nblk;
+    }
+    SelectJob& jb = hsel[li];
+    jb.Wc = Wall;
+    jb.Hc = Hall;
+    jb.w_stride = m * r;
+    jb.h_stride = (int64_t)r * n;
+    jb.obj = obj + (size_t)i * R;
+    jb.core = cores + I.core_off[s];
+    jb.next = stage_next(b, i, s, cores, ws);
+    jb.n = n;
+    jb.m = (int)m;
+    jb.r = r;
+    jb.restarts = R;
+    jb.pad = 0;
+  }
+  for (int p = 0; p < np; ++p) {
+    const int i = S.prob_inst[p], j0 = S.prob_j0[p], g = S.prob_g[p];
+    const int li = (int)(std::find(S.large.begin(), S.large.end(), i) - S.large.begin());
+    const auto& I = b->inst[i];
+    const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
+    const int r = (int)I.ranks[s + 1];
+    float* Wg = reinterpret_cast<float*>(ws + S.wg_off[p]);
+    float* Hg = reinterpret_cast<float*>(ws + S.hall_off[li]) + (size_t)j0 * r * n;
+    InitJob& ij = hi[p];
+    std::memset(&ij, 0, sizeof(ij));
+    ij.W = Wg;
+    ij.H = Hg;
+    ij.n = n;
+    ij.m = (int)m;
+    ij.r = r;
+    ij.g = g;
+    for (int q = 0; q < g; ++q) {
+      ij.kw[q] = stream_key(I.seed, s, j0 + q, 0);
+      ij.kh[q] = stream_key(I.seed, s, j0 + q, 1);
+    }
+    SplitJob& sj = hs[p];
+    sj.Wg = Wg;
+    sj.Wall = reinterpret_cast<float*>(ws + S.wall_off[li]) + (size_t)j0 * m * r;
+    sj.m = (int)m;
+    sj.r = r;
+    sj.g = g;
+    sj.pad = 0;
+    ptrs[p].X = stage_input(b, i, s, A, ws);
+    ptrs[p].H = Hg;
+    ptrs[p].W = Wg;
+  }
+  char* d = ws + b->off_stage;
+  if (cudaMemcpyAsync(d, h, S.tab_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return NTT_ERR_CUDA;
+  const InitJob* di = reinterpret_cast<const InitJob*>(ws + S.off_init);
+  const SplitJob* dsp = reinterpret_cast<const SplitJob*>(ws + S.off_split);
+  const ResJob* dr = reinterpret_cast<const ResJob*>(ws + S.off_res);
+  const int* drm = reinterpret_cast<const int*>(ws + S.off_resmap);
+  double* drp = reinterpret_cast<double*>(ws + S.off_respart);
+  const SelectJob* dsel = reinterpret_cast<const SelectJob*>(ws + S.off_sel);
+  init_groups_kernel<<<dim3(sms, np), 256, 0, st>>>(di);
+  if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
+  NTT_TRY_B(group_run(S.gp, ptrs.data(), ws, h + (S.gp.off_tables - b->off_stage), b->iters, b->eps, st));
+  split_groups_kernel<<<dim3(8, np), 256, 0, st>>>(dsp);
+  resid_groups_kernel<<<S.res_blocks, 256, S.res_smem, st>>>(dr, drm, drp);
+  resid_reduce_kernel<<<(S.nres + 127) / 128, 128, 0, st>>>(dr, S.nres, drp);
+  select_kernel<<<dim3(S.sel_grid, (unsigned)S.large.size()), 256, 0, st>>>(dsel);
+  return cudaGetLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cudaStream_t st) {
   int* status = reinterpret_cast<int*>(ws + b->off_status);
-  unsigned* tickets = reinterpret_cast<unsigned*>(ws + b->off_tickets);
-  double* scal = reinterpret_cast<double*>(ws + b->off_scal);
-  double* obj = reinterpret_cast<double*>(ws + b->off_obj);
-  if (cudaMemsetAsync(status, 0, 64, st) != cudaSuccess || cudaMemsetAsync(tickets, 0, 64, st) != cudaSuccess)
-    return NTT_ERR_CUDA;
-  if (b->streams.empty()) {
-    b->streams.assign(kStreams, nullptr);
-    b->ev_join.assign(kStreams, nullptr);
-    for (int l = 0; l < kStreams; ++l)
-      if (cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&b->ev_join[l], cudaEventDisableTiming) != cudaSuccess)
-        return NTT_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) return NTT_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, 64, st) != cudaSuccess) return NTT_ERR_CUDA;
+  if (!b->side) {
+    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_tables, cudaEventDisableTiming) != cudaSuccess)
+      return NTT_ERR_CUDA;
+    if (cudaFuncSetAttribute(small_nmf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmallSmemCap + 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(resid_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             NTT_MAX_ROWS * NTT_MAX_RANK * 4) != cudaSuccess)
+      return NTT_ERR_CUDA;
   }
-  for (const auto& L : b->lane)
-    if (cudaMemsetAsync(ws + L.tickets, 0, 64, st) != cudaSuccess) return NTT_ERR_CUDA;
-  const int R = b->restarts;
+  // the pinned tables of an earlier call may still be in flight if that call failed early
+  if (b->tables_pending && cudaEventSynchronize(b->ev_tables) != cudaSuccess) return NTT_ERR_CUDA;
+  for (int s = 0; s < b->max_stages; ++s) fill_small_tables(b, s, A, cores, ws);
+  SmallTask* dtasks = reinterpret_cast<SmallTask*>(ws + b->off_tasks);
+  SelectJob* djobs = reinterpret_cast<SelectJob*>(ws + b->off_jobs);
+  if (b->n_tasks && cudaMemcpyAsync(dtasks, b->h_pinned + b->h_tasks_off, b->n_tasks * sizeof(SmallTask),
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return NTT_ERR_CUDA;
+  if (b->n_jobs && cudaMemcpyAsync(djobs, b->h_pinned + b->h_jobs_off, b->n_jobs * sizeof(SelectJob),
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return NTT_ERR_CUDA;
   const int sms = device_sms();
   for (int s = 0; s < b->max_stages; ++s) {
-    // ---- small tasks of this stage
-    b->h_tasks.clear();
-    size_t small_off = 0;
-    std::vector<int> large;
-    for (int i = 0; i < (int)b->inst.size(); ++i) {
-      auto& I = b->inst[i];
-      if (s >= I.d - 1) continue;
-      const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
-      const int r = (int)I.ranks[s + 1];
-      if (!is_small(m, n, r)) {
-        large.push_back(i);
-        continue;
-      }
-      const float* X = (s == 0) ? A + I.a_off
-                                : reinterpret_cast<const float*>(ws + b->off_x) + I.x_off[(s - 1) & 1];
-      for (int j = 0; j < R; ++j) {
-        SmallTask t;
-        t.X = X;
-        t.W = reinterpret_cast<float*>(ws + b->off_small) + small_off;
-        t.H = t.W + m * r;
-        small_off += (size_t)(m * r + r * n);
-        t.obj = obj + (size_t)i * R + j;
-        t.keyW = stream_key(I.seed, s, j, 0);
-        t.keyH = stream_key(I.seed, s, j, 1);
-        t.m = (int)m;
-        t.n = (int)n;
-        t.r = r;
-        t.pad = 0;
-        b->h_tasks.push_back(t);
-      }
-    }
-    if (!b->h_tasks.empty()) {
-      SmallTask* dtasks = reinterpret_cast<SmallTask*>(ws + b->off_tasks);
-      if (cudaMemcpyAsync(dtasks, b->h_tasks.data(), b->h_tasks.size() * sizeof(SmallTask),
-                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+    const auto& S = b->stage[s];
+    // small tasks on the side stream, after everything the caller's stream holds
+    if (S.ntasks) {
+      if (cudaEventRecord(b->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(b->side, b->ev_fork, 0) != cudaSuccess)
         return NTT_ERR_CUDA;
-      size_t smem = 0;
-      for (auto& t : b->h_tasks) smem = std::max(smem, small_smem_bytes(t.m, t.n, t.r));
-      static bool attr = false;
-      if (!attr) {
-        if (cudaFuncSetAttribute(small_nmf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmallSmemCap + 1024) != cudaSuccess)
-          return NTT_ERR_CUDA;
-        attr = true;
-      }
-      int grid = (int)std::min<size_t>(b->h_tasks.size(), (size_t)sms * (smem > 110 * 1024 ? 1 : 2));
-      small_nmf_kernel<<<grid, kSmallThreads, smem, st>>>(dtasks, (int)b->h_tasks.size(), b->iters,
-                                                          b->eps);
+      const int grid = (int)std::min<size_t>(S.ntasks, (size_t)sms * (S.small_smem > 110 * 1024 ? 1 : 2));
+      small_nmf_kernel<<<grid, kSmallThreads, S.small_smem, b->side>>>(dtasks + S.task_base, (int)S.ntasks,
+                                                                        b->iters, b->eps);
+      if (cudaGetLastError() != cudaSuccess || cudaEventRecord(b->ev_join, b->side) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    }
+    NTT_TRY_B(enqueue_large_stage(b, s, A, cores, ws, st, sms));
+    if (S.ntasks) {
+      if (cudaStreamWaitEvent(st, b->ev_join, 0) != cudaSuccess) return NTT_ERR_CUDA;
+      select_kernel<<<dim3(1, (unsigned)S.njobs), 256, 0, st>>>(djobs + S.job_base);
       if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
     }
-    // ---- large tasks: instance i on lane i % kStreams, g restarts side by side
-    if (!large.empty()) {
-      if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return NTT_ERR_CUDA;
-      for (int l = 0; l < kStreams; ++l)
-        if (cudaStreamWaitEvent(b->streams[l], b->ev_fork, 0) != cudaSuccess) return NTT_ERR_CUDA;
-    }
-    for (int i : large) {
-      auto& I = b->inst[i];
-      const int lid = i % kStreams;
-      const auto& L = b->lane[lid];
-      cudaStream_t ls = b->streams[lid];
-      const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
-      const int r = (int)I.ranks[s + 1];
-      const float* X = (s == 0) ? A + I.a_off
-                                : reinterpret_cast<const float*>(ws + b->off_x) + I.x_off[(s - 1) & 1];
-      float* Wall = reinterpret_cast<float*>(ws + L.lW);
-      float* Hall = reinterpret_cast<float*>(ws + L.lH);
-      float* Wg = reinterpret_cast<float*>(ws + L.lWg);
-      unsigned* lt = reinterpret_cast<unsigned*>(ws + L.tickets);
-      double* xn2 = reinterpret_cast<double*>(ws + L.scal);
-      double* part64 = reinterpret_cast<double*>(ws + L.part64);
-      NTT_TRY_B(resid_into(X, 0, nullptr, nullptr, m, n, 0, 0, 1.0, xn2, nullptr, part64, lt + 1, ls));
-      const int g = std::max(1, std::min(R, NTT_MAX_RANK / r));
-      for (int j0 = 0; j0 < R; j0 += g) {
-        const int gj = std::min(g, R - j0);
-        GroupKeys keys;
-        std::memset(&keys, 0, sizeof(keys));
-        for (int q = 0; q < gj; ++q) {
-          keys.w[q] = stream_key(I.seed, s, j0 + q, 0);
-          keys.h[q] = stream_key(I.seed, s, j0 + q, 1);
-        }
-        float* Hg = Hall + (size_t)j0 * r * n;
-        init_group_kernel<<<sms * 2, 256, 0, ls>>>(Wg, Hg, (int)m, n, r, gj, keys);
-        if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-        MuShape shp;
-        NTT_TRY_B(mu_choose_shape(m, n, gj * r, 0, sms, &shp));
-        MuDev dev;
-        dev.X = X;
-        dev.W = Wg;
-        dev.H = Hg;
-        dev.G = reinterpret_cast<float*>(ws + L.G);
-        dev.part = reinterpret_cast<float*>(ws + L.part);
-        dev.red = reinterpret_cast<float*>(ws + L.red);
-        dev.ticket = lt;
-        dev.obj = nullptr;
-        dev.xnorm2 = xn2;
-        dev.status = status;
-        dev.blk = r;
-        if (launch_gram(shp, dev, ls) != cudaSuccess) return NTT_ERR_CUDA;
-        NTT_TRY_B(run_mu_iters(shp, dev, b->eps, b->iters, 0, ls));
-        split_group_w_kernel<<<64, 256, 0, ls>>>(Wg, Wall + (size_t)j0 * m * r, (int)m, r, gj);
-        if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-        double* rtmp = reinterpret_cast<double*>(ws + L.rtmp);
-        for (int q = 0; q < gj; ++q) {
-          NTT_TRY_B(resid_into(X, 0, Wall + (size_t)(j0 + q) * m * r, Hg + (size_t)q * r * n, m, n, r, 1,
-                               0.5, rtmp + 2 * q, nullptr, part64, lt + 1, ls));
-          if (cudaMemcpyAsync(obj + (size_t)i * R + j0 + q, rtmp + 2 * q, sizeof(double),
-                              cudaMemcpyDeviceToDevice, ls) != cudaSuccess)
-            return NTT_ERR_CUDA;
-        }
-      }
-      SelectJob jb;
-      jb.Wc = Wall;
-      jb.Hc = Hall;
-      jb.w_stride = m * r;
-      jb.h_stride = (int64_t)r * n;
-      jb.obj = obj + (size_t)i * R;
-      jb.core = cores + I.core_off[s];
-      jb.next = (s == I.d - 2) ? cores + I.core_off[I.d - 1]
-                               : reinterpret_cast<float*>(ws + b->off_x) + I.x_off[s & 1];
-      jb.n = n;
-      jb.m = (int)m;
-      jb.r = r;
-      jb.restarts = R;
-      jb.pad = 0;
-      SelectJob* dj = reinterpret_cast<SelectJob*>(ws + L.job);
-      if (cudaMemcpyAsync(dj, &jb, sizeof(jb), cudaMemcpyHostToDevice, ls) != cudaSuccess)
-        return NTT_ERR_CUDA;
-      select_kernel<<<dim3(std::max<int64_t>(1, std::min<int64_t>(sms * 4, (r * n + 1023) / 1024)), 1),
-                      256, 0, ls>>>(dj, 1);
-      if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-    }
-    if (!large.empty())
-      for (int l = 0; l < kStreams; ++l) {
-        if (cudaEventRecord(b->ev_join[l], b->streams[l]) != cudaSuccess ||
-            cudaStreamWaitEvent(st, b->ev_join[l], 0) != cudaSuccess)
-          return NTT_ERR_CUDA;
-      }
-    // ---- selection for the small instances of this stage
-    b->h_jobs.clear();
-    {
-      size_t off = 0;
-      for (int i = 0; i < (int)b->inst.size(); ++i) {
-        auto& I = b->inst[i];
-        if (s >= I.d - 1) continue;
-        const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
-        const int r = (int)I.ranks[s + 1];
-        if (!is_small(m, n, r)) continue;
-        SelectJob jb;
-        jb.Wc = reinterpret_cast<float*>(ws + b->off_small) + off;
-        jb.Hc = jb.Wc + m * r;
-        jb.w_stride = m * r + r * n;
-        jb.h_stride = m * r + r * n;
-        off += (size_t)R * (m * r + r * n);
-        jb.obj = obj + (size_t)i * R;
-        jb.core = cores + I.core_off[s];
-        jb.next = (s == I.d - 2) ? cores + I.core_off[I.d - 1]
-                                 : reinterpret_cast<float*>(ws + b->off_x) + I.x_off[s & 1];
-        jb.n = n;
-        jb.m = (int)m;
-        jb.r = r;
-        jb.restarts = R;
-        jb.pad = 0;
-        b->h_jobs.push_back(jb);
-      }
-    }
-    if (!b->h_jobs.empty()) {
-      SelectJob* dj = reinterpret_cast<SelectJob*>(ws + b->off_jobs);
-      if (cudaMemcpyAsync(dj, b->h_jobs.data(), b->h_jobs.size() * sizeof(SelectJob),
-                          cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return NTT_ERR_CUDA;
-      select_kernel<<<dim3(1, (unsigned)b->h_jobs.size()), 256, 0, st>>>(dj, (int)b->h_jobs.size());
-      if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-    }
-    // pageable host-to-device copies are staged before cudaMemcpyAsync returns,
-    // so the host vectors can be rebuilt for the next stage right away
   }
+  if (cudaEventRecord(b->ev_tables, st) != cudaSuccess) return NTT_ERR_CUDA;
+  b->tables_pending = true;
   return NTT_OK;
 }
 
@@ -512,12 +609,6 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
   b->restarts = restarts;
   b->eps = eps_mu;
   size_t dpos = 0, rpos = 0, a_total = 0, c_total = 0, x_total = 0;
-  size_t small_max = 0;
-  std::vector<size_t> lW(kStreams, 1), lH(kStreams, 1), lWg(kStreams, 1), part_max(kStreams, 1),
-      red_max(kStreams, 1);
-  std::vector<size_t> small_per_stage(NTT_MAX_D, 0), tasks_per_stage(NTT_MAX_D, 0),
-      jobs_per_stage(NTT_MAX_D, 0);
-  const int sms = device_sms();
   for (int i = 0; i < B; ++i) {
     ntt_batch_s::Inst I;
     I.d = d[i];
@@ -533,9 +624,14 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
       delete b;
       return NTT_ERR_INVALID_ARG;
     }
+    for (int k = 0; k < I.d; ++k)
+      if (I.dims[k] < 1) {
+        delete b;
+        return NTT_ERR_INVALID_ARG;
+      }
     I.seed = seed + (uint64_t)i;
     I.a_off = a_total;
-    a_total += (size_t)prod64(I.dims, 0, I.d);
+    a_total = align64f(a_total + (size_t)prod64(I.dims, 0, I.d));
     size_t hmax[2] = {0, 0};
     for (int k = 0; k < I.d; ++k) {
       I.core_off.push_back(c_total);
@@ -543,8 +639,8 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
     }
     for (int s = 0; s < I.d - 1; ++s) {
       const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
-      const int r = (int)I.ranks[s + 1];
-      if (I.dims[s] < 1 || r < 1 || r > m || r > n) {
+      const int64_t r = I.ranks[s + 1];
+      if (r < 1 || r > m || r > n) {
         delete b;
         return NTT_ERR_RANK_INFEASIBLE;
       }
@@ -553,39 +649,44 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
         return NTT_ERR_UNSUPPORTED;
       }
       if (s < I.d - 2) hmax[s & 1] = std::max(hmax[s & 1], (size_t)(r * n));
-      if (is_small(m, n, r)) {
-        small_per_stage[s] += (size_t)restarts * (m * r + r * n);
-        tasks_per_stage[s] += restarts;
-      } else {
-        const int l = i % kStreams;
-        lW[l] = std::max(lW[l], (size_t)restarts * m * r);
-        lH[l] = std::max(lH[l], (size_t)restarts * r * n);
-        const int g = std::max(1, std::min(restarts, NTT_MAX_RANK / r));
-        lWg[l] = std::max(lWg[l], (size_t)m * g * r);
-        MuShape shp;
-        if (mu_choose_shape(m, n, g * r, 0, sms, &shp) != NTT_OK) {
-          delete b;
-          return NTT_ERR_UNSUPPORTED;
-        }
-        part_max[l] = std::max(part_max[l], (size_t)shp.grid_cap * shp.part_stride());
-        red_max[l] = std::max(red_max[l], (size_t)shp.part_stride());
-      }
-      jobs_per_stage[s] += 1;
     }
     I.x_off[0] = x_total;
-    x_total += hmax[0] + 1;
+    x_total = align64f(x_total + hmax[0] + 1);
     I.x_off[1] = x_total;
-    x_total += hmax[1] + 1;
+    x_total = align64f(x_total + hmax[1] + 1);
     b->max_stages = std::max(b->max_stages, I.d - 1);
     b->inst.push_back(I);
   }
-  for (int s = 0; s < NTT_MAX_D; ++s) {
-    small_max = std::max(small_max, small_per_stage[s]);
-    b->max_tasks = std::max(b->max_tasks, tasks_per_stage[s]);
-    b->max_jobs = std::max(b->max_jobs, jobs_per_stage[s]);
-  }
   b->a_total = a_total;
   b->cores_total = c_total;
+  const int R = restarts;
+  const int sms = device_sms();
+  // ---- per stage: small tasks, large problems
+  b->stage.resize(b->max_stages);
+  size_t small_max = 0;
+  for (int s = 0; s < b->max_stages; ++s) {
+    auto& S = b->stage[s];
+    S.task_base = b->n_tasks;
+    S.job_base = b->n_jobs;
+    for (int i = 0; i < B; ++i) {
+      const auto& I = b->inst[i];
+      if (s >= I.d - 1) continue;
+      const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d);
+      const int r = (int)I.ranks[s + 1];
+      if (is_small(m, n, r)) {
+        S.ntasks += R;
+        S.njobs += 1;
+        S.small_floats += (size_t)R * (m * r + r * n);
+        S.small_smem = std::max(S.small_smem, small_smem_bytes((int)m, (int)n, r));
+      } else {
+        S.large.push_back(i);
+      }
+    }
+    b->n_tasks += S.ntasks;
+    b->n_jobs += S.njobs;
+    small_max = std::max(small_max, S.small_floats);
+  }
+  // ---- workspace: fixed regions, then the stage region (reused by every stage)
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -593,29 +694,93 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
     return o;
   };
   b->off_status = take(64);
-  b->off_tickets = take(64);
-  b->off_scal = take(8 * sizeof(double));
-  b->off_obj = take((size_t)B * restarts * sizeof(double));
-  b->off_tasks = take(std::max<size_t>(1, b->max_tasks) * sizeof(SmallTask));
-  b->off_jobs = take((b->max_jobs + 1) * sizeof(SelectJob));
+  b->off_obj = take((size_t)B * R * sizeof(double));
+  b->off_tasks = take(std::max<size_t>(1, b->n_tasks) * sizeof(SmallTask));
+  b->off_jobs = take(std::max<size_t>(1, b->n_jobs) * sizeof(SelectJob));
   b->off_small = take(small_max * 4);
   b->off_x = take(x_total * 4);
-  b->lane.resize(kStreams);
-  for (int l = 0; l < kStreams; ++l) {
-    auto& L = b->lane[l];
-    L.tickets = take(64);
-    L.scal = take(8 * sizeof(double));
-    L.G = take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
-    L.red = take(red_max[l] * 4);
-    L.part = take(part_max[l] * 4);
-    L.part64 = take(2 * kMaxResidBlocks * sizeof(double));
-    L.rtmp = take(2 * kMaxRestarts * sizeof(double));
-    L.lW = take(lW[l] * 4);
-    L.lH = take(lH[l] * 4);
-    L.lWg = take(lWg[l] * 4);
-    L.job = take(sizeof(SelectJob));
+  b->off_stage = off;
+  size_t stage_max = 0, host_total = 0;
+  for (int s = 0; s < b->max_stages; ++s) {
+    auto& S = b->stage[s];
+    if (S.large.empty()) continue;
+    // tables first (one host-to-device copy), then factors and engine scratch
+    size_t so = b->off_stage;
+    auto stake = [&](size_t bytes) {
+      const size_t o = so;
+      so = align256(so + (bytes ? bytes : 1));
+      return o;
+    };
+    std::vector<GroupShape> shapes;
+    for (int i : S.large) {
+      const auto& I = b->inst[i];
+      const int r = (int)I.ranks[s + 1];
+      const int g = std::max(1, std::min(R, NTT_MAX_RANK / r));
+      for (int j0 = 0; j0 < R; j0 += g) {
+        const int gj = std::min(g, R - j0);
+        S.prob_inst.push_back(i);
+        S.prob_j0.push_back(j0);
+        S.prob_g.push_back(gj);
+        GroupShape sh;
+        sh.n = prod64(I.dims, s + 1, I.d);
+        sh.m = (int)(I.ranks[s] * I.dims[s]);
+        sh.re = gj * r;
+        sh.blk = r;
+        shapes.push_back(sh);
+      }
+    }
+    const int np = (int)shapes.size();
+    S.nres = (int)S.large.size() * R;
+    int64_t max_rn = 1;
+    S.res_blocks = 0;
+    int res_w = 1;
+    for (int i : S.large) {
+      const auto& I = b->inst[i];
+      const int64_t n = prod64(I.dims, s + 1, I.d);
+      const int64_t m = I.ranks[s] * I.dims[s], r = I.ranks[s + 1];
+      S.res_blocks += R * (int)((n + kResCols - 1) / kResCols);
+      max_rn = std::max(max_rn, r * n);
+      res_w = std::max(res_w, (int)(m * r));
+    }
+    S.res_smem = res_w * 4;
+    S.sel_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, (max_rn + 4095) / 4096));
+    S.off_init = stake((size_t)np * sizeof(InitJob));
+    S.off_split = stake((size_t)np * sizeof(SplitJob));
+    S.off_res = stake((size_t)S.nres * sizeof(ResJob));
+    S.off_resmap = stake((size_t)S.res_blocks * sizeof(int));
+    S.off_sel = stake(S.large.size() * sizeof(SelectJob));
+    S.tab_bytes = so - b->off_stage;
+    // the engine's own tables follow directly, so the host staging stays one block
+    if (group_plan(shapes, sms, so, &S.gp) != NTT_OK) {
+      delete b;
+      return NTT_ERR_UNSUPPORTED;
+    }
+    so = S.gp.bytes;
+    const size_t host_bytes = align256(S.gp.off_tables + S.gp.table_bytes - b->off_stage);
+    S.off_respart = stake((size_t)S.res_blocks * sizeof(double));
+    for (size_t li = 0; li < S.large.size(); ++li) {
+      const auto& I = b->inst[S.large[li]];
+      const int64_t m = I.ranks[s] * I.dims[s], n = prod64(I.dims, s + 1, I.d), r = I.ranks[s + 1];
+      S.wall_off.push_back(stake((size_t)R * m * r * 4));
+      S.hall_off.push_back(stake((size_t)R * r * n * 4));
+    }
+    for (int p = 0; p < np; ++p) S.wg_off.push_back(stake((size_t)shapes[p].m * shapes[p].re * 4));
+    stage_max = std::max(stage_max, so - b->off_stage);
+    S.host_off = host_total;
+    host_total += host_bytes;
   }
-  b->bytes = off;
+  off = b->off_stage + stage_max;
+  b->bytes = align256(off);
+  // ---- pinned host tables
+  b->h_tasks_off = host_total;
+  b->h_jobs_off = align256(b->h_tasks_off + b->n_tasks * sizeof(SmallTask));
+  b->h_bytes = align256(b->h_jobs_off + b->n_jobs * sizeof(SelectJob)) + 256;
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_pinned), b->h_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b->h_pinned = nullptr;
+    delete b;
+    return NTT_ERR_OOM;
+  }
   *out = b;
   return NTT_OK;
 }
@@ -646,14 +811,19 @@ ntt_status ntt_decompose_batched(ntt_batch b, const float* A, float* cores, void
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return NTT_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const ntt_status e = enqueue_batch(b, A, cores, reinterpret_cast<char*>(workspace), st);
-  b->last_stream = st;
-  b->last_ws = workspace;
-  if (e != NTT_OK) return e;
+  if (e != NTT_OK) {
+    // work already queued may still read the pinned tables: let it drain
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    b->tables_pending = false;
+    return e;
+  }
   int status = 0;
   if (cudaMemcpyAsync(&status, reinterpret_cast<char*>(workspace) + b->off_status, sizeof(int),
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return NTT_ERR_CUDA;
+  b->tables_pending = false;
   return status == 0 ? NTT_OK : (ntt_status)status;
 }
 

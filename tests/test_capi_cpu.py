@@ -101,3 +101,19 @@ def test_null_arguments_rejected_without_launch(lib):
     assert lib.nmf_mu_step(8, 8, 2, None, 0, None, None, 1, ctypes.c_float(1e-12), None, None, None) == 1
     assert lib.ntt_plan_workspace_size(None, None) == 1
     assert lib.ntt_uniform_init(1, 0, 0, 2, 10, vp(16), None) == 1   # bad matrix id
+
+
+def test_batch_validation(lib):
+    """Batched form: argument checks run on the host before any device call."""
+    def code(instances, iters=10, restarts=4):
+        with pytest.raises(ntt.NTTError) as e:
+            ntt.ntt_batch_create(instances, iters, restarts)
+        return e.value.code
+    assert code([((8, 8, 8), (1, 9, 3, 1))]) == 2          # r_1 > min(m, n)
+    assert code([((8, 8, 8), (2, 3, 3, 1))]) == 1          # r_0 != 1
+    assert code([((8,), (1, 1))]) == 1                     # d < 2
+    assert code([((64, 64, 64), (1, 33, 33, 1))]) == 6     # rank above the built maximum
+    assert code([((8, 8), (1, 2, 1))], restarts=17) == 1   # more restarts than the built maximum
+    assert code([((8, 8), (1, 2, 1))], iters=0) == 1
+    assert lib.ntt_batch_destroy(None) == 1
+    assert lib.ntt_decompose_batched(None, None, None, None, None) == 1

@@ -65,6 +65,27 @@ def test_batched_per_iterate_matches_oracle(ntt):
             assert np.all(g >= 0)
 
 
+# Unfoldings that reach the grouped engine's edge cases (restarts = 4):
+EDGE = [
+    ((300, 700), (1, 5, 1)),      # 512-row bucket, 4 restarts of rank 5 side by side (20 ranks, blocks of 5)
+    ((37, 3001), (1, 11, 1)),     # odd n: 4-byte copies and ragged last tile; 2 restarts of rank 11
+    ((9, 40001), (1, 1, 1)),      # rank 1: blocks of size 1, 8-rank bucket
+    ((16, 5003), (1, 3, 1)),      # 16-rank bucket, odd n
+    ((64, 4096), (1, 16, 1)),     # blocks of 16 filling the 32-rank bucket
+    ((130, 1000), (1, 32, 1)),    # one restart per pass: dense 32 x 32 Gram, 256-row bucket
+]
+
+
+def test_grouped_engine_edge_shapes_match_oracle(ntt):
+    seed, restarts, iters = 321, 4, 10
+    tensors, views = _run(ntt, EDGE, iters, restarts, seed)
+    for i, ((dims, ranks), T) in enumerate(zip(EDGE, tensors)):
+        ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
+        for k, (g, o) in enumerate(zip(views[i], ref)):
+            assert _rel(g, o) <= 1e-4 * (k + 1), f"instance {i} {dims} core {k}: {_rel(g, o):.2e}"
+            assert np.all(g >= 0)
+
+
 def test_batched_final_error_matches_oracle(ntt):
     seed, restarts, iters = 99, 3, 150
     inst = INSTANCES[:3]
