@@ -42,6 +42,7 @@ extern "C" {
 #define NTT_MAX_D 16      /* maximum tensor order d */
 #define NTT_MAX_RANK 32   /* maximum TT rank r_k */
 #define NTT_MAX_ROWS 512  /* maximum unfolding height r_{k-1} n_k */
+#define NTT_MAX_TALL_ROWS 16384  /* maximum NMF height of the grouped entry points (row blocks of 512) */
 
 typedef enum {
   NTT_OK = 0,
@@ -170,6 +171,26 @@ ntt_status nmf_mu_step_noalloc(int64_t m, int64_t n, int r, const void* X, ntt_d
                                float* W, float* H, int iters, float eps_mu, double* obj_dev,
                                void* stream);
 
+/* Many independent NMFs in one call: problem i is X_i ~ W_i H_i with X_i
+ * m[i] x n[i] FP32 (device, row-major, >= 0), W_i m[i] x r[i] and H_i
+ * r[i] x n[i] FP32 (device, initial factors in, iterates out), and `iters`
+ * multiplicative-update iterations (H first, then W) run on every problem, as
+ * nmf_mu_step does on one.  All problems advance together: per iteration one
+ * pass launch per (height, rank) bucket and one combine launch for all.
+ * Heights above NTT_MAX_ROWS (up to NTT_MAX_TALL_ROWS) run as row blocks of
+ * 512: a W^T X partial per block, a fixed-order sum of the blocks for the H
+ * update, then a second read of X for X H^T (two reads of X per iteration
+ * instead of one).  Every reduction of a problem runs in an order fixed by its
+ * own shape, so a problem's iterates are bitwise the same alone or in any mix.
+ * Host arrays m, n, r, X, W, H of `count` entries; 1 <= r[i] <= NTT_MAX_RANK.
+ * ws: device, nmf_mu_many_workspace_size bytes, 256-byte aligned (overwritten).
+ * The grouped pass computes the H half of Algorithm 3's update with one read
+ * of X per iteration, like nmf_mu_step; the paper has no many-problem form. */
+ntt_status nmf_mu_many_workspace_size(int count, const int64_t* m, const int64_t* n, const int* r,
+                                      size_t* bytes);
+ntt_status nmf_mu_many(int count, const int64_t* m, const int64_t* n, const int* r, const float* const* X,
+                       float* const* W, float* const* H, int iters, float eps_mu, void* ws, void* stream);
+
 /* Device status word left in an nmf_mu_step workspace (sync first). */
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out);
 
@@ -232,6 +253,79 @@ ntt_status ntt_decompose_batched(ntt_batch b, const float* A, float* cores, void
                                  void* stream);
 
 ntt_status ntt_batch_destroy(ntt_batch b);
+
+/* ------------------------------------------------------------------------
+ * Serving form: continuous batching of nTT jobs (Algorithm 2 per job, one
+ * initialisation per stage, fixed iterations per stage).  Jobs wait in FIFO
+ * order; the head is admitted while a job slot is free and its device
+ * footprint (ntt_server_job_footprint) fits the HBM budget, an arena the
+ * server allocates once.  Resident jobs advance together in ticks of
+ * tick_iters multiplicative-update iterations of their current stage through
+ * the grouped engine of nmf_mu_many; at a stage end (stage_iters divisible by
+ * tick_iters) the job takes the column-L1 hand-off, and after its last stage
+ * its cores are copied to the caller's host buffer.  Initial factors of stage
+ * s come from the streams (seed, s, 0, 0/1) of the job's own seed, and every
+ * reduction runs in an order fixed by the job's own shapes: a job's cores are
+ * bitwise the same alone or among any others.  The paper has no serving form.
+ * ------------------------------------------------------------------------ */
+typedef struct ntt_server_s* ntt_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* device arena for jobs (>= 1 MiB); engine tables are extra */
+  int max_jobs;              /* resident job slots */
+  int tick_iters;            /* MU iterations per tick; divides stage_iters */
+  int stage_iters;           /* MU iterations per stage */
+  float eps_mu;
+} ntt_server_config;
+
+#define NTT_JOB_QUEUED 0
+#define NTT_JOB_RUNNING 1
+#define NTT_JOB_DONE 2
+#define NTT_JOB_FAILED 3
+
+typedef struct {
+  int state;                 /* NTT_JOB_* */
+  ntt_status status;         /* NTT_OK, or why the job failed */
+  int stage;                 /* stage in progress (d - 1 when done) */
+  double t_submit, t_admit, t_done;   /* seconds on the server's steady clock; -1 if not yet */
+  size_t footprint_bytes;    /* arena bytes the job holds while resident */
+} ntt_job_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, ticks;
+  int resident, queued;
+  size_t bytes_in_use, peak_bytes, capacity_bytes;
+  double busy_s;             /* engine time spent in ticks */
+} ntt_server_stats;
+
+/* Allocates the arena, starts the engine thread on the current device. */
+ntt_status ntt_server_create(const ntt_server_config* cfg, ntt_server* out);
+
+/* Device bytes a job of this shape holds while resident (input in FP32, plus
+ * its BF16 copy for NTT_BF16 jobs, ping-pong unfoldings, cores, engine scratch). */
+ntt_status ntt_server_job_footprint(int d, const int64_t* dims, const int64_t* ranks, ntt_dtype dtype,
+                                    size_t* bytes);
+
+/* Queue one job.  A_host: host tensor, prod(dims) entries of FP32 or BF16
+ * (C order), read when the job is admitted -- keep it unchanged until the job
+ * is done; pinned memory makes the copy asynchronous.  cores_host: host buffer
+ * of sum_k r_{k-1} n_k r_k floats that receives the cores, core after core.
+ * Returns NTT_ERR_OOM at once when the footprint exceeds the whole budget. */
+ntt_status ntt_server_submit(ntt_server s, int d, const int64_t* dims, const int64_t* ranks, const void* A_host,
+                             ntt_dtype dtype, uint64_t seed, float* cores_host, int64_t* job_id);
+
+/* State of a job (non-blocking). */
+ntt_status ntt_server_poll(ntt_server s, int64_t job_id, ntt_job_info* info);
+
+/* Block until the job is done or failed (timeout_s < 0: no limit; on timeout
+ * NTT_ERR_TIMEOUT and the job stays known).  Returns the job's status and
+ * forgets the job. */
+ntt_status ntt_server_wait(ntt_server s, int64_t job_id, double timeout_s, ntt_job_info* info);
+
+ntt_status ntt_server_get_stats(ntt_server s, ntt_server_stats* out);
+
+/* Stops the engine after its current tick; queued and resident jobs are dropped. */
+ntt_status ntt_server_destroy(ntt_server s);
 
 /* Eq. (4): prod n_i / sum n_i r_{i-1} r_i (host arithmetic). */
 double ntt_compression_ratio(int d, const int64_t* dims, const int64_t* ranks);

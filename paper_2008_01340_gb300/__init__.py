@@ -15,6 +15,8 @@ Entry points mirror include/ntt.h:
 from __future__ import annotations
 
 import ctypes
+
+import numpy as np
 import os
 from dataclasses import dataclass
 
@@ -44,7 +46,9 @@ EXPORTS = (
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
-    "ntt_batch_destroy",
+    "ntt_batch_destroy", "nmf_mu_many_workspace_size", "nmf_mu_many",
+    "ntt_server_create", "ntt_server_job_footprint", "ntt_server_submit", "ntt_server_poll",
+    "ntt_server_wait", "ntt_server_get_stats", "ntt_server_destroy",
 )
 
 
@@ -65,6 +69,27 @@ class _PlanDesc(ctypes.Structure):
         ("refine_iters", ctypes.c_int),
         ("seed", ctypes.c_uint64),
     ]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
+                ("tick_iters", ctypes.c_int), ("stage_iters", ctypes.c_int), ("eps_mu", ctypes.c_float)]
+
+
+class _JobInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("stage", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_size_t)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("ticks", ctypes.c_int64), ("resident", ctypes.c_int), ("queued", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("capacity_bytes", ctypes.c_size_t), ("busy_s", ctypes.c_double)]
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 
 class _Stats(ctypes.Structure):
@@ -322,6 +347,48 @@ def nmf_mu_step_noalloc(X, W, H, iters, eps_mu=1e-12, obj=None, stream=None):
                                      optr, _stream_ptr(stream)), "nmf_mu_step_noalloc")
 
 
+def _many_args(Xs, Ws, Hs):
+    import torch
+    count = len(Xs)
+    if count < 1 or len(Ws) != count or len(Hs) != count:
+        raise ValueError("Xs, Ws, Hs: same non-zero length")
+    m, n, r = [], [], []
+    for X, W, H in zip(Xs, Ws, Hs):
+        if X.dim() != 2 or W.dim() != 2 or H.dim() != 2:
+            raise ValueError("X, W, H must be matrices")
+        if W.shape[0] != X.shape[0] or H.shape != (W.shape[1], X.shape[1]):
+            raise ValueError("shape mismatch")
+        m.append(X.shape[0]); n.append(X.shape[1]); r.append(W.shape[1])
+    return count, _i64arr(m), _i64arr(n), (ctypes.c_int * count)(*r)
+
+
+def nmf_mu_many_workspace_size(shapes):
+    """shapes: list of (m, n, r)."""
+    count = len(shapes)
+    b = ctypes.c_size_t()
+    _check(lib().nmf_mu_many_workspace_size(count, _i64arr([s[0] for s in shapes]),
+                                            _i64arr([s[1] for s in shapes]),
+                                            (ctypes.c_int * count)(*[s[2] for s in shapes]),
+                                            ctypes.byref(b)), "nmf_mu_many_workspace_size")
+    return b.value
+
+
+def nmf_mu_many(Xs, Ws, Hs, iters, eps_mu=1e-12, workspace=None, stream=None):
+    """`iters` MU iterations of every (X_i, W_i, H_i), in place on W_i, H_i (FP32 CUDA tensors)."""
+    import torch
+    count, m, n, r = _many_args(Xs, Ws, Hs)
+    if workspace is None:
+        workspace = empty_workspace(nmf_mu_many_workspace_size(
+            [(X.shape[0], X.shape[1], W.shape[1]) for X, W in zip(Xs, Ws)]), Xs[0].device)
+    vp = ctypes.c_void_p
+    xa = (vp * count)(*[_dev_ptr(X, torch.float32, "X") for X in Xs])
+    wa = (vp * count)(*[_dev_ptr(W, torch.float32, "W") for W in Ws])
+    ha = (vp * count)(*[_dev_ptr(H, torch.float32, "H") for H in Hs])
+    _check(lib().nmf_mu_many(count, m, n, r, xa, wa, ha, int(iters), ctypes.c_float(eps_mu),
+                             _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)), "nmf_mu_many")
+    return workspace
+
+
 def ntt_status_of_workspace(workspace):
     v = ctypes.c_int(0)
     _check(lib().ntt_status_of_workspace(_dev_ptr(workspace, None, "ws"), ctypes.byref(v)),
@@ -427,6 +494,94 @@ def ntt_decompose_batched(batch, A_packed, cores_packed, workspace, stream=None)
                                        _dev_ptr(cores_packed, torch.float32, "cores"),
                                        _dev_ptr(workspace, None, "workspace"), _stream_ptr(stream)),
            "ntt_decompose_batched")
+
+
+def _info_dict(info):
+    return {"state": JOB_STATES.get(info.state, info.state), "status": STATUS.get(info.status, info.status),
+            "stage": info.stage, "t_submit": info.t_submit, "t_admit": info.t_admit, "t_done": info.t_done,
+            "footprint_bytes": info.footprint_bytes}
+
+
+def ntt_server_job_footprint(dims, ranks, x_dtype="f32"):
+    b = ctypes.c_size_t()
+    _check(lib().ntt_server_job_footprint(len(dims), _i64arr(dims), _i64arr(ranks),
+                                          NTT_BF16 if x_dtype == "bf16" else NTT_F32, ctypes.byref(b)),
+           "ntt_server_job_footprint")
+    return b.value
+
+
+class ServerJob:
+    """A submitted job: `cores` (host float32, filled when done) and the input it keeps alive."""
+
+    def __init__(self, job_id, dims, ranks, A, cores):
+        self.id, self.dims, self.ranks, self._A, self.cores = job_id, dims, ranks, A, cores
+
+    def core_views(self):
+        out, off = [], 0
+        for k, n in enumerate(self.dims):
+            size = self.ranks[k] * n * self.ranks[k + 1]
+            out.append(self.cores[off:off + size].view(self.ranks[k], n, self.ranks[k + 1]))
+            off += size
+        return out
+
+
+class Server:
+    """Serving form (include/ntt.h): continuous batching of nTT jobs on the current device."""
+
+    def __init__(self, hbm_budget_bytes, max_jobs=256, tick_iters=10, stage_iters=100, eps_mu=1e-12):
+        cfg = _ServerConfig(int(hbm_budget_bytes), int(max_jobs), int(tick_iters), int(stage_iters),
+                            float(eps_mu))
+        h = ctypes.c_void_p()
+        _check(lib().ntt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
+        self.handle = h
+
+    def submit(self, A, dims, ranks, seed=0, pin_output=True):
+        """A: host torch tensor (float32 or bfloat16, contiguous, prod(dims) entries)."""
+        import torch
+        if A.is_cuda or not A.is_contiguous() or A.numel() != int(np.prod(dims)):
+            raise ValueError("A must be a contiguous host tensor of prod(dims) entries")
+        if A.dtype not in (torch.float32, torch.bfloat16):
+            raise TypeError("A must be float32 or bfloat16")
+        dims = tuple(int(x) for x in dims)
+        ranks = tuple(int(x) for x in ranks)
+        ncore = sum(ranks[k] * n * ranks[k + 1] for k, n in enumerate(dims))
+        cores = torch.zeros(ncore, dtype=torch.float32, pin_memory=pin_output)
+        jid = ctypes.c_int64()
+        _check(lib().ntt_server_submit(self.handle, len(dims), _i64arr(dims), _i64arr(ranks),
+                                       ctypes.c_void_p(A.data_ptr()),
+                                       NTT_BF16 if A.dtype == torch.bfloat16 else NTT_F32,
+                                       ctypes.c_uint64(int(seed)), ctypes.c_void_p(cores.data_ptr()),
+                                       ctypes.byref(jid)), "ntt_server_submit")
+        return ServerJob(jid.value, dims, ranks, A, cores)
+
+    def poll(self, job):
+        info = _JobInfo()
+        _check(lib().ntt_server_poll(self.handle, ctypes.c_int64(job.id), ctypes.byref(info)), "ntt_server_poll")
+        return _info_dict(info)
+
+    def wait(self, job, timeout=-1.0):
+        """Block until `job` is done; returns its info dict (raises NTTError if it failed)."""
+        info = _JobInfo()
+        code = lib().ntt_server_wait(self.handle, ctypes.c_int64(job.id), ctypes.c_double(timeout),
+                                     ctypes.byref(info))
+        _check(code, "ntt_server_wait")
+        return _info_dict(info)
+
+    def stats(self):
+        st = _ServerStats()
+        _check(lib().ntt_server_get_stats(self.handle, ctypes.byref(st)), "ntt_server_get_stats")
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ntt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ntt_compression_ratio(dims, ranks):

@@ -9,19 +9,24 @@
 
 namespace ntt {
 
-// One problem of a grouped pass launch (device table entry).
+// One problem of a grouped pass launch (device table entry).  For a tall
+// unfolding (m > NTT_MAX_ROWS) one entry per row block: X and W point at the
+// block's first row, m is the block's row count.
 struct GProb {
   const float* X;    // m x n, row stride n
   float* H;          // re x n, row stride n, updated in place
   const float* W;    // m x re
   const float* G;    // R x R (bucket R), zero outside the diagonal blocks
-  float* part;       // S x (MP + R) x R partials of [P ; Q]
+  float* part;       // S x E partials of [P ; Q]
+  float* Y;          // tall phase A: re x n partial W^T X of this row block
   int64_t n;
   int m, re, blk;    // rows, ranks, rank block size
   int S;             // CTAs of this problem in its launch
   int cta0;          // first CTA of this problem in its launch
   int aligned;       // X and H rows start on 16 bytes: 16-byte copies
-  int pad[2];
+  int prow0, qrow0;  // partial rows of P (this block's first row) and of Q
+  int E;             // partial stride (floats) = (qrow0 + R) x R
+  int hasq;          // this entry also accumulates Q
 };
 
 // One problem of the grouped combine launch (device table entry).
@@ -38,32 +43,53 @@ struct GComb {
 int group_mp_bucket(int m);     // 16, 32, ..., 512; -1 above NTT_MAX_ROWS
 int group_r_bucket(int re);     // 8, 16, 32; -1 above NTT_MAX_RANK
 int group_tile_cols(int MP, int R);
-cudaError_t launch_gpass(int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
+int group_ctas_per_sm(int MP, int R);   // resident pass CTAs per SM (shared memory bound)
+// mode 0: fused pass; 1: tall phase A (MP = 512 only); 2: tall phase B (MP = 512 only)
+cudaError_t launch_gpass(int mode, int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
                          cudaStream_t st);
-cudaError_t launch_gpass_r8(int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
+int gpass_occupancy_r8(int MP);
+int gpass_occupancy_r16(int MP);
+int gpass_occupancy_r32(int MP);
+cudaError_t launch_gpass_r8(int mode, int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
                             cudaStream_t st);
-cudaError_t launch_gpass_r16(int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
+cudaError_t launch_gpass_r16(int mode, int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
                              cudaStream_t st);
-cudaError_t launch_gpass_r32(int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
+cudaError_t launch_gpass_r32(int mode, int MP, const GProb* probs, const int* cta_prob, int ncta, float eps,
                              cudaStream_t st);
+
+// Tall unfolding: the H update of one problem from its row blocks' partial Y.
+struct GTall {
+  const float* Y;    // nb x re x n partial W^T X, block after block
+  float* H;          // re x n
+  const float* G;    // R x R
+  int64_t n;
+  int re, R, nb, blk0;
+};
 
 // Shapes, buckets and the scratch layout of one grouped run.
 struct GroupPlan {
   struct Prob {
     int64_t n;
-    int m, re, blk;
-    int MP, R, S, cta0, bucket, blk0, nblk;
-    size_t part_off, red_off, g_off;   // bytes into the scratch
-    int aligned_hint;                  // caller promises 16-byte rows (checked again at run time)
+    int m, re, blk, R;
+    int tall, nb, mb;                  // tall: nb row blocks of mb rows (the last one shorter)
+    int qrow0, E, S, blk0, nblk;       // partial layout, CTAs per entry, combine blocks
+    int tblk0, tnblk;                  // tall H-update blocks
+    size_t g_off, red_off, part_off, y_off;   // plan scratch (bytes) when the plan owns it
+  };
+  struct Entry {
+    int p, b, mode, bucket, cta0;
   };
   struct Bucket {
-    int MP, R, ncta, cta_off;
+    int mode, MP, R, ncta, cta_off;
   };
   std::vector<Prob> probs;
+  std::vector<Entry> entries;
   std::vector<Bucket> buckets;
-  int total_cta = 0, total_cblk = 0;
-  size_t off_tables, table_bytes;      // GProb[], GComb[], CTA map, combine-block map
-  size_t off_tickets, bytes;           // scratch bytes in total
+  int total_cta = 0, total_cblk = 0, ntall = 0, total_tblk = 0;
+  bool own_scratch = true;
+  size_t o_prob, o_comb, o_tall, o_cta, o_cblk, o_tblk;   // offsets inside the table block
+  size_t off_tables, table_bytes;      // tables (one host-to-device copy)
+  size_t off_tickets, bytes;           // scratch bytes in total (end offset)
 };
 
 struct GroupShape {
@@ -71,15 +97,26 @@ struct GroupShape {
   int m, re, blk;
 };
 
+// Per-problem device buffers.  G, red, part and Y are the problem's engine
+// scratch when the plan does not own it (group_problem_scratch bytes, in that order).
 struct GroupPtrs {
   const float* X;
   float* H;
   float* W;
+  char* scratch;
 };
 
-// Plan a grouped run of `shapes` (m <= NTT_MAX_ROWS, re <= NTT_MAX_RANK,
-// 1 <= blk <= re); `base` is the scratch offset the plan starts at.
-ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, GroupPlan* out);
+// Plan a grouped run of `shapes` (re <= NTT_MAX_RANK, 1 <= blk <= re; m above
+// NTT_MAX_ROWS runs as row blocks); `base` is the scratch offset the plan
+// starts at.  fixed_split: every problem's CTA count (and so its reduction
+// order) depends on its own shape only, not on the other problems.
+// own_scratch: G, red, part and Y of every problem live in the plan's scratch;
+// otherwise GroupPtrs::scratch supplies them.
+ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, bool fixed_split,
+                      bool own_scratch, GroupPlan* out);
+
+// Engine scratch of one problem under fixed_split (bytes, 256-byte multiple).
+size_t group_problem_scratch(const GroupShape& shape, int sms);
 
 // `iters` MU iterations of every problem of the plan.  W and H hold the
 // initial factors; `host_tables` is pinned host memory of plan.table_bytes

@@ -11,6 +11,7 @@
 // problem (ticket counter, no waiting) updates W and G_W and resets the ticket.
 #include <algorithm>
 #include <cstring>
+#include <tuple>
 
 #include "group_engine.cuh"
 
@@ -31,12 +32,21 @@ int group_r_bucket(int re) {
 
 int group_tile_cols(int MP, int R) { return std::max(16, std::min(4096 / R, 8192 / MP)); }
 
-cudaError_t launch_gpass(int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
+int group_ctas_per_sm(int MP, int R) {
+  switch (R) {
+    case 8: return gpass_occupancy_r8(MP);
+    case 16: return gpass_occupancy_r16(MP);
+    case 32: return gpass_occupancy_r32(MP);
+    default: return 1;
+  }
+}
+
+cudaError_t launch_gpass(int mode, int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
                          cudaStream_t st) {
   switch (R) {
-    case 8: return launch_gpass_r8(MP, probs, cta_prob, ncta, eps, st);
-    case 16: return launch_gpass_r16(MP, probs, cta_prob, ncta, eps, st);
-    case 32: return launch_gpass_r32(MP, probs, cta_prob, ncta, eps, st);
+    case 8: return launch_gpass_r8(mode, MP, probs, cta_prob, ncta, eps, st);
+    case 16: return launch_gpass_r16(mode, MP, probs, cta_prob, ncta, eps, st);
+    case 32: return launch_gpass_r32(mode, MP, probs, cta_prob, ncta, eps, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -128,86 +138,183 @@ __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb*
   if (tid == 0) *c.ticket = 0u;
 }
 
+// Tall unfoldings: H <- max(0, H o Y / (G H + eps)) with Y the fixed-order sum
+// of the row blocks' partials; one thread per column, G (zero outside the
+// diagonal blocks) in shared memory.
+constexpr int kTallCols = 256;
+__global__ void __launch_bounds__(kTallCols) tall_hupd_kernel(const GTall* __restrict__ talls,
+                                                              const int* __restrict__ blk_tall, float eps) {
+  __shared__ float Gs[NTT_MAX_RANK * NTT_MAX_RANK];
+  const GTall t = talls[blk_tall[blockIdx.x]];
+  for (int e = threadIdx.x; e < t.R * t.R; e += blockDim.x) Gs[e] = t.G[e];
+  __syncthreads();
+  const int64_t c = (int64_t)(blockIdx.x - t.blk0) * kTallCols + threadIdx.x;
+  if (c >= t.n) return;
+  float h[NTT_MAX_RANK], y[NTT_MAX_RANK];
+#pragma unroll
+  for (int k = 0; k < NTT_MAX_RANK; ++k) {
+    h[k] = k < t.re ? t.H[(int64_t)k * t.n + c] : 0.0f;
+    y[k] = 0.0f;
+  }
+  for (int b = 0; b < t.nb; ++b) {
+    const float* Yb = t.Y + (int64_t)b * t.re * t.n;
+#pragma unroll
+    for (int k = 0; k < NTT_MAX_RANK; ++k)
+      if (k < t.re) y[k] += Yb[(int64_t)k * t.n + c];
+  }
+#pragma unroll
+  for (int k = 0; k < NTT_MAX_RANK; ++k) {
+    if (k < t.re) {
+      float gh = 0.0f;
+#pragma unroll
+      for (int l = 0; l < NTT_MAX_RANK; ++l)
+        if (l < t.R) gh = fmaf(Gs[k * t.R + l], h[l], gh);
+      t.H[(int64_t)k * t.n + c] = fmaxf(0.0f, __fdividef(h[k] * y[k], gh + eps));
+    }
+  }
+}
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+constexpr int kTallRows = NTT_MAX_ROWS;   // rows per block of a tall unfolding (pass bucket 512)
+
+// CTAs of one problem when its split may not depend on other problems.
+int fixed_ctas(int64_t ntiles, int sms) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>({ntiles, (int64_t)2 * std::max(1, sms), (ntiles + 7) / 8}));
+}
 
 }  // namespace
 
-ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, GroupPlan* out) {
+size_t group_problem_scratch(const GroupShape& sh, int sms) {
+  const int R = group_r_bucket(sh.re);
+  const bool tall = sh.m > kTallRows;
+  const int MP = tall ? kTallRows : group_mp_bucket(sh.m);
+  const int qrow0 = tall ? (sh.m + 15) / 16 * 16 : MP;
+  const size_t E = (size_t)(qrow0 + R) * R;
+  const int T = group_tile_cols(MP, R);
+  const int S = fixed_ctas((sh.n + T - 1) / T, sms);
+  const int nb = tall ? (sh.m + kTallRows - 1) / kTallRows : 0;
+  return align256((size_t)R * R * 4) + align256(E * 4) + align256((size_t)S * E * 4) +
+         align256((size_t)nb * sh.re * sh.n * 4);
+}
+
+ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, bool fixed_split,
+                      bool own_scratch, GroupPlan* out) {
   GroupPlan& pl = *out;
   pl = GroupPlan();
+  pl.own_scratch = own_scratch;
   const int np = (int)shapes.size();
   pl.probs.resize(np);
-  // bucket every problem
-  std::vector<std::pair<int, int>> keys;
-  for (int p = 0; p < np; ++p) {
-    const GroupShape& s = shapes[p];
-    if (s.n < 1 || s.m < 1 || s.re < 1 || s.blk < 1 || s.blk > s.re) return NTT_ERR_INVALID_ARG;
-    const int MP = group_mp_bucket(s.m), R = group_r_bucket(s.re);
-    if (MP < 0 || R < 0) return NTT_ERR_UNSUPPORTED;
-    auto& q = pl.probs[p];
-    q.n = s.n;
-    q.m = s.m;
-    q.re = s.re;
-    q.blk = s.blk;
-    q.MP = MP;
-    q.R = R;
-    const std::pair<int, int> key(MP, R);
+  // buckets are (mode, MP, R); mode 0 entries are whole problems, tall
+  // problems give one mode-1 and one mode-2 entry per row block
+  std::vector<std::tuple<int, int, int>> keys;
+  auto bucket_of = [&](int mode, int MP, int R) {
+    const auto key = std::make_tuple(mode, MP, R);
     auto it = std::find(keys.begin(), keys.end(), key);
-    if (it == keys.end()) {
-      keys.push_back(key);
-      q.bucket = (int)keys.size() - 1;
+    if (it != keys.end()) return (int)(it - keys.begin());
+    keys.push_back(key);
+    return (int)keys.size() - 1;
+  };
+  for (int p = 0; p < np; ++p) {
+    const GroupShape& sh = shapes[p];
+    if (sh.n < 1 || sh.m < 1 || sh.re < 1 || sh.blk < 1 || sh.blk > sh.re) return NTT_ERR_INVALID_ARG;
+    auto& q = pl.probs[p];
+    q.n = sh.n;
+    q.m = sh.m;
+    q.re = sh.re;
+    q.blk = sh.blk;
+    q.R = group_r_bucket(sh.re);
+    if (q.R < 0) return NTT_ERR_UNSUPPORTED;
+    q.tall = sh.m > kTallRows ? 1 : 0;
+    if (q.tall) {
+      q.nb = (sh.m + kTallRows - 1) / kTallRows;
+      q.mb = kTallRows;
+      q.qrow0 = (sh.m + 15) / 16 * 16;
+      for (int b = 0; b < q.nb; ++b) {
+        pl.entries.push_back({p, b, 1, bucket_of(1, kTallRows, q.R), 0});
+        pl.entries.push_back({p, b, 2, bucket_of(2, kTallRows, q.R), 0});
+      }
     } else {
-      q.bucket = (int)(it - keys.begin());
+      q.nb = 1;
+      q.mb = sh.m;
+      q.qrow0 = group_mp_bucket(sh.m);
+      pl.entries.push_back({p, 0, 0, bucket_of(0, q.qrow0, q.R), 0});
     }
+    q.E = (q.qrow0 + q.R) * q.R;
+    const int T = group_tile_cols(q.tall ? kTallRows : q.qrow0, q.R);
+    q.S = (q.tall || fixed_split) ? fixed_ctas((q.n + T - 1) / T, sms) : 0;
   }
-  // CTAs per problem: every bucket launch aims at about two CTAs per SM, each
-  // problem getting CTAs in proportion to its column tiles
-  for (int b = 0; b < (int)keys.size(); ++b) {
+  // split the remaining (fused, not fixed) problems of each mode-0 bucket in
+  // proportion to their column tiles
+  for (int bk = 0; bk < (int)keys.size(); ++bk) {
+    const int mode = std::get<0>(keys[bk]), MP = std::get<1>(keys[bk]), R = std::get<2>(keys[bk]);
+    if (mode != 0) continue;
+    const int T = group_tile_cols(MP, R);
+    std::vector<int> ps;
+    for (const auto& e : pl.entries)
+      if (e.bucket == bk && !pl.probs[e.p].S) ps.push_back(e.p);
+    if (ps.empty()) continue;
+    // per-CTA tile count of a quarter of one wave's share: big problems get
+    // many CTAs, small ones one CTA each, and CTAs that finish early leave
+    // their SM to the rest (the tail is about a quarter of a wave's work)
+    const int64_t wave = (int64_t)std::max(1, sms) * std::max(1, group_ctas_per_sm(MP, R));
+    int64_t tiles = 0;
+    for (int p : ps) tiles += (pl.probs[p].n + T - 1) / T;
+    const int64_t per = std::max<int64_t>(1, (tiles + 4 * wave - 1) / (4 * wave));
+    for (int p : ps) pl.probs[p].S = (int)(((pl.probs[p].n + T - 1) / T + per - 1) / per);
+  }
+  // CTA ranges of the entries inside their bucket launches
+  for (int bk = 0; bk < (int)keys.size(); ++bk) {
     GroupPlan::Bucket B;
-    B.MP = keys[b].first;
-    B.R = keys[b].second;
+    B.mode = std::get<0>(keys[bk]);
+    B.MP = std::get<1>(keys[bk]);
+    B.R = std::get<2>(keys[bk]);
     B.ncta = 0;
     B.cta_off = pl.total_cta;
-    const int T = group_tile_cols(B.MP, B.R);
-    int64_t tiles = 0;
-    for (auto& q : pl.probs)
-      if (q.bucket == b) tiles += (q.n + T - 1) / T;
-    const int64_t target = 2LL * std::max(1, sms);
-    const int64_t per = std::max<int64_t>(1, (tiles + target - 1) / target);
-    for (auto& q : pl.probs) {
-      if (q.bucket != b) continue;
-      const int64_t nt = (q.n + T - 1) / T;
-      q.S = (int)std::min<int64_t>(nt, (nt + per - 1) / per);
-      q.cta0 = B.ncta;
-      B.ncta += q.S;
-    }
+    for (auto& e : pl.entries)
+      if (e.bucket == bk) {
+        e.cta0 = B.ncta;
+        B.ncta += pl.probs[e.p].S;
+      }
     pl.total_cta += B.ncta;
     pl.buckets.push_back(B);
   }
-  // scratch: tables, tickets, then per problem G, red, part
-  size_t off = base;
-  pl.off_tables = off;
-  pl.table_bytes = align256((size_t)np * sizeof(GProb)) + align256((size_t)np * sizeof(GComb)) +
-                   align256((size_t)pl.total_cta * sizeof(int));
   for (auto& q : pl.probs) {
-    const int E = (q.MP + q.R) * q.R;
-    q.nblk = (E + kEntries - 1) / kEntries;
+    q.nblk = (q.E + kEntries - 1) / kEntries;
     q.blk0 = pl.total_cblk;
     pl.total_cblk += q.nblk;
+    if (q.tall) {
+      q.tnblk = (int)((q.n + kTallCols - 1) / kTallCols);
+      q.tblk0 = pl.total_tblk;
+      pl.total_tblk += q.tnblk;
+      ++pl.ntall;
+    }
   }
-  pl.table_bytes += align256((size_t)pl.total_cblk * sizeof(int));
+  // tables: GProb per entry, GComb per problem, GTall per tall problem, block maps
+  const int ne = (int)pl.entries.size();
+  pl.o_prob = 0;
+  pl.o_comb = pl.o_prob + align256((size_t)ne * sizeof(GProb));
+  pl.o_tall = pl.o_comb + align256((size_t)np * sizeof(GComb));
+  pl.o_cta = pl.o_tall + align256((size_t)std::max(1, pl.ntall) * sizeof(GTall));
+  pl.o_cblk = pl.o_cta + align256((size_t)pl.total_cta * sizeof(int));
+  pl.o_tblk = pl.o_cblk + align256((size_t)pl.total_cblk * sizeof(int));
+  pl.table_bytes = pl.o_tblk + align256((size_t)std::max(1, pl.total_tblk) * sizeof(int));
+  size_t off = base;
+  pl.off_tables = off;
   off = align256(off + pl.table_bytes);
   pl.off_tickets = off;
   off = align256(off + (size_t)np * sizeof(unsigned));
-  for (auto& q : pl.probs) {
-    const size_t E = (size_t)(q.MP + q.R) * q.R;
-    q.g_off = off;
-    off = align256(off + (size_t)q.R * q.R * 4);
-    q.red_off = off;
-    off = align256(off + E * 4);
-    q.part_off = off;
-    off = align256(off + (size_t)q.S * E * 4);
-  }
+  if (own_scratch)
+    for (auto& q : pl.probs) {
+      q.g_off = off;
+      off = align256(off + (size_t)q.R * q.R * 4);
+      q.red_off = off;
+      off = align256(off + (size_t)q.E * 4);
+      q.part_off = off;
+      off = align256(off + (size_t)q.S * q.E * 4);
+      q.y_off = off;
+      off = align256(off + (size_t)(q.tall ? q.nb : 0) * q.re * q.n * 4);
+    }
   pl.bytes = off;
   return NTT_OK;
 }
@@ -217,44 +324,74 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
   const int np = (int)pl.probs.size();
   if (np == 0) return NTT_OK;
   char* h = reinterpret_cast<char*>(host_tables);
-  GProb* hp = reinterpret_cast<GProb*>(h);
-  const size_t o_comb = align256((size_t)np * sizeof(GProb));
-  GComb* hc = reinterpret_cast<GComb*>(h + o_comb);
-  const size_t o_cta = o_comb + align256((size_t)np * sizeof(GComb));
-  int* hcta = reinterpret_cast<int*>(h + o_cta);
-  const size_t o_cblk = o_cta + align256((size_t)pl.total_cta * sizeof(int));
-  int* hcblk = reinterpret_cast<int*>(h + o_cblk);
+  GProb* hp = reinterpret_cast<GProb*>(h + pl.o_prob);
+  GComb* hc = reinterpret_cast<GComb*>(h + pl.o_comb);
+  GTall* ht = reinterpret_cast<GTall*>(h + pl.o_tall);
+  int* hcta = reinterpret_cast<int*>(h + pl.o_cta);
+  int* hcblk = reinterpret_cast<int*>(h + pl.o_cblk);
+  int* htblk = reinterpret_cast<int*>(h + pl.o_tblk);
   unsigned* tickets = reinterpret_cast<unsigned*>(scratch + pl.off_tickets);
+  // per-problem scratch pointers
+  std::vector<float*> G(np), red(np), part(np), Y(np);
   for (int p = 0; p < np; ++p) {
     const auto& q = pl.probs[p];
-    const GroupPtrs& g = ptrs[p];
-    GProb& a = hp[p];
+    if (pl.own_scratch) {
+      G[p] = reinterpret_cast<float*>(scratch + q.g_off);
+      red[p] = reinterpret_cast<float*>(scratch + q.red_off);
+      part[p] = reinterpret_cast<float*>(scratch + q.part_off);
+      Y[p] = reinterpret_cast<float*>(scratch + q.y_off);
+    } else {
+      char* s0 = ptrs[p].scratch;
+      G[p] = reinterpret_cast<float*>(s0);
+      s0 += align256((size_t)q.R * q.R * 4);
+      red[p] = reinterpret_cast<float*>(s0);
+      s0 += align256((size_t)q.E * 4);
+      part[p] = reinterpret_cast<float*>(s0);
+      s0 += align256((size_t)q.S * q.E * 4);
+      Y[p] = reinterpret_cast<float*>(s0);
+    }
+  }
+  int ti = 0;
+  for (int e = 0; e < (int)pl.entries.size(); ++e) {
+    const auto& en = pl.entries[e];
+    const auto& q = pl.probs[en.p];
+    const GroupPtrs& g = ptrs[en.p];
+    GProb& a = hp[e];
     std::memset(&a, 0, sizeof(a));
-    a.X = g.X;
+    const int r0 = en.b * q.mb;
+    a.X = g.X + (int64_t)r0 * q.n;
     a.H = g.H;
-    a.W = g.W;
-    a.G = reinterpret_cast<const float*>(scratch + q.g_off);
-    a.part = reinterpret_cast<float*>(scratch + q.part_off);
+    a.W = g.W + (int64_t)r0 * q.re;
+    a.G = G[en.p];
+    a.part = part[en.p];
+    a.Y = Y[en.p] + (int64_t)en.b * q.re * q.n;
     a.n = q.n;
-    a.m = q.m;
+    a.m = q.tall ? std::min(q.mb, q.m - r0) : q.m;
     a.re = q.re;
     a.blk = q.blk;
     a.S = q.S;
-    a.cta0 = q.cta0;
+    a.cta0 = en.cta0;
     a.aligned = (q.n % 4 == 0 && reinterpret_cast<uintptr_t>(g.X) % 16 == 0 &&
-                 reinterpret_cast<uintptr_t>(g.H) % 16 == 0)
+                 reinterpret_cast<uintptr_t>(g.H) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0)
                     ? 1
                     : 0;
-    for (int s = 0; s < q.S; ++s) hcta[pl.buckets[q.bucket].cta_off + q.cta0 + s] = p;
+    a.prow0 = r0;
+    a.qrow0 = q.qrow0;
+    a.E = q.E;
+    a.hasq = (en.mode == 0 || (en.mode == 2 && en.b == 0)) ? 1 : 0;
+    for (int s = 0; s < q.S; ++s) hcta[pl.buckets[en.bucket].cta_off + en.cta0 + s] = e;
+  }
+  for (int p = 0; p < np; ++p) {
+    const auto& q = pl.probs[p];
     GComb& c = hc[p];
     std::memset(&c, 0, sizeof(c));
-    c.part = a.part;
-    c.red = reinterpret_cast<float*>(scratch + q.red_off);
-    c.W = g.W;
-    c.G = reinterpret_cast<float*>(scratch + q.g_off);
+    c.part = part[p];
+    c.red = red[p];
+    c.W = ptrs[p].W;
+    c.G = G[p];
     c.ticket = tickets + p;
     c.S = q.S;
-    c.MP = q.MP;
+    c.MP = q.qrow0;
     c.R = q.R;
     c.m = q.m;
     c.re = q.re;
@@ -262,20 +399,43 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
     c.blk0 = q.blk0;
     c.nblk = q.nblk;
     for (int b = 0; b < q.nblk; ++b) hcblk[q.blk0 + b] = p;
+    if (q.tall) {
+      GTall& t = ht[ti];
+      t.Y = Y[p];
+      t.H = ptrs[p].H;
+      t.G = G[p];
+      t.n = q.n;
+      t.re = q.re;
+      t.R = q.R;
+      t.nb = q.nb;
+      t.blk0 = q.tblk0;
+      for (int b = 0; b < q.tnblk; ++b) htblk[q.tblk0 + b] = ti;
+      ++ti;
+    }
   }
   char* d = scratch + pl.off_tables;
   if (cudaMemcpyAsync(d, h, pl.table_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(tickets, 0, (size_t)np * sizeof(unsigned), st) != cudaSuccess)
     return NTT_ERR_CUDA;
-  const GProb* dp = reinterpret_cast<const GProb*>(d);
-  const GComb* dc = reinterpret_cast<const GComb*>(d + o_comb);
-  const int* dcta = reinterpret_cast<const int*>(d + o_cta);
-  const int* dcblk = reinterpret_cast<const int*>(d + o_cblk);
+  const GProb* dp = reinterpret_cast<const GProb*>(d + pl.o_prob);
+  const GComb* dc = reinterpret_cast<const GComb*>(d + pl.o_comb);
+  const GTall* dt = reinterpret_cast<const GTall*>(d + pl.o_tall);
+  const int* dcta = reinterpret_cast<const int*>(d + pl.o_cta);
+  const int* dcblk = reinterpret_cast<const int*>(d + pl.o_cblk);
+  const int* dtblk = reinterpret_cast<const int*>(d + pl.o_tblk);
   group_gram_kernel<<<np, kAuxThreads, 0, st>>>(dc);
   if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
   for (int t = 0; t < iters; ++t) {
-    for (const auto& B : pl.buckets)
-      if (launch_gpass(B.MP, B.R, dp, dcta + B.cta_off, B.ncta, eps, st) != cudaSuccess) return NTT_ERR_CUDA;
+    for (int mode = 0; mode <= 2; ++mode) {
+      if (mode == 2 && pl.ntall) {
+        tall_hupd_kernel<<<pl.total_tblk, kTallCols, 0, st>>>(dt, dtblk, eps);
+        if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
+      }
+      for (const auto& B : pl.buckets)
+        if (B.mode == mode && B.ncta > 0 &&
+            launch_gpass(B.mode, B.MP, B.R, dp, dcta + B.cta_off, B.ncta, eps, st) != cudaSuccess)
+          return NTT_ERR_CUDA;
+    }
     group_combine_kernel<<<pl.total_cblk, kAuxThreads, 0, st>>>(dc, dcblk, eps);
     if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
   }

@@ -92,7 +92,10 @@ __device__ __forceinline__ float f4c(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-template <class C>
+// MODE 0: the fused pass.  MODE 1 (tall unfoldings, one CTA group per row
+// block): phase A only, the block's partial Y written to P.Y.  MODE 2: phase B
+// only, on the updated H read back from HBM; Q only where P.hasq.
+template <class C, int MODE>
 __global__ void __launch_bounds__(256, 1)
 gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, float eps) {
   constexpr int T = C::T, R = C::R, MP = C::MP, NT = C::NT, LDX = C::LDX, LDH = C::LDH;
@@ -124,6 +127,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
   const int rqe = (re + 3) / 4;   // rank groups in use
   if (tid == 0) {
     int nq = 0;
+    if (MODE != 1 && P.hasq)
     for (int a = 0; a < rqe; ++a)
       for (int b = 0; b < rqe; ++b) {
         const int a0 = 4 * a / blk, a1 = (gmin(4 * a + 4, re) - 1) / blk;
@@ -138,7 +142,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
   auto issue = [&](int stage, int tile) {
     float* dstb = ring + stage * C::STAGE_FLOATS;
     const int64_t col0 = (int64_t)tile * T;
-    const int rows = m + re;
+    const int rows = m + (MODE == 1 ? 0 : re);
     if (P.aligned) {
       for (int e = tid; e < rows * C::CQ; e += NT) {
         const int row = e / C::CQ, ch = e % C::CQ;
@@ -177,8 +181,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
   const int ra = (m + 3) / 4;                 // P row groups (strided rows)
   const int np = ra * rqe;
   const int ntb = np + s_nq;
-  int cg = 1;
-  while (ntb * cg * 2 <= NT && cg * 2 <= C::CQ) cg *= 2;
+  const int cg = gmax(1, gmin(NT / ntb, C::CQ));   // column groups: chunks q, q + cg, ...
   const int qB = tid / ntb;                   // column group (cg > 1), else 0
   constexpr int NACC = C::PAIR ? 2 : 4;
   float2 accp[C::TPB][4][2];
@@ -216,6 +219,16 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
     const int64_t col0 = (int64_t)tile * T;
 
     // ---------------- phase A: Y (and GH in split 0) as 4 x 4 register tiles
+    if constexpr (MODE == 2) {
+      // H already updated in HBM: transpose its tile into H_new^T
+      if (sa == 0)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+          *reinterpret_cast<float4*>(Hnt + (c0 + cc) * LDH + k0) =
+              make_float4(Hs[(k0 + 0) * LDX + c0 + cc], Hs[(k0 + 1) * LDX + c0 + cc],
+                          Hs[(k0 + 2) * LDX + c0 + cc], Hs[(k0 + 3) * LDX + c0 + cc]);
+      __syncthreads();
+    } else {
     float2 ay[4][2], ag[4][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i) ay[i][0] = ay[i][1] = ag[i][0] = ag[i][1] = make_float2(0.f, 0.f);
@@ -232,7 +245,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
         ay[kk][1] = __ffma2_rn(ww, x23, ay[kk][1]);
       }
     }
-    if (sa == 0) {
+    if (MODE == 0 && sa == 0) {
 #pragma unroll 4
       for (int l = glo; l < ghi; ++l) {
         const float4 g = *reinterpret_cast<const float4*>(Gs + l * R + k0);
@@ -265,7 +278,25 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
             ay[kk][1].y += v.w;
           }
     }
-    if (sa == 0) {
+    if (MODE == 1 && sa == 0) {
+      // partial Y of this row block to HBM, ranks < re, columns < n
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + kk;
+        if (k >= re) break;
+        float* dst = P.Y + (int64_t)k * n + col0 + c0;
+        const int64_t left = n - (col0 + c0);
+        const float y[4] = {ay[kk][0].x, ay[kk][0].y, ay[kk][1].x, ay[kk][1].y};
+        if (P.aligned && left >= 4) {
+          *reinterpret_cast<float4*>(dst) = make_float4(y[0], y[1], y[2], y[3]);
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            if (cc < left) dst[cc] = y[cc];
+        }
+      }
+    }
+    if (MODE == 0 && sa == 0) {
       float hn[4][4];
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
@@ -297,9 +328,10 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
       }
     }
     __syncthreads();
+    }
 
     // ---------------- phase B: [P ; Q] += [X ; H_new] H_new^T on 4 x 4 tiles
-    if (qB < cg) {
+    if (MODE != 1 && qB < cg) {
 #pragma unroll
       for (int t = 0; t < C::TPB; ++t) {
         const int j = (cg > 1) ? (tid % ntb) : (tid + t * NT);
@@ -359,6 +391,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
   }
   cp_async_wait<0>();
   __syncthreads();
+  if constexpr (MODE == 1) return;
 
   // ---------------- CTA reduction: [P ; Q] (MS x R) in the ring, column groups in fixed order
   float* F = ring;                  // MS x R
@@ -415,21 +448,44 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
     }
   }
   __syncthreads();
-  float* out = P.part + (size_t)slot * (C::MS * R);
-  for (int e = tid; e < C::MS * R; e += NT) out[e] = F[e];
+  // P rows of this problem (or row block) at rows prow0 + i, Q rows at qrow0 + k
+  float* out = P.part + (size_t)slot * P.E;
+  for (int e = tid; e < C::MS * R; e += NT) {
+    const int row = e / R, k = e % R;
+    if (row < MP) {
+      if (row < m) out[(int64_t)(P.prow0 + row) * R + k] = F[e];
+    } else if (P.hasq) {
+      out[(int64_t)(P.qrow0 + row - MP) * R + k] = F[e];
+    }
+  }
 }
 
+// Resident CTAs per SM of one instantiation (1 when the query fails).
 template <class C>
+int gpass_occupancy_cfg() {
+  if (cudaFuncSetAttribute(gpass_kernel<C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gpass_kernel<C, 0>, C::NT, C::SMEM) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb;
+}
+
+template <class C, int MODE>
 cudaError_t launch_gpass_cfg(const GProb* probs, const int* cta_prob, int ncta, float eps,
                              cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     const cudaError_t e =
-        cudaFuncSetAttribute(gpass_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(gpass_kernel<C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  gpass_kernel<C><<<ncta, C::NT, C::SMEM, st>>>(probs, cta_prob, eps);
+  gpass_kernel<C, MODE><<<ncta, C::NT, C::SMEM, st>>>(probs, cta_prob, eps);
   return cudaGetLastError();
 }
 

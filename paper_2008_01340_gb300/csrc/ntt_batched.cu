@@ -523,6 +523,7 @@ ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores,
     ptrs[p].X = stage_input(b, i, s, A, ws);
     ptrs[p].H = Hg;
     ptrs[p].W = Wg;
+    ptrs[p].scratch = nullptr;
   }
   char* d = ws + b->off_stage;
   if (cudaMemcpyAsync(d, h, S.tab_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return NTT_ERR_CUDA;
@@ -751,7 +752,7 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
     S.off_sel = stake(S.large.size() * sizeof(SelectJob));
     S.tab_bytes = so - b->off_stage;
     // the engine's own tables follow directly, so the host staging stays one block
-    if (group_plan(shapes, sms, so, &S.gp) != NTT_OK) {
+    if (group_plan(shapes, sms, so, false, true, &S.gp) != NTT_OK) {
       delete b;
       return NTT_ERR_UNSUPPORTED;
     }

@@ -117,3 +117,18 @@ def test_batch_validation(lib):
     assert code([((8, 8), (1, 2, 1))], iters=0) == 1
     assert lib.ntt_batch_destroy(None) == 1
     assert lib.ntt_decompose_batched(None, None, None, None, None) == 1
+
+
+def test_many_validation(lib):
+    """nmf_mu_many: argument checks on the host, before any device call."""
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64 * 1
+    i32 = ctypes.c_int * 1
+    b = ctypes.c_size_t()
+    assert lib.nmf_mu_many_workspace_size(0, i64(8), i64(8), i32(2), ctypes.byref(b)) == 1      # count < 1
+    assert lib.nmf_mu_many_workspace_size(1, i64(8), i64(8), i32(33), ctypes.byref(b)) == 6     # rank above 32
+    assert lib.nmf_mu_many_workspace_size(1, i64(16385), i64(8), i32(2), ctypes.byref(b)) == 6  # taller than 16384
+    assert lib.nmf_mu_many_workspace_size(1, i64(0), i64(8), i32(2), ctypes.byref(b)) == 1
+    ptrs = (vp * 1)(None)
+    assert lib.nmf_mu_many(1, i64(8), i64(8), i32(2), ptrs, ptrs, ptrs, 1, ctypes.c_float(1e-12),
+                           vp(256), None) == 1                                                  # null factors
