@@ -294,6 +294,107 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving form: 1000 Poisson requests (d 4-7, 1e4-1e8 entries, ranks 4-32,
+    FP32 or BF16), 100 MU iterations per stage, ticks of 10.  First the
+    closed-loop saturation throughput (all requests submitted at once), then an
+    open loop at 0.8x that rate with p50/p99 latency from submit to result on
+    the host.  Inputs come from pinned host memory; results land in pinned host
+    memory: the timed region is host to host."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2008_01340_gb300 as ntt
+    from paper_2008_01340_gb300 import _build
+
+    _build.build()
+    reqs = synth.serving_requests(args.requests)
+    # host pools the jobs slice their inputs from (U[0,1) values; the data do
+    # not change the work): FP32 and its BF16 rounding, both pinned
+    pool_n = 1 << 28
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    pool_dev = torch.rand(pool_n, device="cuda", generator=g)
+    pool32 = torch.empty(pool_n, dtype=torch.float32, pin_memory=True)
+    pool32.copy_(pool_dev)
+    pool16 = torch.empty(pool_n, dtype=torch.bfloat16, pin_memory=True)
+    pool16.copy_(pool_dev.to(torch.bfloat16))
+    del pool_dev
+    torch.cuda.empty_cache()
+
+    def job_input(i, q):
+        size = int(np.prod(q["dims"]))
+        off = (i * 7919 * 1024) % (pool_n - size) // 64 * 64
+        pool = pool16 if q["x_dtype"] == "bf16" else pool32
+        return pool[off:off + size]
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+    h2d = sum(int(np.prod(q["dims"])) * (2 if q["x_dtype"] == "bf16" else 4) for q in reqs)
+
+    def one_run(arrivals):
+        srv = ntt.Server(budget, max_jobs=args.serve_slots, tick_iters=10, stage_iters=100)
+        handles = [None] * len(reqs)
+        t0 = time.perf_counter()
+        if arrivals is None:
+            for i, q in enumerate(reqs):
+                handles[i] = srv.submit(job_input(i, q), q["dims"], q["ranks"], seed=q["data_seed"])
+        else:
+            def submitter():
+                for i, q in enumerate(reqs):
+                    dt = arrivals[i] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    handles[i] = srv.submit(job_input(i, q), q["dims"], q["ranks"], seed=q["data_seed"])
+            th = threading.Thread(target=submitter)
+            th.start()
+            th.join()
+        infos = [srv.wait(h, timeout=3600) for h in handles]
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+        first = min(i["t_submit"] for i in infos)
+        last = max(i["t_done"] for i in infos)
+        return {"jobs": len(infos), "makespan_s": last - first, "wall_s": wall,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "ticks": stats["ticks"], "peak_gb": stats["peak_bytes"] / 2**30, "busy_s": stats["busy_s"]}
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    closed = one_run(None)
+    x_sat = closed["jobs"] / closed["makespan_s"]
+    base_arr = np.array([q["arrival"] for q in reqs])      # rate-1 Poisson arrival times
+    lam = 0.8 * x_sat
+    opened = one_run(base_arr / lam)
+    sweep = {}
+    if args.serve_sweep:
+        for f in (0.25, 0.5, 0.95):
+            r = one_run(base_arr / (f * x_sat))
+            sweep[str(f)] = {"p50_s": r["p50_s"], "p99_s": r["p99_s"]}
+    clocks = sampler.stop()
+    line = {
+        "metric": METRIC, "value": round(x_sat, 3), "unit": "NTT jobs/s (closed loop, host to host)",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(closed["makespan_s"] * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"c5_serving: {len(reqs)} Poisson requests, d~U{{4..7}}, size~logU[1e4,1e8], "
+                               "r~U{4..32} clamped, FP32/BF16 p=1/2, 100 MU iterations per stage, ticks of 10",
+                   "budget_gb": args.serve_budget_gb, "slots": args.serve_slots},
+        "latency": {"lambda_jobs_s": round(lam, 3), "p50_s": round(opened["p50_s"], 4),
+                    "p99_s": round(opened["p99_s"], 4),
+                    "throughput_jobs_s": round(opened["jobs"] / opened["makespan_s"], 3), "sweep": sweep},
+        "closed_loop": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in closed.items()},
+        "e2e": {"value": round(x_sat, 3), "unit": "NTT jobs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": sum(4 * sum(q["ranks"][k] * n * q["ranks"][k + 1]
+                                                  for k, n in enumerate(q["dims"])) for q in reqs)},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,7 +403,11 @@ def main():
     ap.add_argument("--impl", default="ntt", choices=["ntt", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "c4_batched"],
+    ap.add_argument("--requests", type=int, default=1000, help="c5_serving: number of requests")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-slots", type=int, default=512)
+    ap.add_argument("--serve-sweep", action="store_true", help="c5_serving: also 0.25/0.5/0.95 x saturation")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "c4_batched", "c5_serving"],
                     help="c4_batched: 512 nTT instances (d 3-6, n_k 8-24, r_k 2-12), 8 restarts "
                          "per stage, 300 MU iterations, one batched decomposition per step")
     ap.add_argument("--case", default="full", choices=["full", "stage1_small"],
@@ -316,6 +421,8 @@ def main():
         return run_stage1_small(args)
     if args.workload == "c4_batched":
         return run_batched(args)
+    if args.workload == "c5_serving":
+        return run_serving(args)
 
     import numpy as np
     import torch
