@@ -44,6 +44,7 @@ if ROOT not in sys.path:
 METRIC = "NMF-MU iterations/sec and HBM GB/s (% roofline) per NTT; NTT jobs/sec, p50/p99"
 UNIT = "NTT jobs/s"
 WORKLOAD = "c2_32x6"
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 flop x max SM clock
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture, valid
 # only for the kernel source it was measured on (hash of mu_pass_impl.cuh).
@@ -407,9 +408,11 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=512)
     ap.add_argument("--serve-sweep", action="store_true", help="c5_serving: also 0.25/0.5/0.95 x saturation")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "c4_batched", "c5_serving"],
-                    help="c4_batched: 512 nTT instances (d 3-6, n_k 8-24, r_k 2-12), 8 restarts "
-                         "per stage, 300 MU iterations, one batched decomposition per step")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "c3_16x8", "c4_batched", "c5_serving"],
+                    help="c3_16x8: precision form on 16^8 (BF16 X per stage, 5 FP32 refinement "
+                         "iterations); c4_batched: 512 nTT instances (d 3-6, n_k 8-24, r_k 2-12), 8 "
+                         "restarts per stage, 300 MU iterations, one batched decomposition per step; "
+                         "c5_serving: 1000 Poisson requests through the serving form")
     ap.add_argument("--case", default="full", choices=["full", "stage1_small"],
                     help="stage1_small: MU iterations of the stage-1 shape on 32 x 4194304 "
                          "(512 MB, larger than L2) for profiler captures")
@@ -443,14 +446,16 @@ def main():
     ntt.lib()
     dev = torch.device("cuda", local)
 
-    cfg = synth.CONFIGS[WORKLOAD]
+    wl = args.workload
+    cfg = synth.CONFIGS[wl]
     dims, ranks, iters = cfg["dims"], cfg["ranks"], cfg["iters"]
+    x_dtype, refine = cfg["x_dtype"], cfg.get("refine_iters", 0)
     N = math.prod(dims)
     A_host = torch.empty(N, dtype=torch.float32).pin_memory()
     A_np, info = synth.tt_tensor(dims, ranks, cfg["core_dist"], cfg["noise"], cfg["data_seed"],
                                  out=A_host.numpy())
     Ad = A_host.to(dev, non_blocking=False)
-    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, "f32", 0, cfg["init_seed"])
+    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, cfg["init_seed"])
     ws = ntt.empty_workspace(plan.workspace_size(), dev)
     ws_rel = ntt.empty_workspace(ntt.ntt_reconstruct_workspace_size(dims, ranks), dev)
     cores = [torch.empty(s, dtype=torch.float32, device=dev) for s in plan.core_shapes()]
@@ -516,20 +521,34 @@ def main():
     h2d = N * 4
     d2h = sum(math.prod(s) for s in plan.core_shapes()) * 4 + 3 * 8
 
-    # ---- roofline of the dominant kernel (stage-1 fused pass)
-    st1 = stats["stages"][0]
+    # ---- roofline of the dominant kernel: the fused pass of the stage with the
+    # longest MU loop, against HBM bandwidth, or against the FP32 FMA rate when
+    # its arithmetic (4 m r + 4 r^2 flops per column) binds first
+    peak, peak_src = _peaks()
+    dom = max(range(len(stats["stages"])), key=lambda k: stats["stages"][k]["iter_ms"])
+    st1 = stats["stages"][dom]
     per_iter_s = st1["iter_ms"] / 1e3 / st1["iters"]
     if per_iter_s <= 0:
         raise RuntimeError("stage timing events did not record")
     achieved = st1["alg_bytes"] / per_iter_s / 1e9
-    peak, peak_src = _peaks()
+    flops = 4.0 * st1["n"] * (st1["m"] * st1["r"] + st1["r"] ** 2)
+    tflops = flops / per_iter_s / 1e12
     traffic = None
-    if NCU_TRAFFIC["kernel_sha"] == _kernel_sha():
+    if NCU_TRAFFIC["kernel_sha"] == _kernel_sha() and wl == WORKLOAD:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "mu_pass_kernel<MP=32,R=8,f32> + combine, stage 1 (32 x 33554432, r=8)",
-                "alg_bytes_per_launch": st1["alg_bytes"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    kname = (f"mu_pass_kernel<m={st1['m']},r={st1['r']},{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
+             f"stage {dom + 1} ({st1['m']} x {st1['n']}, r={st1['r']})")
+    if achieved / peak >= tflops / FP32_FMA_TFLOPS:
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
+                    "alg_bytes_per_launch": st1["alg_bytes"],
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roofline = {"bound": "alu", "achieved": round(tflops, 2), "peak": FP32_FMA_TFLOPS, "unit": "TFLOP/s",
+                    "frac": round(tflops / FP32_FMA_TFLOPS, 4), "traffic": traffic, "kernel": kname,
+                    "alg_flops_per_launch": flops,
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                    "hbm": {"achieved": round(achieved, 1), "frac": round(achieved / peak, 4)}}
 
     rel_launches = 0
     # Eq. (3): chain products left and right of the split point, then one residual pass
@@ -551,11 +570,15 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 X, f32 arithmetic" if x_dtype == "bf16" else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD + ": 32^6 FP32 tensor from random U[0,1) TT cores, ranks "
-                   "(1,8,16,16,16,8,1), 1% |Gaussian| noise; 200 MU iterations per unfolding + Eq. (3)",
-                   "global_batch": world, "l2_policy": "inputs larger than L2 (4.3 GB tensor)",
+        "config": {"workload": (WORKLOAD + ": 32^6 FP32 tensor from random U[0,1) TT cores, ranks "
+                                "(1,8,16,16,16,8,1), 1% |Gaussian| noise; 200 MU iterations per unfolding + Eq. (3)")
+                   if wl == WORKLOAD else
+                   (wl + ": 16^8 FP32 tensor from random Exp(1) TT cores, ranks (1,16,32,32,32,32,32,16,1), "
+                    "1% |Gaussian| noise; per unfolding 200 MU iterations on its BF16 copy then 5 on FP32 + Eq. (3)"),
+                   "global_batch": world, "l2_policy": f"inputs larger than L2 ({N * 4 / 1e9:.1f} GB tensor)",
                    "parallelism": f"independent jobs x{world}"},
         "roofline": roofline,
         "e2e": {"value": round(world * 1e3 / e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -17,6 +17,9 @@ of the paper it restates:
   both denominators                                -> mu_update_H, mu_update_W, nmf_mu
 * objective 1/2 ||X - WH||_F^2 (Algorithm 3's objective)   -> objective
 * counter-based SplitMix64 initialisation (the paper only says "rand") -> uniform01
+* precision form (not in the paper, whose experiments are FP32: each unfolding
+  rounded to bfloat16, the MU iterations on it, then refinement iterations on
+  the unrounded unfolding)                          -> bf16_round, ntt_decompose(x_precision=)
 
 Readings where the paper is silent or garbled (the list is repeated in the
 design notes):
@@ -157,19 +160,47 @@ def handoff_normalize(W, H):
 # Algorithm 2 with fixed ranks.
 # --------------------------------------------------------------------------
 
+# --------------------------------------------------------------------------
+# Precision form.
+# --------------------------------------------------------------------------
+
+def bf16_round(x):
+    """Round-to-nearest, ties-to-even of real values to bfloat16 (8 significand
+    bits including the leading one, FP32's exponent range), returned as float64.
+    Defined from the format: with e = floor(log2 |x|) the representable values
+    near x are the multiples of 2^(e-7); x is rounded to the nearest multiple,
+    halfway cases to the even multiple.  Zero stays zero; inputs are finite and
+    inside the normal range."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0.0
+    ax = np.abs(x[nz])
+    e = np.floor(np.log2(ax))
+    # log2 can land one below/above at exact powers of two: correct e so that 2^e <= ax < 2^(e+1)
+    e = np.where(np.exp2(e) > ax, e - 1, e)
+    e = np.where(np.exp2(e + 1) <= ax, e + 1, e)
+    ulp = np.exp2(e - 7)
+    out[nz] = np.sign(x[nz]) * np.rint(ax / ulp) * ulp      # np.rint: halfway to even
+    return out
+
+
 def unfold(T, m):
     """Algorithm 1 on one device: the C-order reshape of T into m x (size/m)."""
     T = np.asarray(T)
     return T.reshape(m, T.size // m)
 
 
-def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True):
+def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, x_precision="f32",
+                  refine=0):
     """Non-negative tensor train of A with given TT ranks (Algorithm 2).
 
     Stage l (0-based s = l-1): X = reshape(current, r_{l-1} n_l, rest); NMF of
     rank r_l by multiplicative updates from the counter-RNG init; W becomes core
     G_l (r_{l-1} x n_l x r_l) after the column-L1 hand-off normalisation and H
     becomes the next `current`.  The last core is the final H.
+    x_precision="bf16": the stage's `iters` iterations run on bf16_round(X),
+    then `refine` more on X itself (the precision form); the objective that
+    picks the restart is on X.
     Returns (cores, traces), traces[s] = objective trace of the kept restart
     (with record=False only the final objective of each stage).
     """
@@ -189,14 +220,19 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True):
             raise ValueError(f"rank r_{s+1}={r} exceeds min(m, n)=min({m},{n})")
         X = unfold(cur, m)
         best = None
+        Xi = bf16_round(X) if x_precision == "bf16" else X
         for rs in range(restarts):
             W0, H0 = init_factors(m, n, r, seed, s, rs)
-            W, H, tr = nmf_mu(X, W0, H0, iters, eps, record=record)
+            W, H, tr = nmf_mu(Xi, W0, H0, iters, eps, record=record)
+            if refine:
+                W, H, tr2 = nmf_mu(X, W, H, refine, eps, record=record)
+                tr = np.concatenate([tr, tr2])
+            final = objective(X, W, H)          # on the unrounded unfolding
             if not record:
-                tr = np.array([objective(X, W, H)])
-            if best is None or tr[-1] < best[2][-1]:
-                best = (W, H, tr)
-        W, H, tr = best
+                tr = np.array([final])
+            if best is None or final < best[3]:
+                best = (W, H, tr, final)
+        W, H, tr, _ = best
         W, H = handoff_normalize(W, H)
         cores.append(W.reshape(ranks[s], dims[s], r))
         traces.append(tr)

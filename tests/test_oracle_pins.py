@@ -290,3 +290,52 @@ def test_synth_instance_generators():
         assert 4 <= len(q["dims"]) <= 7
         for (m, n, r) in synth.stage_shapes(q["dims"], q["ranks"]):
             assert 1 <= r <= min(m, n)
+
+
+# ---------------------------------------------------------------- precision form
+
+def test_bf16_round_fixed_points_and_ties():
+    """Values with 8 significand bits are unchanged; halfway cases go to the even neighbour."""
+    exact = np.array([1.0, 1.5, 1.0 + 2.0 ** -7, 3.0 * 2.0 ** 20, 2.0 ** -30, 255.0, 0.0, -6.5])
+    assert np.array_equal(oracle.bf16_round(exact), exact)
+    one = 1.0
+    # 1 + 2^-8 is halfway between 1 (even) and 1 + 2^-7 (odd last bit) -> 1
+    assert oracle.bf16_round(one + 2.0 ** -8) == 1.0
+    # 1 + 3*2^-8 is halfway between 1 + 2^-7 (odd) and 1 + 2^-6 (even) -> 1 + 2^-6
+    assert oracle.bf16_round(one + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    # just above / below a halfway point
+    assert oracle.bf16_round(one + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert oracle.bf16_round(one + 2.0 ** -8 - 2.0 ** -20) == 1.0
+    # carry into the next binade
+    assert oracle.bf16_round(2.0 - 2.0 ** -9) == 2.0
+    assert oracle.bf16_round(-(1.0 + 2.0 ** -8)) == -1.0
+
+
+def test_bf16_round_matches_library_conversion():
+    """Round-to-nearest-even FP32 -> bfloat16 of the library (torch, CPU) on random FP32 values."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.Generator(np.random.PCG64(17))
+    x = (rng.random(200000) * 10.0 ** rng.integers(-20, 20, 200000)).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(oracle.bf16_round(x.astype(np.float64)), ref)
+
+
+def test_precision_form_reduces_to_fp32_form_on_bf16_exact_input():
+    """With an input already representable in bfloat16 and no refinement, rounding is the
+    identity at stage 1; the stage-1 core equals the FP32 form's."""
+    dims, ranks = (6, 5, 4), (1, 3, 2, 1)
+    A = oracle.bf16_round(synth.uniform_matrix((6, 20), 31)).reshape(dims)
+    c32, _ = oracle.ntt_decompose(A, ranks, 8, seed=3, record=False)
+    cbf, _ = oracle.ntt_decompose(A, ranks, 8, seed=3, record=False, x_precision="bf16")
+    assert np.array_equal(c32[0], cbf[0])
+
+
+def test_precision_form_refinement_lowers_the_fp64_objective():
+    """The refinement iterations are plain MU on the unrounded unfolding, so they cannot
+    raise its objective (MU is monotone): the stage-1 objective with refinement is no
+    higher than without."""
+    dims, ranks = (8, 7, 6), (1, 4, 3, 1)
+    A = synth.uniform_matrix((8, 42), 5).reshape(dims)
+    _, t0 = oracle.ntt_decompose(A, ranks, 20, seed=9, record=False, x_precision="bf16", refine=0)
+    _, t5 = oracle.ntt_decompose(A, ranks, 20, seed=9, record=False, x_precision="bf16", refine=5)
+    assert t5[0][-1] <= t0[0][-1]
