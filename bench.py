@@ -247,7 +247,12 @@ def run_batched(args):
 
     _build.build()
     inst = synth.batched_instances(512)
-    b = ntt.ntt_batch_create([(i["dims"], i["ranks"]) for i in inst], 300, 8, 1e-12, 4)
+    iters = args.batch_iters or 300
+    if args.batch_top:
+        # profiling subset: the largest instances only
+        order = np.argsort([-int(np.prod(i["dims"])) for i in inst], kind="stable")
+        inst = [inst[k] for k in order[:args.batch_top]]
+    b = ntt.ntt_batch_create([(i["dims"], i["ranks"]) for i in inst], iters, 8, 1e-12, 4)
     A = torch.empty(b.input_floats, dtype=torch.float32).pin_memory()
     An = A.numpy()
     for k, it in enumerate(inst):
@@ -285,8 +290,9 @@ def run_batched(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "c4_batched: 512 nTTs, d~U{3..6}, n_k~U{8..24}, r_k~U{2..12} clamped, "
-                   "U[0,1) cores + 1% noise, 8 restarts/stage, 300 MU iterations",
+        "config": {"workload": (f"c4_batched: {len(inst)} nTTs, d~U{{3..6}}, n_k~U{{8..24}}, r_k~U{{2..12}} "
+                                f"clamped, U[0,1) cores + 1% noise, 8 restarts/stage, {iters} MU iterations")
+                   + (" (profiling subset: largest instances)" if args.batch_top else ""),
                    "input_entries": b.input_floats},
         "rel_error": {"median": float(np.median(errs)), "max": float(np.max(errs))},
         "clocks": clocks,
@@ -405,6 +411,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=1000, help="c5_serving: number of requests")
+    ap.add_argument("--batch-iters", type=int, default=0, help="c4_batched: MU iterations (profiling runs)")
+    ap.add_argument("--batch-top", type=int, default=0, help="c4_batched: only the largest K instances")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=512)
     ap.add_argument("--serve-sweep", action="store_true", help="c5_serving: also 0.25/0.5/0.95 x saturation")

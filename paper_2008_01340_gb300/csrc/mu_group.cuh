@@ -62,7 +62,11 @@ struct GCfg {
   static constexpr int YP_FLOATS = (SA - 1) * R * T;
   static constexpr int FIXED_BYTES = 4 * (HNT_FLOATS + W_FLOATS + G_FLOATS + YP_FLOATS) + 4 * RQ * RQ + 256;
   static constexpr int SMEM_CAP = 227 * 1024 - 1024;
-  static constexpr int STAGES = gmin(3, (SMEM_CAP - FIXED_BYTES) / (4 * STAGE_FLOATS));
+  // two CTAs per SM (16 warps) when two ring stages fit in half the SM's shared memory
+  static constexpr int SMEM_CAP2 = 113 * 1024 - 1024;
+  static constexpr bool TWO = FIXED_BYTES + 2 * 4 * STAGE_FLOATS <= SMEM_CAP2;
+  static constexpr int MINB = TWO ? 2 : 1;
+  static constexpr int STAGES = gmin(3, ((TWO ? SMEM_CAP2 : SMEM_CAP) - FIXED_BYTES) / (4 * STAGE_FLOATS));
   static constexpr int SMEM = 4 * STAGES * STAGE_FLOATS + FIXED_BYTES;
   // end-of-CTA reduction scratch, in the stage ring: [P ; Q] (MS x R) + column-group partials
   static constexpr int RED_FLOATS = MS * R + NT * 16;
@@ -96,7 +100,7 @@ __device__ __forceinline__ float f4c(const float4& v, int i) {
 // block): phase A only, the block's partial Y written to P.Y.  MODE 2: phase B
 // only, on the updated H read back from HBM; Q only where P.hasq.
 template <class C, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, C::MINB)
 gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, float eps) {
   constexpr int T = C::T, R = C::R, MP = C::MP, NT = C::NT, LDX = C::LDX, LDH = C::LDH;
   extern __shared__ float4 smem4[];
