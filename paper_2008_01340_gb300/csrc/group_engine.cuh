@@ -13,7 +13,7 @@ namespace ntt {
 // unfolding (m > NTT_MAX_ROWS) one entry per row block: X and W point at the
 // block's first row, m is the block's row count.
 struct GProb {
-  const float* X;    // m x n, row stride n
+  const void* X;     // m x n, row stride n, FP32 (or BF16 in the BF16 buckets)
   float* H;          // re x n, row stride n, updated in place
   const float* W;    // m x re
   const float* G;    // R x R (bucket R), zero outside the diagonal blocks
@@ -36,6 +36,8 @@ struct GComb {
   float* W;            // m x re, updated in place
   float* G;            // R x R, W^T W on the diagonal blocks
   unsigned* ticket;    // zero between launches
+  double* obj;         // objective trace (obj[t] after iteration t) or NULL
+  const double* xnorm2;   // ||X||^2 (FP64) when obj is set
   int S, MP, R, m, re, blk;
   int blk0, nblk;      // combine blocks of this problem
 };
@@ -43,10 +45,15 @@ struct GComb {
 int group_mp_bucket(int m);     // 16, 32, ..., 512; -1 above NTT_MAX_ROWS
 int group_r_bucket(int re);     // 8, 16, 32; -1 above NTT_MAX_RANK
 int group_tile_cols(int MP, int R);
-int group_ctas_per_sm(int MP, int R);   // resident pass CTAs per SM (shared memory bound)
-// mode 0: fused pass; 1: tall phase A (MP = 512 only); 2: tall phase B (MP = 512 only)
-cudaError_t launch_gpass(int mode, int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
-                         cudaStream_t st);
+int group_ctas_per_sm(int MP, int R, bool xb);   // resident pass CTAs per SM
+// mode 0: fused pass; 1: tall phase A (MP = 512 only); 2: tall phase B (MP = 512 only);
+// xb: BF16 X rows (mode 0, MP <= 256, R = 16 or 32)
+cudaError_t launch_gpass(int mode, int MP, int R, bool xb, const GProb* probs, const int* cta_prob, int ncta,
+                         float eps, cudaStream_t st);
+bool gpass_bf16_supported(int MP, int R);
+int gpass_occupancy_bf16(int MP, int R);
+cudaError_t launch_gpass_bf16(int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
+                              cudaStream_t st);
 int gpass_occupancy_r8(int MP);
 int gpass_occupancy_r16(int MP);
 int gpass_occupancy_r32(int MP);
@@ -72,6 +79,7 @@ struct GroupPlan {
     int64_t n;
     int m, re, blk, R;
     int tall, nb, mb;                  // tall: nb row blocks of mb rows (the last one shorter)
+    int xbf16;                         // X in BF16
     int qrow0, E, S, blk0, nblk;       // partial layout, CTAs per entry, combine blocks
     int tblk0, tnblk;                  // tall H-update blocks
     size_t g_off, red_off, part_off, y_off;   // plan scratch (bytes) when the plan owns it
@@ -80,7 +88,7 @@ struct GroupPlan {
     int p, b, mode, bucket, cta0;
   };
   struct Bucket {
-    int mode, MP, R, ncta, cta_off;
+    int mode, MP, R, xb, ncta, cta_off;
   };
   std::vector<Prob> probs;
   std::vector<Entry> entries;
@@ -95,15 +103,18 @@ struct GroupPlan {
 struct GroupShape {
   int64_t n;
   int m, re, blk;
+  int xbf16 = 0;     // X in BF16 (fused buckets up to 256 rows, ranks 9..32; 16-byte aligned rows)
 };
 
 // Per-problem device buffers.  G, red, part and Y are the problem's engine
 // scratch when the plan does not own it (group_problem_scratch bytes, in that order).
 struct GroupPtrs {
-  const float* X;
+  const void* X;
   float* H;
   float* W;
   char* scratch;
+  double* obj = nullptr;          // objective trace of this problem (Gram form, FP64) or NULL
+  const double* xnorm2 = nullptr; // ||X||^2 when obj is set
 };
 
 // Plan a grouped run of `shapes` (re <= NTT_MAX_RANK, 1 <= blk <= re; m above
@@ -122,6 +133,6 @@ size_t group_problem_scratch(const GroupShape& shape, int sms);
 // initial factors; `host_tables` is pinned host memory of plan.table_bytes
 // that must stay untouched until the stream has passed this call's copy.
 ntt_status group_run(const GroupPlan& plan, const GroupPtrs* ptrs, char* scratch, void* host_tables,
-                     int iters, float eps, cudaStream_t st);
+                     int iters, float eps, cudaStream_t st, int t0 = 0);
 
 }  // namespace ntt

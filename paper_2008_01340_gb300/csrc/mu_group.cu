@@ -32,7 +32,8 @@ int group_r_bucket(int re) {
 
 int group_tile_cols(int MP, int R) { return std::max(16, std::min(4096 / R, 8192 / MP)); }
 
-int group_ctas_per_sm(int MP, int R) {
+int group_ctas_per_sm(int MP, int R, bool xb) {
+  if (xb) return gpass_occupancy_bf16(MP, R);
   switch (R) {
     case 8: return gpass_occupancy_r8(MP);
     case 16: return gpass_occupancy_r16(MP);
@@ -41,8 +42,9 @@ int group_ctas_per_sm(int MP, int R) {
   }
 }
 
-cudaError_t launch_gpass(int mode, int MP, int R, const GProb* probs, const int* cta_prob, int ncta, float eps,
-                         cudaStream_t st) {
+cudaError_t launch_gpass(int mode, int MP, int R, bool xb, const GProb* probs, const int* cta_prob, int ncta,
+                         float eps, cudaStream_t st) {
+  if (xb) return mode == 0 ? launch_gpass_bf16(MP, R, probs, cta_prob, ncta, eps, st) : cudaErrorInvalidValue;
   switch (R) {
     case 8: return launch_gpass_r8(mode, MP, probs, cta_prob, ncta, eps, st);
     case 16: return launch_gpass_r16(mode, MP, probs, cta_prob, ncta, eps, st);
@@ -81,8 +83,9 @@ __global__ void __launch_bounds__(kAuxThreads) group_gram_kernel(const GComb* co
 
 __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb* __restrict__ combs,
                                                                     const int* __restrict__ blk_comb,
-                                                                    float eps) {
+                                                                    float eps, int t) {
   __shared__ float chunk[kChunks][kEntries];
+  __shared__ double dsh[kAuxThreads];
   __shared__ int s_last;
   const GComb c = combs[blk_comb[blockIdx.x]];
   const int tid = threadIdx.x;
@@ -135,6 +138,34 @@ __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb*
   }
   __syncthreads();
   group_gram(c.W, m, re, blk, R, c.G);
+  if (c.obj) {
+    // f = 1/2 (||X||^2 - 2 <W, P> + <W^T W, Q>) on the rank blocks, FP64 sums in a fixed order
+    __syncthreads();
+    double a = 0.0, b = 0.0;
+    for (int e = tid; e < m * re; e += blockDim.x) {
+      const int i = e / re, k = e % re;
+      a += (double)__ldcg(&c.W[e]) * (double)__ldcg(&c.red[i * R + k]);
+    }
+    for (int kl = tid; kl < re * re; kl += blockDim.x) {
+      const int k = kl / re, l = kl % re;
+      if (k / blk == l / blk) b += (double)__ldcg(&c.G[k * R + l]) * (double)__ldcg(&c.red[(MP + k) * R + l]);
+    }
+    dsh[tid] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (tid < s) dsh[tid] += dsh[tid + s];
+      __syncthreads();
+    }
+    const double A = dsh[0];
+    __syncthreads();
+    dsh[tid] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (tid < s) dsh[tid] += dsh[tid + s];
+      __syncthreads();
+    }
+    if (tid == 0) c.obj[t] = 0.5 * (*c.xnorm2 - 2.0 * A + dsh[0]);
+  }
   if (tid == 0) *c.ticket = 0u;
 }
 
@@ -207,9 +238,9 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
   pl.probs.resize(np);
   // buckets are (mode, MP, R); mode 0 entries are whole problems, tall
   // problems give one mode-1 and one mode-2 entry per row block
-  std::vector<std::tuple<int, int, int>> keys;
-  auto bucket_of = [&](int mode, int MP, int R) {
-    const auto key = std::make_tuple(mode, MP, R);
+  std::vector<std::tuple<int, int, int, int>> keys;
+  auto bucket_of = [&](int mode, int MP, int R, int xb) {
+    const auto key = std::make_tuple(mode, MP, R, xb);
     auto it = std::find(keys.begin(), keys.end(), key);
     if (it != keys.end()) return (int)(it - keys.begin());
     keys.push_back(key);
@@ -226,19 +257,22 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
     q.R = group_r_bucket(sh.re);
     if (q.R < 0) return NTT_ERR_UNSUPPORTED;
     q.tall = sh.m > kTallRows ? 1 : 0;
+    q.xbf16 = sh.xbf16 ? 1 : 0;
+    if (q.xbf16 && (q.tall || !gpass_bf16_supported(group_mp_bucket(sh.m), q.R) || sh.n % 8 != 0))
+      return NTT_ERR_UNSUPPORTED;
     if (q.tall) {
       q.nb = (sh.m + kTallRows - 1) / kTallRows;
       q.mb = kTallRows;
       q.qrow0 = (sh.m + 15) / 16 * 16;
       for (int b = 0; b < q.nb; ++b) {
-        pl.entries.push_back({p, b, 1, bucket_of(1, kTallRows, q.R), 0});
-        pl.entries.push_back({p, b, 2, bucket_of(2, kTallRows, q.R), 0});
+        pl.entries.push_back({p, b, 1, bucket_of(1, kTallRows, q.R, 0), 0});
+        pl.entries.push_back({p, b, 2, bucket_of(2, kTallRows, q.R, 0), 0});
       }
     } else {
       q.nb = 1;
       q.mb = sh.m;
       q.qrow0 = group_mp_bucket(sh.m);
-      pl.entries.push_back({p, 0, 0, bucket_of(0, q.qrow0, q.R), 0});
+      pl.entries.push_back({p, 0, 0, bucket_of(0, q.qrow0, q.R, q.xbf16), 0});
     }
     q.E = (q.qrow0 + q.R) * q.R;
     const int T = group_tile_cols(q.tall ? kTallRows : q.qrow0, q.R);
@@ -248,6 +282,7 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
   // proportion to their column tiles
   for (int bk = 0; bk < (int)keys.size(); ++bk) {
     const int mode = std::get<0>(keys[bk]), MP = std::get<1>(keys[bk]), R = std::get<2>(keys[bk]);
+    const int xb = std::get<3>(keys[bk]);
     if (mode != 0) continue;
     const int T = group_tile_cols(MP, R);
     std::vector<int> ps;
@@ -257,10 +292,12 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
     // per-CTA tile count of a quarter of one wave's share: big problems get
     // many CTAs, small ones one CTA each, and CTAs that finish early leave
     // their SM to the rest (the tail is about a quarter of a wave's work)
-    const int64_t wave = (int64_t)std::max(1, sms) * std::max(1, group_ctas_per_sm(MP, R));
+    const int64_t wave = (int64_t)std::max(1, sms) * std::max(1, group_ctas_per_sm(MP, R, xb != 0));
     int64_t tiles = 0;
     for (int p : ps) tiles += (pl.probs[p].n + T - 1) / T;
-    const int64_t per = std::max<int64_t>(1, (tiles + 4 * wave - 1) / (4 * wave));
+    // one problem alone: equal CTAs, one whole wave; several: a quarter wave's share each
+    const int64_t per = ps.size() == 1 ? std::max<int64_t>(1, (tiles + wave - 1) / wave)
+                                       : std::max<int64_t>(1, (tiles + 4 * wave - 1) / (4 * wave));
     for (int p : ps) pl.probs[p].S = (int)(((pl.probs[p].n + T - 1) / T + per - 1) / per);
   }
   // CTA ranges of the entries inside their bucket launches
@@ -269,6 +306,7 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
     B.mode = std::get<0>(keys[bk]);
     B.MP = std::get<1>(keys[bk]);
     B.R = std::get<2>(keys[bk]);
+    B.xb = std::get<3>(keys[bk]);
     B.ncta = 0;
     B.cta_off = pl.total_cta;
     for (auto& e : pl.entries)
@@ -320,7 +358,7 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
 }
 
 ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, void* host_tables,
-                     int iters, float eps, cudaStream_t st) {
+                     int iters, float eps, cudaStream_t st, int t0) {
   const int np = (int)pl.probs.size();
   if (np == 0) return NTT_OK;
   char* h = reinterpret_cast<char*>(host_tables);
@@ -359,7 +397,7 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
     GProb& a = hp[e];
     std::memset(&a, 0, sizeof(a));
     const int r0 = en.b * q.mb;
-    a.X = g.X + (int64_t)r0 * q.n;
+    a.X = reinterpret_cast<const char*>(g.X) + (int64_t)r0 * q.n * (q.xbf16 ? 2 : 4);
     a.H = g.H;
     a.W = g.W + (int64_t)r0 * q.re;
     a.G = G[en.p];
@@ -390,6 +428,8 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
     c.W = ptrs[p].W;
     c.G = G[p];
     c.ticket = tickets + p;
+    c.obj = ptrs[p].obj;
+    c.xnorm2 = ptrs[p].xnorm2;
     c.S = q.S;
     c.MP = q.qrow0;
     c.R = q.R;
@@ -433,10 +473,10 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
       }
       for (const auto& B : pl.buckets)
         if (B.mode == mode && B.ncta > 0 &&
-            launch_gpass(B.mode, B.MP, B.R, dp, dcta + B.cta_off, B.ncta, eps, st) != cudaSuccess)
+            launch_gpass(B.mode, B.MP, B.R, B.xb != 0, dp, dcta + B.cta_off, B.ncta, eps, st) != cudaSuccess)
           return NTT_ERR_CUDA;
     }
-    group_combine_kernel<<<pl.total_cblk, kAuxThreads, 0, st>>>(dc, dcblk, eps);
+    group_combine_kernel<<<pl.total_cblk, kAuxThreads, 0, st>>>(dc, dcblk, eps, t0 + t);
     if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
   }
   return NTT_OK;

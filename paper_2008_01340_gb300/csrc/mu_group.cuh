@@ -39,13 +39,16 @@ namespace ntt {
 __host__ __device__ constexpr int gmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int gmax(int a, int b) { return a > b ? a : b; }
 
-template <int MP_, int R_>
+template <int MP_, int R_, bool XB_ = false>
 struct GCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
+  static constexpr bool XB = XB_;                 // X rows in BF16 (H stays FP32)
   static constexpr int NT = 256;
   static constexpr int T = gmax(16, gmin(4096 / R, 8192 / MP));
-  static constexpr int LDX = T + 4;
+  static constexpr int LDX = T + 4;               // H rows (floats)
+  // X rows: T + 4 floats, or T + 8 BF16 values; both a 16-byte pad, in float units
+  static constexpr int XLD = XB ? T / 2 + 4 : T + 4;
   static constexpr int LDH = R + 4;            // H_new^T row stride
   static constexpr int RQ = R / 4;
   static constexpr int CQ = T / 4;
@@ -55,7 +58,7 @@ struct GCfg {
   static constexpr int NTB_MAX = (MP / 4) * RQ + RQ * RQ;
   static constexpr int TPB = (NTB_MAX + NT - 1) / NT;   // phase-B tiles per thread (max)
   static constexpr bool PAIR = TPB <= 2;
-  static constexpr int STAGE_FLOATS = MS * LDX;
+  static constexpr int STAGE_FLOATS = MP * XLD + R * LDX;
   static constexpr int HNT_FLOATS = T * LDH;
   static constexpr int W_FLOATS = MP * R;
   static constexpr int G_FLOATS = R * R;
@@ -68,14 +71,15 @@ struct GCfg {
   static constexpr int MINB = TWO ? 2 : 1;
   static constexpr int STAGES = gmin(3, ((TWO ? SMEM_CAP2 : SMEM_CAP) - FIXED_BYTES) / (4 * STAGE_FLOATS));
   static constexpr int SMEM = 4 * STAGES * STAGE_FLOATS + FIXED_BYTES;
-  // end-of-CTA reduction scratch, in the stage ring: [P ; Q] (MS x R) + column-group partials
+  // end-of-CTA reduction scratch, from the ring on: [P ; Q] (MS x R) + column-group partials
   static constexpr int RED_FLOATS = MS * R + NT * 16;
 
-  static_assert(R % 8 == 0 && R <= 32 && MP % 16 == 0, "bucket");
+  static_assert(R % 8 == 0 && R <= 32 && MP % 16 == 0 && T % 8 == 0, "bucket");
   static_assert(NA <= NT && NT % NA == 0 && MP % SA == 0, "phase A mapping");
   static_assert(STAGES >= 2, "pipeline depth");
   static_assert(SMEM <= SMEM_CAP, "shared memory");
-  static_assert(RED_FLOATS <= STAGES * STAGE_FLOATS, "reduction scratch");
+  // the scratch may run into the H_new buffer, which follows the ring and is free by then
+  static_assert(RED_FLOATS <= STAGES * STAGE_FLOATS + HNT_FLOATS, "reduction scratch");
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
@@ -94,6 +98,20 @@ __device__ __forceinline__ void cp_async_wait() {
 
 __device__ __forceinline__ float f4c(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Four consecutive X values of row `row` from column c (c % 4 == 0) of a ring
+// stage: FP32 rows of XLD floats, or BF16 rows of 2 XLD values widened exactly.
+template <class C>
+__device__ __forceinline__ float4 ldx4(const float* Xs, int row, int c) {
+  if constexpr (C::XB) {
+    const uint2 u = *reinterpret_cast<const uint2*>(reinterpret_cast<const char*>(Xs) +
+                                                    (size_t)row * C::XLD * 4 + (size_t)c * 2);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+  } else {
+    return *reinterpret_cast<const float4*>(Xs + row * C::XLD + c);
+  }
 }
 
 // MODE 0: the fused pass.  MODE 1 (tall unfoldings, one CTA group per row
@@ -147,13 +165,34 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
     float* dstb = ring + stage * C::STAGE_FLOATS;
     const int64_t col0 = (int64_t)tile * T;
     const int rows = m + (MODE == 1 ? 0 : re);
-    if (P.aligned) {
+    if constexpr (C::XB) {
+      // BF16 X rows (8 values per 16-byte copy; rows 16-byte aligned, checked on the host)
+      constexpr int CQB = T / 8;
+      for (int e = tid; e < m * CQB; e += NT) {
+        const int row = e / CQB, ch = e % CQB;
+        const int64_t col = col0 + 8 * ch;
+        const int64_t left = n - col;
+        const int bytes = left >= 8 ? 16 : (left > 0 ? (int)left * 2 : 0);
+        const char* src = reinterpret_cast<const char*>(P.X) + ((int64_t)row * n + (bytes ? col : 0)) * 2;
+        cp_async16(smem_u32(reinterpret_cast<char*>(dstb) + (size_t)row * C::XLD * 4 + 16 * ch), src, bytes);
+      }
+      if constexpr (MODE != 1)
+        for (int e = tid; e < re * C::CQ; e += NT) {
+          const int k = e / C::CQ, ch = e % C::CQ;
+          const int64_t col = col0 + 4 * ch;
+          const int64_t left = n - col;
+          const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+          const float* src = P.H + (int64_t)k * n;
+          cp_async16(smem_u32(dstb + MP * C::XLD + k * LDX + 4 * ch), bytes ? src + col : src, bytes);
+        }
+    } else if (P.aligned) {
       for (int e = tid; e < rows * C::CQ; e += NT) {
         const int row = e / C::CQ, ch = e % C::CQ;
         const int64_t col = col0 + 4 * ch;
         const int64_t left = n - col;
         const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
-        const float* src = row < m ? P.X + (int64_t)row * n : P.H + (int64_t)(row - m) * n;
+        const float* src = row < m ? reinterpret_cast<const float*>(P.X) + (int64_t)row * n
+                                   : P.H + (int64_t)(row - m) * n;
         const int srow = row < m ? row : MP + row - m;
         cp_async16(smem_u32(dstb + srow * LDX + 4 * ch), bytes ? src + col : src, bytes);
       }
@@ -162,7 +201,8 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
         const int row = e / T, c = e % T;
         const int64_t col = col0 + c;
         const int bytes = col < n ? 4 : 0;
-        const float* src = row < m ? P.X + (int64_t)row * n : P.H + (int64_t)(row - m) * n;
+        const float* src = row < m ? reinterpret_cast<const float*>(P.X) + (int64_t)row * n
+                                   : P.H + (int64_t)(row - m) * n;
         const int srow = row < m ? row : MP + row - m;
         cp_async4(smem_u32(dstb + srow * LDX + c), bytes ? src + col : src, bytes);
       }
@@ -219,7 +259,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
     cp_async_wait<C::STAGES - 1>();
     __syncthreads();
     const float* Xs = ring + (it % C::STAGES) * C::STAGE_FLOATS;
-    const float* Hs = Xs + MP * LDX;
+    const float* Hs = Xs + MP * C::XLD;
     const int64_t col0 = (int64_t)tile * T;
 
     // ---------------- phase A: Y (and GH in split 0) as 4 x 4 register tiles
@@ -239,7 +279,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
 #pragma unroll 4
     for (int i = ia0; i < ia1; ++i) {
       const float4 w = *reinterpret_cast<const float4*>(Ws + i * R + k0);
-      const float4 x = *reinterpret_cast<const float4*>(Xs + i * LDX + c0);
+      const float4 x = ldx4<C>(Xs, i, c0);
       const float2 x01 = make_float2(x.x, x.y), x23 = make_float2(x.z, x.w);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
@@ -359,7 +399,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
           if (isP) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              const float4 x = *reinterpret_cast<const float4*>(Xs + (a + i * ra) * LDX + c);
+              const float4 x = ldx4<C>(Xs, a + i * ra, c);
               av[i][0] = x.x;
               av[i][1] = x.y;
               av[i][2] = x.z;

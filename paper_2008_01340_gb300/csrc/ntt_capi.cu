@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "ntt_internal.cuh"
+#include "group_engine.cuh"
 
 #define NTT_CUDA_TRY_NS(expr)                      \
   do {                                             \
@@ -217,10 +217,19 @@ struct ntt_plan_s {
   int refine = 0;
   uint64_t seed = 0;
 
+  // A stage's MU loop runs either on the single-problem pass (TMA, phase
+  // split) or on the grouped engine with this one problem, whichever measured
+  // faster for its shape (plan_route_group).
+  struct Route {
+    bool on = false;
+    ntt::GroupPlan gp;
+    size_t host_off = 0;   // pinned host tables of this route
+  };
   struct Stage {
     int64_t m, n;
     int r;
     MuShape f32, bf16;
+    Route gf32, gbf16;
     int iters_total;
     size_t obj_off;  // index into the objective array
     double alg_bytes;
@@ -241,6 +250,9 @@ struct ntt_plan_s {
   std::vector<cudaEvent_t> ev;   // 4 per stage + 2 total
   int64_t launches = 0;          // kernels per decomposition
   size_t off_chain = 0, off_err = 0;
+  size_t off_grp = 0;            // grouped-engine scratch shared by the routed stages
+  char* h_tables = nullptr;      // pinned host tables of the routed stages
+  size_t h_bytes = 0;
   cudaStream_t last_stream = nullptr;
   void* last_ws = nullptr;
   bool ran = false;
@@ -250,11 +262,26 @@ struct ntt_plan_s {
     if (cap) cudaStreamDestroy(cap);
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
+    if (h_tables) cudaFreeHost(h_tables);
     cudaGetLastError();
   }
 };
 
 namespace {
+
+// Which MU loop a stage runs: the grouped engine when its height bucket is at
+// most 256 rows and its rank bucket at least 16 (where it measured faster than
+// the single-problem pass on GB300), else the pass.  NTT_PLAN_ENGINE=pass or
+// =group forces one of them where both apply.
+bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16) {
+  const int MP = group_mp_bucket((int)m), R = group_r_bucket(r);
+  if (MP < 0 || R < 0) return false;
+  if (xbf16 && (!gpass_bf16_supported(MP, R) || n % 8 != 0)) return false;
+  const char* e = std::getenv("NTT_PLAN_ENGINE");
+  if (e && std::strcmp(e, "pass") == 0) return false;
+  if (e && std::strcmp(e, "group") == 0) return true;
+  return MP <= 256 && R >= 16;
+}
 
 // Record the whole decomposition on stream `st` (captured or eager).
 ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, char* ws,
@@ -297,19 +324,33 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
     dev.status = status;
     NTT_CUDA_TRY(launch_gram(S.f32, dev, st));
     launches += 4;
+    auto mu = [&](const ntt_plan_s::Route& rt, const MuShape& shp, const void* Xv, int iters,
+                  int t0) -> ntt_status {
+      if (iters <= 0) return NTT_OK;
+      if (!rt.on) {
+        dev.X = Xv;
+        return run_mu_iters(shp, dev, p->eps, iters, t0, st);
+      }
+      GroupPtrs g;
+      g.X = Xv;
+      g.H = H;
+      g.W = W;
+      g.scratch = nullptr;
+      g.obj = obj + S.obj_off;
+      g.xnorm2 = xnorm2;
+      launches += 1;   // the engine's own Gram launch
+      return group_run(rt.gp, &g, ws, p->h_tables + rt.host_off, iters, p->eps, st, t0);
+    };
     if (p->xdt == NTT_BF16) {
       __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
       NTT_CUDA_TRY(launch_cast_bf16(X, xb, S.m * S.n, st));
       launches += 1;
       NTT_CUDA_TRY(rec(4 * s + 2));
-      dev.X = xb;
-      NTT_TRY(run_mu_iters(S.bf16, dev, p->eps, p->iters, 0, st));
-      dev.X = X;
-      NTT_TRY(run_mu_iters(S.f32, dev, p->eps, p->refine, p->iters, st));
+      NTT_TRY(mu(S.gbf16, S.bf16, xb, p->iters, 0));
+      NTT_TRY(mu(S.gf32, S.f32, X, p->refine, p->iters));
     } else {
       NTT_CUDA_TRY(rec(4 * s + 2));
-      dev.X = X;
-      NTT_TRY(run_mu_iters(S.f32, dev, p->eps, p->iters, 0, st));
+      NTT_TRY(mu(S.gf32, S.f32, X, p->iters, 0));
     }
     NTT_CUDA_TRY(rec(4 * s + 3));
     launches += 2LL * S.iters_total;
@@ -416,6 +457,28 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
     if ((size_t)(S.m * S.n) > max_xb) max_xb = (size_t)(S.m * S.n);
     p->st.push_back(S);
   }
+  // grouped-engine routes: plan each at offset 0 for its size; one scratch
+  // region shared by the routed stages follows the device layout
+  size_t grp = 0;
+  for (auto& S : p->st) {
+    for (int xb = 0; xb < 2; ++xb) {
+      ntt_plan_s::Route& rt = xb ? S.gbf16 : S.gf32;
+      if (xb && p->xdt != NTT_BF16) continue;
+      if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
+      if (!plan_route_group(S.m, S.n, S.r, xb != 0)) continue;
+      GroupShape sh;
+      sh.n = S.n;
+      sh.m = (int)S.m;
+      sh.re = S.r;
+      sh.blk = S.r;
+      sh.xbf16 = xb;
+      if (group_plan({sh}, sms, 0, false, true, &rt.gp) != NTT_OK) continue;
+      rt.on = true;
+      grp = std::max(grp, rt.gp.bytes);
+      rt.host_off = p->h_bytes;
+      p->h_bytes += (rt.gp.table_bytes + 255) / 256 * 256;
+    }
+  }
   Arena ar;
   p->off_status = ar.take(64);
   p->off_tickets = ar.take(64);
@@ -429,6 +492,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->off_H[0] = ar.take(maxH[0] * 4);
   p->off_H[1] = ar.take(maxH[1] * 4);
   if (p->xdt == NTT_BF16) p->off_xb = ar.take(max_xb * 2);
+  if (grp) p->off_grp = ar.take(grp);
   p->ws_bytes = ar.off;
   p->off_A = ar.take((size_t)prod(dims, 0, d) * 4);
   for (int k = 0; k < d; ++k)
@@ -436,6 +500,18 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->off_err = ar.take(8 * sizeof(double));
   p->off_chain = ar.take(chain_layout(d, dims, ranks).total);
   p->ws_bytes_host = ar.off;
+  if (p->off_grp)
+    for (auto& S : p->st)
+      for (ntt_plan_s::Route* rt : {&S.gf32, &S.gbf16}) {
+        if (!rt->on) continue;
+        GroupShape sh;
+        sh.n = S.n;
+        sh.m = (int)S.m;
+        sh.re = S.r;
+        sh.blk = S.r;
+        sh.xbf16 = rt == &S.gbf16 ? 1 : 0;
+        if (group_plan({sh}, sms, p->off_grp, false, true, &rt->gp) != NTT_OK) rt->on = false;
+      }
   *out = p;
   return NTT_OK;
 }
@@ -471,7 +547,10 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
     p->ev.assign(4 * d + 2, nullptr);
     for (auto& e : p->ev) NTT_CUDA_TRY(cudaEventCreate(&e));
   }
+  if (p->h_bytes && !p->h_tables) NTT_CUDA_TRY(cudaMallocHost(&p->h_tables, p->h_bytes));
   if (eager_mode()) {
+    // the engine's pinned tables are rewritten: the previous run must have read them
+    if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
     NTT_TRY(enqueue_decompose(p, A, cores, ws, st));
   } else {
     bool hit = p->exec && p->gA == A && p->gws == workspace &&

@@ -372,3 +372,20 @@ def test_tensor_core_and_fma_passes_agree(ntt, m, n, r, monkeypatch):
     for Wg, Hg in ((Wt, Ht), (Wf, Hf)):
         assert _fro_rel(Wg, Wo) <= REL_ITERATE
         assert _fro_rel(Hg, Ho) <= REL_ITERATE
+
+
+@pytest.mark.parametrize("x_dtype,refine", [("f32", 0), ("bf16", 3)])
+def test_plan_engine_routes_agree(ntt, monkeypatch, x_dtype, refine):
+    """Stages with <= 256 rows and rank >= 16 run on the grouped engine by default;
+    forcing the single-problem pass everywhere gives the same iterates within
+    rounding (10 MU iterations per stage, per-core relative 1e-4 x stage index)."""
+    dims, ranks = (16, 16, 16, 16, 16), (1, 8, 16, 16, 8, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=12)
+    out = {}
+    for engine in ("pass", "group"):
+        monkeypatch.setenv("NTT_PLAN_ENGINE", engine)
+        cores, stats, *_ = _decompose(ntt, A, ranks, 10, 7, x_dtype=x_dtype, refine=refine)
+        assert stats["status"] == "NTT_OK"
+        out[engine] = cores
+    for k, (a, b) in enumerate(zip(out["group"], out["pass"])):
+        assert _fro_rel(a, b) <= 1e-4 * (k + 1), f"core {k}: {_fro_rel(a, b):.2e}"
