@@ -223,7 +223,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_stage1_small(args):
-    """Stage-1 MU iterations (32 x 4194304, r = 8, FP32) through nmf_mu_step."""
+    """Stage-1 MU iterations (32 x 4194304, r = 8, FP32) through nmf_mu_step
+    (the single-problem pass) or, with --engine group, nmf_mu_many (the grouped
+    engine), for profiler captures."""
     import torch
 
     import synth
@@ -235,18 +237,23 @@ def run_stage1_small(args):
     X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
     W = torch.from_numpy(synth.uniform_matrix((m, r), 2)).cuda()
     H = torch.from_numpy(synth.uniform_matrix((r, n), 3)).cuda()
-    ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r))
+    if args.engine == "group":
+        ws = ntt.empty_workspace(ntt.nmf_mu_many_workspace_size([(m, n, r)]))
+        run = lambda k: ntt.nmf_mu_many([X], [W], [H], k, workspace=ws)
+    else:
+        ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r))
+        run = lambda k: ntt.nmf_mu_step(X, W, H, k, workspace=ws)
     for _ in range(args.warmup):
-        ntt.nmf_mu_step(X, W, H, 1, workspace=ws)
+        run(1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    ntt.nmf_mu_step(X, W, H, args.steps, workspace=ws)
+    run(args.steps)
     e1.record()
     torch.cuda.synchronize()
     it = e0.elapsed_time(e1) / args.steps / 1e3
     gb = (m * n * 4 + 8 * r * n) / it / 1e9
-    print(json.dumps({"case": "stage1_small", "m": m, "n": n, "r": r, "ms_per_iter": it * 1e3,
+    print(json.dumps({"case": "stage1_small", "engine": args.engine, "m": m, "n": n, "r": r, "ms_per_iter": it * 1e3,
                       "alg_GBps": round(gb, 1)}), flush=True)
     return 0
 
@@ -436,6 +443,8 @@ def main():
                          "iterations); c4_batched: 512 nTT instances (d 3-6, n_k 8-24, r_k 2-12), 8 "
                          "restarts per stage, 300 MU iterations, one batched decomposition per step; "
                          "c5_serving: 1000 Poisson requests through the serving form")
+    ap.add_argument("--engine", default="pass", choices=["pass", "group"],
+                    help="stage1_small: single-problem pass or grouped engine")
     ap.add_argument("--case", default="full", choices=["full", "stage1_small"],
                     help="stage1_small: MU iterations of the stage-1 shape on 32 x 4194304 "
                          "(512 MB, larger than L2) for profiler captures")

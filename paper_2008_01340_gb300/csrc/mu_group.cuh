@@ -213,13 +213,19 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
   const int ua = tid % C::NA, sa = tid / C::NA;
   const int kq = ua % C::RQ, cq = ua / C::RQ;
   const int k0 = 4 * kq, c0 = 4 * cq;
-  const int rps = (m + C::SA - 1) / C::SA;
-  const int ia0 = sa * rps, ia1 = gmin(m, ia0 + rps);
   int glo = 0, ghi = 0;   // rank range of the GH contraction for ranks k0..k0+3
   if (k0 < re) {
     glo = (k0 / blk) * blk;
     ghi = gmin(re, ((gmin(k0 + 3, re - 1) / blk) + 1) * blk);
   }
+  // Row splits share the m X rows and the G H rows evenly: splits before the
+  // last take q X rows each, the last split the remaining X rows plus all G H
+  // rows, and it also sums the others' partial Y (in split order) and forms H_new.
+  const bool last = sa == C::SA - 1;
+  const int gk = MODE == 0 ? ghi - glo : 0;
+  const int qa = (m + gk + C::SA - 1) / C::SA;
+  const int ia0 = gmin(m, sa * qa);
+  const int ia1 = last ? m : gmin(m, (sa + 1) * qa);
 
   // ---- phase-B role
   const int ra = (m + 3) / 4;                 // P row groups (strided rows)
@@ -262,10 +268,10 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
     const float* Hs = Xs + MP * C::XLD;
     const int64_t col0 = (int64_t)tile * T;
 
-    // ---------------- phase A: Y (and GH in split 0) as 4 x 4 register tiles
+    // ---------------- phase A: Y (and GH in the last split) as 4 x 4 register tiles
     if constexpr (MODE == 2) {
       // H already updated in HBM: transpose its tile into H_new^T
-      if (sa == 0)
+      if (last)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc)
           *reinterpret_cast<float4*>(Hnt + (c0 + cc) * LDH + k0) =
@@ -289,7 +295,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
         ay[kk][1] = __ffma2_rn(ww, x23, ay[kk][1]);
       }
     }
-    if (MODE == 0 && sa == 0) {
+    if (MODE == 0 && last) {
 #pragma unroll 4
       for (int l = glo; l < ghi; ++l) {
         const float4 g = *reinterpret_cast<const float4*>(Gs + l * R + k0);
@@ -305,24 +311,36 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
       }
     }
     if constexpr (C::SA > 1) {
-      if (sa > 0)
+      if (!last)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          *reinterpret_cast<float4*>(Yp + ((sa - 1) * R + k0 + kk) * T + c0) =
+          *reinterpret_cast<float4*>(Yp + (sa * R + k0 + kk) * T + c0) =
               make_float4(ay[kk][0].x, ay[kk][0].y, ay[kk][1].x, ay[kk][1].y);
       __syncthreads();
-      if (sa == 0)
-        for (int s2 = 1; s2 < C::SA; ++s2)
+      if (last) {
+        // Y = (partial of split 0 + ... + split SA-2) + own partial, in that order
+        float4 acc[4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc[kk] = *reinterpret_cast<const float4*>(Yp + (k0 + kk) * T + c0);
+        for (int s2 = 1; s2 < C::SA - 1; ++s2)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const float4 v = *reinterpret_cast<const float4*>(Yp + ((s2 - 1) * R + k0 + kk) * T + c0);
-            ay[kk][0].x += v.x;
-            ay[kk][0].y += v.y;
-            ay[kk][1].x += v.z;
-            ay[kk][1].y += v.w;
+            const float4 v = *reinterpret_cast<const float4*>(Yp + (s2 * R + k0 + kk) * T + c0);
+            acc[kk].x += v.x;
+            acc[kk].y += v.y;
+            acc[kk].z += v.z;
+            acc[kk].w += v.w;
           }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          ay[kk][0].x += acc[kk].x;
+          ay[kk][0].y += acc[kk].y;
+          ay[kk][1].x += acc[kk].z;
+          ay[kk][1].y += acc[kk].w;
+        }
+      }
     }
-    if (MODE == 1 && sa == 0) {
+    if (MODE == 1 && last) {
       // partial Y of this row block to HBM, ranks < re, columns < n
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
@@ -340,7 +358,7 @@ gpass_kernel(const GProb* __restrict__ probs, const int* __restrict__ cta_prob, 
         }
       }
     }
-    if (MODE == 0 && sa == 0) {
+    if (MODE == 0 && last) {
       float hn[4][4];
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
