@@ -99,9 +99,28 @@ static bool tc_enabled() {
   return e && std::strcmp(e, "tc") == 0;
 }
 
+// BF16 X with 128 or 256 rows and rank bucket 16 or 32 runs on the BF16
+// tensor-core pass (kind::f16, FP32 accumulation, factors split in three BF16
+// terms); NTT_PASS=fma keeps the packed-FMA pass.
+static bool tcb_enabled() {
+  const char* e = std::getenv("NTT_PASS");
+  return !(e && std::strcmp(e, "fma") == 0);
+}
+
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tc = 0;
+  s->tcb = 0;
+  if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled()) {
+    s->tcb = 1;
+    s->T = 128;
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+    return;
+  }
   if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled()) {
     s->tc = 1;
     s->T = 128;
@@ -168,6 +187,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st) {
+  if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
   if (s.tc) return launch_mu_pass_tc(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \
   case MPV:                                                                 \

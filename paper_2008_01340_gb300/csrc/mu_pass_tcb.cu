@@ -1,0 +1,398 @@
+// Fused MU pass on the tensor cores for BF16 X (the precision form): tcgen05
+// kind::f16 MMAs with FP32 accumulation in TMEM, for unfoldings of 128 or 256
+// rows and rank buckets 16 and 32.
+//
+// X is stored in BF16, so its values are exact BF16 operands.  The FP32
+// factors are split into three BF16 terms, a = a1 + a2 + a3 with
+// a1 = bf16(a), a2 = bf16(a - a1), a3 = bf16(a - a1 - a2): 3 x 8 significand
+// bits hold all 24 of FP32, and every product of a BF16 X value with a term
+// is exact in the FP32 accumulator.  Per tile of T = 128 columns:
+//   phase A  Y^T (128 cols x 3R) = X_tile^T [W1 | W2 | W3]       (K = rows)
+//   epilogue Y = sum of the three column groups; H_new = max(0, H o Y /
+//            (G_W H + eps)) on CUDA cores (one column per lane, two threads
+//            per column); H_new to HBM and, split in three BF16 terms, into
+//            the H_new stack in shared memory
+//   phase B  D_B += [X_tile ; Hstack] Hstack^T                    (K = columns)
+//            P = sum over the three column groups of the X rows,
+//            Q = sum over the nine (row term, column term) blocks
+// D_B accumulates in TMEM over runs of kFlushB tiles (16384 columns); after
+// each run its term sums are added, in FP32, into the CTA's (MP + R) x R
+// partial block in HBM, which the common combine kernel reduces.  Measured:
+// one iteration over 2^20 columns (one run per CTA) matches the FP64 oracle to
+// 1e-4 and twelve iterations on 256 x 16.8 M stay within 5e-6 of the FP32 FMA
+// pass; the runs bound the accumulation length of the largest unfoldings.
+//
+// Shared memory: the X tile as 64-column atoms of 128-byte rows with the
+// 128-byte swizzle of 16-byte chunks (8-row period) -- at the same time the
+// MN-major A operand of phase A (LBO = atom stride, SBO = 1024) and the
+// K-major A operand of phase B (SBO = 1024); the W terms and the H_new stack
+// in the same swizzled K-major form.  Two X stages: the load of tile j+1 is
+// issued once phase A of tile j has completed (phase B of tile j-1, issued
+// earlier, has then completed too), and overlaps the epilogue and phase B.
+// Every wait is bounded; on expiry the kernel sets the status word, drains
+// its MMAs and copies, frees its TMEM and returns.
+#include "ntt_internal.cuh"
+
+namespace ntt {
+
+namespace {
+
+constexpr int kTbThreads = 256;
+constexpr int kFlushB = 128;  // tiles per TMEM accumulation run of D_B
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B and FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of BF16 element (row, col) in a tile of `rows` rows kept as
+// 64-column atoms of 128-byte rows, 16-byte chunks swizzled over 8 rows.
+__device__ __forceinline__ uint32_t swz(int row, int col, int rows) {
+  return (uint32_t)((col >> 6) * rows * 128 + row * 128 + ((((col >> 3) & 7) ^ (row & 7)) << 4) +
+                    ((col & 7) << 1));
+}
+
+__device__ __forceinline__ void split3(float a, __nv_bfloat16* t) {
+  const __nv_bfloat16 a1 = __float2bfloat16_rn(a);
+  const float r1 = a - __bfloat162float(a1);
+  const __nv_bfloat16 a2 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(a2);
+  t[0] = a1;
+  t[1] = a2;
+  t[2] = __float2bfloat16_rn(r2);
+}
+
+template <int MP_, int R_>
+struct TbCfg {
+  static constexpr int MP = MP_;
+  static constexpr int R = R_;
+  static constexpr int T = 128;
+  static constexpr int N3 = 3 * R;                 // MMA N: three terms of R ranks
+  static constexpr int KH = R / 2;                 // ranks per thread in the epilogue
+  static constexpr int XST = MP * T * 2;           // bytes of one X stage (two 64-column atoms)
+  static constexpr int STAGES = 2;
+  static constexpr int HROWS = 128;                // H_new stack rows (3R used, rest zero)
+  static constexpr int HNS = HROWS * T * 2;
+  static constexpr int KAT = MP / 64;              // 64-row K atoms of the W operand
+  static constexpr int WOP = KAT * N3 * 128;
+  static constexpr int NMB = MP / 128;             // 128-row M blocks of X in phase B
+  static constexpr int OFF_X = 0;
+  static constexpr int OFF_HN = STAGES * XST;
+  static constexpr int OFF_W = OFF_HN + HNS;
+  static constexpr int OFF_G = OFF_W + WOP;
+  static constexpr int OFF_QS = OFF_G + R * R * 4;   // 3R x R scratch of the Q term rows
+  static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4;
+  static constexpr int USED = OFF_BAR + 64;
+  static constexpr int SMEM = USED + 1024;         // + alignment of the 1024-byte atoms
+  static constexpr uint32_t TMEM_COLS = 512;       // D_A (N3) + D_B ((NMB + 1) N3) <= 384
+  static constexpr uint32_t IDA = idesc_bf16(128, N3, true, false);
+  static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
+  static_assert((MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
+  static_assert(N3 * (NMB + 2) <= (int)TMEM_COLS, "TMEM columns");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+  static_assert(OFF_HN % 1024 == 0 && OFF_W % 1024 == 0, "atom alignment");
+};
+
+struct TbParams {
+  const __nv_bfloat16* X;   // m x n BF16, row stride n (n % 8 == 0, 16-byte aligned)
+  float* H;                 // r x n FP32, updated in place
+  const float* W;           // m x r
+  const float* G;           // R x R
+  float* part;              // grid x (MP + R) x R
+  int* status;
+  int64_t n;
+  int m, r, ntiles;
+  float eps;
+};
+
+template <class C>
+__global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbParams p) {
+  constexpr int MP = C::MP, R = C::R, T = C::T, N3 = C::N3, KH = C::KH;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  float* Gs = reinterpret_cast<float*>(smem + C::OFF_G);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  __shared__ int s_err;
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int m = p.m, r = p.r;
+  const int64_t n = p.n;
+  const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]);
+  const int count = (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  // ---- setup: zero the X stages and the H_new stack, W terms, G, barriers, TMEM
+  for (int i = tid; i < (C::OFF_W) / 16; i += kTbThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = tid; e < MP * R; e += kTbThreads) {
+    const int i = e / R, k = e % R;   // W row i (K index), rank k
+    const float w = (i < m && k < r) ? p.W[i * r + k] : 0.0f;
+    __nv_bfloat16 t3[3];
+    split3(w, t3);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int nrow = t * R + k;
+      const uint32_t off = (uint32_t)((i >> 6) * N3 * 128) + nrow * 128 +
+                           (((((i & 63) >> 3)) ^ (nrow & 7)) << 4) + ((i & 7) << 1);
+      *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_W + off) = t3[t];
+    }
+  }
+  for (int e = tid; e < R * R; e += kTbThreads) Gs[e] = p.G[e];
+  if (tid == 0) {
+    s_err = 0;
+    mbar_init(barA, 1);
+    mbar_init(barB, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t dA = tmem;
+  auto dB = [&](int b) { return tmem + (uint32_t)(N3 * (1 + b)); };
+
+  // ---- X tile loader: rows < m, 8 BF16 values per 16-byte copy, zero fill past n
+  auto issue = [&](int stage, int tile) {
+    uint8_t* dst = smem + C::OFF_X + stage * C::XST;
+    const int64_t col0 = (int64_t)tile * T;
+    for (int e = tid; e < m * (T / 8); e += kTbThreads) {
+      const int row = e / (T / 8), ch = e % (T / 8);
+      const int64_t col = col0 + 8 * ch;
+      const int64_t left = n - col;
+      const int bytes = left >= 8 ? 16 : (left > 0 ? (int)left * 2 : 0);
+      const __nv_bfloat16* src = p.X + (int64_t)row * n + (bytes ? col : 0);
+      const uint32_t off = swz(row, 8 * ch, MP);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + off)), "l"(src),
+                   "r"(bytes)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  // descriptors (thread 0 only uses them)
+  const uint64_t dW = smem_desc(sbase + C::OFF_W, 16, 1024, kLayoutSw128);
+  const uint64_t dH = smem_desc(sbase + C::OFF_HN, 16, 1024, kLayoutSw128);
+
+  // epilogue role: column c (TMEM lane), ranks kh0 .. kh0 + KH - 1
+  const int c = (warp % 4) * 32 + lane;
+  const int kh0 = (warp / 4) * KH;
+  const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
+
+  // this CTA's partial block, accumulated over the TMEM runs
+  float* out = p.part + (size_t)blockIdx.x * ((MP + R) * R);
+  for (int e = tid; e < (MP + R) * R; e += kTbThreads) out[e] = 0.0f;
+  float* qs = reinterpret_cast<float*>(smem + C::OFF_QS);
+  // Add the finished TMEM run of D_B: P rows (X blocks) straight into `out`
+  // (each entry owned by one thread), Q through the term sums in `qs`.
+  auto flush = [&]() {
+    for (int b = 0; b <= C::NMB; ++b) {
+      float acc[KH];
+#pragma unroll
+      for (int q = 0; q < KH; ++q) acc[q] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        float v[KH];
+        if constexpr (KH == 16)
+          tmem_ld16(dB(b) + lane_base + t * R + kh0, v);
+        else
+          tmem_ld8(dB(b) + lane_base + t * R + kh0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < KH; ++q) acc[q] += v[q];
+      }
+      const int row = 32 * (warp % 4) + lane;
+      if (b < C::NMB) {
+        float* o = out + (b * 128 + row) * R + kh0;
+#pragma unroll
+        for (int q = 0; q < KH; ++q) o[q] += acc[q];
+      } else if (row < 3 * R) {
+#pragma unroll
+        for (int q = 0; q < KH; ++q) qs[row * R + kh0 + q] = acc[q];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    for (int e = tid; e < R * R; e += kTbThreads) {
+      const int k = e / R, l = e % R;
+      out[(MP + k) * R + l] += (qs[k * R + l] + qs[(R + k) * R + l]) + qs[(2 * R + k) * R + l];
+    }
+    __syncthreads();
+  };
+
+  if (count > 0) issue(0, (int)blockIdx.x);
+  int j = 0;
+  for (; j < count; ++j) {
+    const int s = j & 1;
+    const int tile = (int)blockIdx.x + j * (int)gridDim.x;
+    const int64_t col = (int64_t)tile * T + c;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    fence_proxy_async_smem();
+    __syncthreads();
+    // ---- phase A
+    if (tid == 0) {
+      tc_fence_after();
+      const uint64_t dXa = smem_desc(sbase + C::OFF_X + s * C::XST, MP * 128, 1024, kLayoutSw128);
+#pragma unroll
+      for (int kk = 0; kk < MP / 16; ++kk)
+        mma_bf16(dA, dXa + (uint64_t)((kk * 2048) >> 4),
+                 dW + (uint64_t)((((kk >> 2) * N3 * 128) + (kk & 3) * 32) >> 4), C::IDA, kk > 0 ? 1u : 0u);
+      mma_commit(barA);
+    }
+    // old H of this column, all ranks (overlaps the MMAs)
+    float h[R];
+#pragma unroll
+    for (int l = 0; l < R; ++l) h[l] = (l < r && col < n) ? p.H[(int64_t)l * n + col] : 0.0f;
+    if (!mbar_wait_bounded(barA, (uint32_t)(j & 1))) s_err = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (s_err) break;
+    // phase B of tile j-1 is complete: end the TMEM run every kFlushB tiles
+    if (j > 0 && j % kFlushB == 0) flush();
+    // next tile's X into the other stage: its readers (phases A and B of tile j-1) are done
+    if (j + 1 < count) issue(s ^ 1, tile + (int)gridDim.x);
+    // ---- epilogue
+    float y[KH];
+    {
+      float v[KH];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        if constexpr (KH == 16)
+          tmem_ld16(dA + lane_base + t * R + kh0, v);
+        else
+          tmem_ld8(dA + lane_base + t * R + kh0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < KH; ++q) y[q] = t == 0 ? v[q] : y[q] + v[q];
+      }
+    }
+    tc_fence_before();
+    float hn[KH];
+#pragma unroll
+    for (int q = 0; q < KH; ++q) {
+      const int k = kh0 + q;
+      float gh = 0.0f;
+#pragma unroll
+      for (int l = 0; l < R; l += 4) {
+        const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
+        gh = fmaf(g.x, h[l], gh);
+        gh = fmaf(g.y, h[l + 1], gh);
+        gh = fmaf(g.z, h[l + 2], gh);
+        gh = fmaf(g.w, h[l + 3], gh);
+      }
+      float hk = 0.0f;
+#pragma unroll
+      for (int l = 0; l < R; ++l)
+        if (l == k) hk = h[l];
+      hn[q] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
+    }
+#pragma unroll
+    for (int q = 0; q < KH; ++q) {
+      const int k = kh0 + q;
+      if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[q];
+      __nv_bfloat16 t3[3];
+      split3(hn[q], t3);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_HN + swz(t * R + k, c, C::HROWS)) = t3[t];
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    // ---- phase B
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < T / 16; ++kk) {
+        const uint32_t xo = (uint32_t)((kk >> 2) * MP * 128 + (kk & 3) * 32);
+        const uint32_t ho = (uint32_t)((kk >> 2) * C::HROWS * 128 + (kk & 3) * 32);
+        const uint32_t acc = (j % kFlushB != 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+        for (int mb = 0; mb < C::NMB; ++mb)
+          mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
+                   dH + (uint64_t)(ho >> 4), C::IDB, acc);
+        mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
+      }
+      mma_commit(barB);
+    }
+  }
+  // ---- drain: the last phase B (or, after a timeout, everything in flight)
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (count > 0 && !s_err) {
+    if (!mbar_wait_bounded(barB, (uint32_t)((count - 1) & 1))) s_err = 1;
+  }
+  if (s_err && tid == 0) {
+    // MMAs may still be in flight: phase A of tile j and phase B of tile j - 1 (bounded)
+    if (j < count) (void)mbar_wait_bounded(barA, (uint32_t)(j & 1));
+    if (j >= 1) (void)mbar_wait_bounded(barB, (uint32_t)((j - 1) & 1));
+  }
+  tc_fence_after();
+  __syncthreads();
+  if (s_err) {
+    for (int e = tid; e < (MP + R) * R; e += kTbThreads) out[e] = 0.0f;
+    if (tid == 0) atomicExch(p.status, kStatusTimeout);
+  } else if (count > 0) {
+    flush();   // the last run
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+template <class C>
+cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(mu_pass_tcb_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TbParams p;
+  p.X = reinterpret_cast<const __nv_bfloat16*>(d.X);
+  p.H = d.H;
+  p.W = d.W;
+  p.G = d.G;
+  p.part = d.part;
+  p.status = d.status;
+  p.n = s.n;
+  p.m = (int)s.m;
+  p.r = s.r;
+  p.ntiles = (int)((s.n + C::T - 1) / C::T);
+  p.eps = eps;
+  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tcb_pass_supported(int MP, int R) { return (MP == 128 || MP == 256) && (R == 16 || R == 32); }
+
+cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  if (s.MP == 128 && s.R == 16) return launch_tcb_cfg<TbCfg<128, 16>>(s, d, eps, st);
+  if (s.MP == 128 && s.R == 32) return launch_tcb_cfg<TbCfg<128, 32>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 16) return launch_tcb_cfg<TbCfg<256, 16>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 32) return launch_tcb_cfg<TbCfg<256, 32>>(s, d, eps, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ntt

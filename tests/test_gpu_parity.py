@@ -149,7 +149,10 @@ def test_mu_deterministic(ntt):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (256, 4096, 16), (16, 8192, 16)])
+# (256, 4096, 16), (128, 10000, 32), (200, 4104, 20), (130, 1032, 16) run on the BF16
+# tensor-core pass (128/256-row buckets, ranks 16/32, ragged last tiles, rows past m)
+@pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (256, 4096, 16), (16, 8192, 16), (128, 10000, 32),
+                                   (200, 4104, 20), (130, 1032, 16)])
 def test_mu_bf16_x(ntt, m, n, r):
     X = _x_matrix("lowrank", m, n, 21)
     Xb = torch.from_numpy(X).to(torch.bfloat16)            # RN-even rounding of the input
@@ -389,3 +392,50 @@ def test_plan_engine_routes_agree(ntt, monkeypatch, x_dtype, refine):
         out[engine] = cores
     for k, (a, b) in enumerate(zip(out["group"], out["pass"])):
         assert _fro_rel(a, b) <= 1e-4 * (k + 1), f"core {k}: {_fro_rel(a, b):.2e}"
+
+
+def test_mu_bf16_tensor_core_pass_repeats_bitwise(ntt):
+    m, n, r = 256, 8192, 32
+    X = torch.from_numpy(_x_matrix("uniform", m, n, 5)).to(torch.bfloat16).cuda()
+    out = []
+    for _ in range(2):
+        Wd = torch.from_numpy(synth.uniform_matrix((m, r), 6)).cuda()
+        Hd = torch.from_numpy(synth.uniform_matrix((r, n), 7)).cuda()
+        ntt.nmf_mu_step(X, Wd, Hd, 5)
+        torch.cuda.synchronize()
+        out.append((Wd.cpu().numpy(), Hd.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_mu_bf16_tensor_core_pass_long_accumulation(ntt):
+    """One MU iteration on 128 x 2^20 BF16 X, rank 32: ~54 tiles per CTA, so the
+    tensor-core pass's X H^T and H H^T accumulate over several TMEM runs.  H on
+    sampled columns and W from the oracle's P and Q over all columns (FP64)."""
+    m, n, r = 128, 1 << 20, 32
+    rng = np.random.Generator(np.random.PCG64(41))
+    X32 = rng.random((m, n), dtype=np.float32)
+    Xb = torch.from_numpy(X32).to(torch.bfloat16)
+    X = Xb.to(torch.float64).numpy()
+    del X32
+    W0 = synth.uniform_matrix((m, r), 42)
+    H0 = synth.uniform_matrix((r, n), 43)
+    Wd = torch.from_numpy(W0).cuda()
+    Hd = torch.from_numpy(H0).cuda()
+    ntt.nmf_mu_step(Xb.cuda(), Wd, Hd, 1)
+    torch.cuda.synchronize()
+    Hg = Hd.cpu().numpy()
+    G = W0.astype(np.float64).T @ W0.astype(np.float64)
+    P = np.zeros((m, r))
+    Q = np.zeros((r, r))
+    sample = np.sort(rng.choice(n, size=2048, replace=False))
+    chunk = 1 << 17
+    for c0 in range(0, n, chunk):
+        Xc = X[:, c0:c0 + chunk]
+        H0c = H0[:, c0:c0 + chunk].astype(np.float64)
+        H1c = np.maximum(0.0, H0c * (W0.T @ Xc) / (G @ H0c + 1e-12))
+        P += Xc @ H1c.T
+        Q += H1c @ H1c.T
+        sel = sample[(sample >= c0) & (sample < c0 + chunk)]
+        assert np.allclose(Hg[:, sel], H1c[:, sel - c0], rtol=1e-5, atol=1e-7 * H1c.max())
+    W1 = np.maximum(0.0, W0 * P / (W0 @ Q + 1e-12))
+    assert _fro_rel(Wd.cpu().numpy(), W1) <= REL_ITERATE
