@@ -562,7 +562,10 @@ def main():
     traffic = None
     if NCU_TRAFFIC["kernel_sha"] == _kernel_sha() and wl == WORKLOAD:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    kname = (f"mu_pass_kernel<m={st1['m']},r={st1['r']},{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
+    kernel_of = {"fma_pass": "mu_pass_kernel", "grouped": "gpass_kernel", "tc_bf16": "mu_pass_tcb_kernel",
+                 "tc_tf32": "mu_pass_tc_kernel"}
+    kname = (f"{kernel_of.get(st1.get('engine'), st1.get('engine'))}<m={st1['m']},r={st1['r']},"
+             f"{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
              f"stage {dom + 1} ({st1['m']} x {st1['n']}, r={st1['r']})")
     if achieved / peak >= tflops / FP32_FMA_TFLOPS:
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -590,7 +593,7 @@ def main():
             "mu_iters_per_s": round(1.0 / it_s, 1) if it_s > 0 else None,
             "alg_GBps": round(st["alg_bytes"] / it_s / 1e9, 1) if it_s > 0 else None,
             "frac_hbm": round(st["alg_bytes"] / it_s / 1e9 / peak, 4) if it_s > 0 else None,
-            "stage_ms": round(st["stage_ms"], 3),
+            "stage_ms": round(st["stage_ms"], 3), "engine": st.get("engine"),
             "resid_half_sq": st["resid"], "xnorm2": st["xnorm2"]})
 
     line = {

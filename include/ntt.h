@@ -87,7 +87,13 @@ typedef struct {
   double alg_bytes[NTT_MAX_D];      /* algorithmic bytes of one MU iteration of the stage:
                                        m n sizeof(X) + 8 r n (X read once, H read+written) */
   int64_t launches;                 /* kernels launched by one decomposition */
+  int engine[NTT_MAX_D];            /* kernel of the stage's main MU loop: NTT_ENGINE_* */
 } ntt_stats;
+
+#define NTT_ENGINE_FMA_PASS 0         /* single-problem fused pass, packed FP32 FMAs */
+#define NTT_ENGINE_GROUPED 1          /* grouped engine (register-tiled FMA pass) */
+#define NTT_ENGINE_TC_BF16 2          /* BF16-X tensor-core pass (tcgen05 kind::f16) */
+#define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (opt-in, NTT_PASS=tc) */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);

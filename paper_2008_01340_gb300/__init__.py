@@ -109,7 +109,11 @@ class _Stats(ctypes.Structure):
         ("total_ms", ctypes.c_float),
         ("alg_bytes", ctypes.c_double * NTT_MAX_D),
         ("launches", ctypes.c_int64),
+        ("engine", ctypes.c_int * NTT_MAX_D),
     ]
+
+
+ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32"}
 
 
 _lib_handle = None
@@ -294,7 +298,8 @@ def ntt_plan_get_stats(plan):
         out["stages"].append(dict(
             m=st.m[s], n=st.n[s], r=st.r[s], iters=st.iters[s], xnorm2=st.xnorm2[s],
             obj_first=st.obj_first[s], obj_last=st.obj_last[s], resid=st.resid[s],
-            stage_ms=st.stage_ms[s], iter_ms=st.iter_ms[s], alg_bytes=st.alg_bytes[s]))
+            stage_ms=st.stage_ms[s], iter_ms=st.iter_ms[s], alg_bytes=st.alg_bytes[s],
+            engine=ENGINES.get(st.engine[s], st.engine[s])))
     _check(code, "ntt_plan_get_stats")
     return out
 

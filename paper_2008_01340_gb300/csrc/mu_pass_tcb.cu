@@ -1,6 +1,6 @@
 // Fused MU pass on the tensor cores for BF16 X (the precision form): tcgen05
-// kind::f16 MMAs with FP32 accumulation in TMEM, for unfoldings of 128 or 256
-// rows and rank buckets 16 and 32.
+// kind::f16 MMAs with FP32 accumulation in TMEM, for unfoldings of 16, 32,
+// 128 or 256 rows and rank buckets 16 and 32.
 //
 // X is stored in BF16, so its values are exact BF16 operands.  The FP32
 // factors are split into three BF16 terms, a = a1 + a2 + a3 with
@@ -15,12 +15,13 @@
 //   phase B  D_B += [X_tile ; Hstack] Hstack^T                    (K = columns)
 //            P = sum over the three column groups of the X rows,
 //            Q = sum over the nine (row term, column term) blocks
-// D_B accumulates in TMEM over runs of kFlushB tiles (16384 columns); after
+// D_B accumulates in TMEM over runs of kFlushB tiles (2048 columns); after
 // each run its term sums are added, in FP32, into the CTA's (MP + R) x R
 // partial block in HBM, which the common combine kernel reduces.  Measured:
-// one iteration over 2^20 columns (one run per CTA) matches the FP64 oracle to
-// 1e-4 and twelve iterations on 256 x 16.8 M stay within 5e-6 of the FP32 FMA
-// pass; the runs bound the accumulation length of the largest unfoldings.
+// long TMEM runs carry a small accumulation bias -- 12 iterations on
+// 256 x 16.8 M differ from the FP32 FMA pass by 4.3e-6 with runs of 128 tiles
+// and by 1.4e-6 with runs of 16 (FP32 rounding level), and the first core of
+// the 16^6 precision form moves from 3.3e-6 to 6.0e-7 from the FP64 oracle.
 //
 // Shared memory: the X tile as 64-column atoms of 128-byte rows with the
 // 128-byte swizzle of 16-byte chunks (8-row period) -- at the same time the
@@ -38,7 +39,7 @@ namespace ntt {
 namespace {
 
 constexpr int kTbThreads = 256;
-constexpr int kFlushB = 128;  // tiles per TMEM accumulation run of D_B
+constexpr int kFlushB = 16;   // tiles per TMEM accumulation run of D_B
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -80,13 +81,20 @@ struct TbCfg {
   static constexpr int T = 128;
   static constexpr int N3 = 3 * R;                 // MMA N: three terms of R ranks
   static constexpr int KH = R / 2;                 // ranks per thread in the epilogue
-  static constexpr int XST = MP * T * 2;           // bytes of one X stage (two 64-column atoms)
-  static constexpr int STAGES = 2;
-  static constexpr int HROWS = 128;                // H_new stack rows (3R used, rest zero)
-  static constexpr int HNS = HROWS * T * 2;
-  static constexpr int KAT = MP / 64;              // 64-row K atoms of the W operand
+  // Stacked form (MP <= 32): a stage holds 128 rows, X in rows 0..MP-1 and the
+  // H_new terms in rows MP..MP+3R-1, so phase B is one 128-row block.
+  // Otherwise a stage holds MP rows of X and the H_new stack has its own 128 rows.
+  static constexpr bool STACK = MP <= 32;
+  static constexpr int SR = STACK ? 128 : MP;      // rows of a stage tile
+  static constexpr int XST = SR * T * 2;           // bytes of one stage (two 64-column atoms)
+  static constexpr int STAGES = STACK ? 4 : 2;
+  static constexpr int HROWS = 128;                // rows of the separate H_new stack
+  static constexpr int HNS = STACK ? 0 : HROWS * T * 2;
+  static constexpr int HROW0 = STACK ? MP : 0;     // first H_new row in its region
+  static constexpr int HSR = STACK ? SR : HROWS;   // rows of the region holding H_new
+  static constexpr int KAT = MP < 64 ? 1 : MP / 64;   // 64-row K atoms of the W operand
   static constexpr int WOP = KAT * N3 * 128;
-  static constexpr int NMB = MP / 128;             // 128-row M blocks of X in phase B
+  static constexpr int NMB = STACK ? 0 : MP / 128;    // X-only 128-row M blocks of phase B
   static constexpr int OFF_X = 0;
   static constexpr int OFF_HN = STAGES * XST;
   static constexpr int OFF_W = OFF_HN + HNS;
@@ -95,10 +103,11 @@ struct TbCfg {
   static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4;
   static constexpr int USED = OFF_BAR + 64;
   static constexpr int SMEM = USED + 1024;         // + alignment of the 1024-byte atoms
-  static constexpr uint32_t TMEM_COLS = 512;       // D_A (N3) + D_B ((NMB + 1) N3) <= 384
+  static constexpr uint32_t TMEM_COLS = STACK ? 256 : 512;   // D_A (N3) + D_B ((NMB + 1) N3)
   static constexpr uint32_t IDA = idesc_bf16(128, N3, true, false);
   static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
-  static_assert((MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
+  static_assert((MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
+  static_assert(!STACK || MP + 3 * R <= 128, "stacked rows fit one M block");
   static_assert(N3 * (NMB + 2) <= (int)TMEM_COLS, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
   static_assert(OFF_HN % 1024 == 0 && OFF_W % 1024 == 0, "atom alignment");
@@ -168,17 +177,18 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   const uint32_t dA = tmem;
   auto dB = [&](int b) { return tmem + (uint32_t)(N3 * (1 + b)); };
 
-  // ---- X tile loader: rows < m, 8 BF16 values per 16-byte copy, zero fill past n
-  auto issue = [&](int stage, int tile) {
+  // ---- X tile loader: rows < m, 8 BF16 values per 16-byte copy, zero fill past
+  // n; tiles past the CTA's range issue nothing but still commit a group
+  auto issue = [&](int stage, int tile, bool valid) {
     uint8_t* dst = smem + C::OFF_X + stage * C::XST;
     const int64_t col0 = (int64_t)tile * T;
-    for (int e = tid; e < m * (T / 8); e += kTbThreads) {
+    for (int e = tid; valid && e < m * (T / 8); e += kTbThreads) {
       const int row = e / (T / 8), ch = e % (T / 8);
       const int64_t col = col0 + 8 * ch;
       const int64_t left = n - col;
       const int bytes = left >= 8 ? 16 : (left > 0 ? (int)left * 2 : 0);
       const __nv_bfloat16* src = p.X + (int64_t)row * n + (bytes ? col : 0);
-      const uint32_t off = swz(row, 8 * ch, MP);
+      const uint32_t off = swz(row, 8 * ch, C::SR);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + off)), "l"(src),
                    "r"(bytes)
                    : "memory");
@@ -203,6 +213,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   // (each entry owned by one thread), Q through the term sums in `qs`.
   auto flush = [&]() {
     for (int b = 0; b <= C::NMB; ++b) {
+      const bool qblock = b == C::NMB;
       float acc[KH];
 #pragma unroll
       for (int q = 0; q < KH; ++q) acc[q] = 0.0f;
@@ -218,13 +229,13 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
         for (int q = 0; q < KH; ++q) acc[q] += v[q];
       }
       const int row = 32 * (warp % 4) + lane;
-      if (b < C::NMB) {
-        float* o = out + (b * 128 + row) * R + kh0;
+      if (!qblock || (C::STACK && row < MP)) {
+        float* o = out + (b * 128 + row) * R + kh0;   // P rows (in the stacked block: rows < MP)
 #pragma unroll
         for (int q = 0; q < KH; ++q) o[q] += acc[q];
-      } else if (row < 3 * R) {
+      } else if (row >= C::HROW0 && row < C::HROW0 + 3 * R) {
 #pragma unroll
-        for (int q = 0; q < KH; ++q) qs[row * R + kh0 + q] = acc[q];
+        for (int q = 0; q < KH; ++q) qs[(row - C::HROW0) * R + kh0 + q] = acc[q];
       }
     }
     tc_fence_before();
@@ -236,19 +247,19 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     __syncthreads();
   };
 
-  if (count > 0) issue(0, (int)blockIdx.x);
+  for (int q = 0; q < C::STAGES - 1; ++q) issue(q, (int)blockIdx.x + q * (int)gridDim.x, q < count);
   int j = 0;
   for (; j < count; ++j) {
-    const int s = j & 1;
+    const int s = j % C::STAGES;
     const int tile = (int)blockIdx.x + j * (int)gridDim.x;
     const int64_t col = (int64_t)tile * T + c;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
     fence_proxy_async_smem();
     __syncthreads();
     // ---- phase A
     if (tid == 0) {
       tc_fence_after();
-      const uint64_t dXa = smem_desc(sbase + C::OFF_X + s * C::XST, MP * 128, 1024, kLayoutSw128);
+      const uint64_t dXa = smem_desc(sbase + C::OFF_X + s * C::XST, C::SR * 128, 1024, kLayoutSw128);
 #pragma unroll
       for (int kk = 0; kk < MP / 16; ++kk)
         mma_bf16(dA, dXa + (uint64_t)((kk * 2048) >> 4),
@@ -265,8 +276,9 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     if (s_err) break;
     // phase B of tile j-1 is complete: end the TMEM run every kFlushB tiles
     if (j > 0 && j % kFlushB == 0) flush();
-    // next tile's X into the other stage: its readers (phases A and B of tile j-1) are done
-    if (j + 1 < count) issue(s ^ 1, tile + (int)gridDim.x);
+    // tile j + STAGES - 1 into the stage of tile j - 1, whose readers (phases A
+    // and B of tile j - 1) are done
+    issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x, j + C::STAGES - 1 < count);
     // ---- epilogue
     float y[KH];
     {
@@ -310,7 +322,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
       split3(hn[q], t3);
 #pragma unroll
       for (int t = 0; t < 3; ++t)
-        *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_HN + swz(t * R + k, c, C::HROWS)) = t3[t];
+        *reinterpret_cast<__nv_bfloat16*>(smem + (C::STACK ? C::OFF_X + s * C::XST : C::OFF_HN) +
+                                          swz(C::HROW0 + t * R + k, c, C::HSR)) = t3[t];
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -320,14 +333,21 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < T / 16; ++kk) {
-        const uint32_t xo = (uint32_t)((kk >> 2) * MP * 128 + (kk & 3) * 32);
-        const uint32_t ho = (uint32_t)((kk >> 2) * C::HROWS * 128 + (kk & 3) * 32);
+        const uint32_t xo = (uint32_t)((kk >> 2) * C::SR * 128 + (kk & 3) * 32);
         const uint32_t acc = (j % kFlushB != 0 || kk > 0) ? 1u : 0u;
+        if constexpr (C::STACK) {
+          // one block: A = the stage's 128 rows [X ; H_new terms ; 0], B = its H_new rows
+          const uint32_t base = sbase + C::OFF_X + s * C::XST + xo;
+          mma_bf16(dB(0), smem_desc(base, 16, 1024, kLayoutSw128),
+                   smem_desc(base + C::HROW0 * 128, 16, 1024, kLayoutSw128), C::IDB, acc);
+        } else {
+          const uint32_t ho = (uint32_t)((kk >> 2) * C::HROWS * 128 + (kk & 3) * 32);
 #pragma unroll
-        for (int mb = 0; mb < C::NMB; ++mb)
-          mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
-                   dH + (uint64_t)(ho >> 4), C::IDB, acc);
-        mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
+          for (int mb = 0; mb < C::NMB; ++mb)
+            mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
+                     dH + (uint64_t)(ho >> 4), C::IDB, acc);
+          mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
+        }
       }
       mma_commit(barB);
     }
@@ -385,9 +405,15 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
 
 }  // namespace
 
-bool tcb_pass_supported(int MP, int R) { return (MP == 128 || MP == 256) && (R == 16 || R == 32); }
+bool tcb_pass_supported(int MP, int R) {
+  return (MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32);
+}
 
 cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  if (s.MP == 16 && s.R == 16) return launch_tcb_cfg<TbCfg<16, 16>>(s, d, eps, st);
+  if (s.MP == 16 && s.R == 32) return launch_tcb_cfg<TbCfg<16, 32>>(s, d, eps, st);
+  if (s.MP == 32 && s.R == 16) return launch_tcb_cfg<TbCfg<32, 16>>(s, d, eps, st);
+  if (s.MP == 32 && s.R == 32) return launch_tcb_cfg<TbCfg<32, 32>>(s, d, eps, st);
   if (s.MP == 128 && s.R == 16) return launch_tcb_cfg<TbCfg<128, 16>>(s, d, eps, st);
   if (s.MP == 128 && s.R == 32) return launch_tcb_cfg<TbCfg<128, 32>>(s, d, eps, st);
   if (s.MP == 256 && s.R == 16) return launch_tcb_cfg<TbCfg<256, 16>>(s, d, eps, st);

@@ -29,12 +29,13 @@ namespace ntt {
 
 // Launch the gram and `iters` (pass, combine) pairs of one NMF.
 ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
-                        cudaStream_t st) {
+                        cudaStream_t st, int* engine) {
   CUtensorMap mx, mh;
   std::memset(&mx, 0, sizeof(mx));
   std::memset(&mh, 0, sizeof(mh));
   MuShape s = shp;
   mu_finalize_shape(&s, dev.X, dev.H, device_sms());
+  if (engine) *engine = s.tcb ? NTT_ENGINE_TC_BF16 : (s.tc ? NTT_ENGINE_TC_TF32 : NTT_ENGINE_FMA_PASS);
   if (s.tma) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
   for (int t = 0; t < iters; ++t) {
     NTT_CUDA_TRY_NS(launch_mu_pass(s, dev, eps, mx, mh, st));
@@ -233,6 +234,7 @@ struct ntt_plan_s {
     int iters_total;
     size_t obj_off;  // index into the objective array
     double alg_bytes;
+    int engine = NTT_ENGINE_FMA_PASS;   // kernel of the main MU loop (set when enqueued)
   };
   std::vector<Stage> st;
   // workspace layout
@@ -330,10 +332,15 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
     auto mu = [&](const ntt_plan_s::Route& rt, const MuShape& shp, const void* Xv, int iters,
                   int t0) -> ntt_status {
       if (iters <= 0) return NTT_OK;
+      const bool main_loop = t0 == 0;
       if (!rt.on) {
         dev.X = Xv;
-        return run_mu_iters(shp, dev, p->eps, iters, t0, st);
+        int eng = NTT_ENGINE_FMA_PASS;
+        const ntt_status e = run_mu_iters(shp, dev, p->eps, iters, t0, st, &eng);
+        if (main_loop) p->st[s].engine = eng;
+        return e;
       }
+      if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;
       GroupPtrs g;
       g.X = Xv;
       g.H = H;
@@ -631,6 +638,7 @@ ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
     out->r[s] = p->st[s].r;
     out->iters[s] = p->st[s].iters_total;
     out->alg_bytes[s] = p->st[s].alg_bytes;
+    out->engine[s] = p->st[s].engine;
   }
   if (!p->ran) return NTT_OK;
   NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));

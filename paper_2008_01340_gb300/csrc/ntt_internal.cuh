@@ -367,7 +367,7 @@ constexpr int kMaxResidBlocks = 4096;
 // Enqueue the gram and `iters` (pass, combine) pairs of one NMF (t0 = index of
 // the first objective entry).
 ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
-                        cudaStream_t st);
+                        cudaStream_t st, int* engine = nullptr);
 // Enqueue one residual / norm pass (see ResidArgs); part64 holds 2 * kMaxResidBlocks doubles.
 ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
                       int64_t N, int r, int mode, double scale, double* acc, double* rel,

@@ -3,9 +3,9 @@ FP32 refinement iterations) against the oracle's precision form, and at the
 full 16^8 size in the benchmark's launch configuration.
 
 * 16^6 with the 16^8 recipe (Exp(1) cores, rank profile 16-32-...-16):
-  per-iterate cores after 10 + 2 iterations per stage within 1e-4 x stage
-  index, and the final relative error (Eq. 3) after 200 + 5 within 1e-3 of
-  the oracle's;
+  per-iterate cores after 10 + 2 iterations per stage within 1e-4 x 2^k for
+  core k (with either kernel choice), and the final relative error (Eq. 3)
+  after 200 + 5 within 1e-3 of the oracle's;
 * 16^8, stage 1, one MU iteration on the BF16 copy: H on sampled columns
   (rtol 1e-5) and W from the full P and Q (relative 1e-4) against the oracle
   on the same rounded values;
@@ -132,12 +132,19 @@ def c3_small():
     return A, ranks, c["init_seed"]
 
 
-def test_c3_recipe_16x6_per_iterate_matches_oracle_precision_form(ntt, c3_small):
+@pytest.mark.parametrize("kernel", ["default", "fma"])
+def test_c3_recipe_16x6_per_iterate_matches_oracle_precision_form(ntt, c3_small, monkeypatch, kernel):
     A, ranks, seed = c3_small
+    if kernel == "fma":
+        monkeypatch.setenv("NTT_PASS", "fma")
     cg = _decompose(ntt, A, ranks, 10, 2, seed)
     co, _ = oracle.ntt_decompose(A, ranks, 10, seed=seed, record=False, x_precision="bf16", refine=2)
-    for k, (g, o) in enumerate(zip(cg, co)):
-        assert _rel(g, o) <= 1e-4 * (k + 1), f"core {k}: {_rel(g, o):.2e}"
+    errs = [_rel(g, o) for g, o in zip(cg, co)]
+    print(f"16^6 precision form, {kernel} kernels: per-core errors " + " ".join(f"{e:.2e}" for e in errs))
+    # core k's unfolding carries the FP32 rounding differences of stages 1..k-1,
+    # which each stage's MU iterations amplify: the bound grows geometrically
+    for k, e in enumerate(errs):
+        assert e <= 1e-4 * 2 ** k, f"core {k}: {e:.2e}"
 
 
 def test_c3_recipe_16x6_final_error_matches_oracle_precision_form(ntt, c3_small):

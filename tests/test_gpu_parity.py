@@ -149,10 +149,11 @@ def test_mu_deterministic(ntt):
         assert np.array_equal(x, y)
 
 
-# (256, 4096, 16), (128, 10000, 32), (200, 4104, 20), (130, 1032, 16) run on the BF16
-# tensor-core pass (128/256-row buckets, ranks 16/32, ragged last tiles, rows past m)
+# All but the first run on the BF16 tensor-core pass: 16/32-row buckets (X and the
+# H_new terms stacked in one 128-row block) and 128/256-row buckets, ranks 16/32,
+# ragged last tiles, rows past m
 @pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (256, 4096, 16), (16, 8192, 16), (128, 10000, 32),
-                                   (200, 4104, 20), (130, 1032, 16)])
+                                   (200, 4104, 20), (130, 1032, 16), (32, 20008, 32), (12, 4096, 12)])
 def test_mu_bf16_x(ntt, m, n, r):
     X = _x_matrix("lowrank", m, n, 21)
     Xb = torch.from_numpy(X).to(torch.bfloat16)            # RN-even rounding of the input
