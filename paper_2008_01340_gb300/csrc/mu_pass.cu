@@ -101,17 +101,23 @@ static bool tc_enabled() {
 
 // BF16 X with 128 or 256 rows and rank bucket 16 or 32 runs on the BF16
 // tensor-core pass (kind::f16, FP32 accumulation, factors split in three BF16
-// terms); NTT_PASS=fma keeps the packed-FMA pass.
-static bool tcb_enabled() {
+// terms); NTT_PASS=fma keeps the packed-FMA pass.  Its stacked form for 16 and
+// 32 rows is selected only with NTT_PASS=tcb: on 16 x 268,435,456 (rank 16) it
+// ran 30.8 iterations/s against 52.3 for the grouped FMA pass -- that shape
+// moves 160 B of H per column against 32 B of X, and one CTA per SM with its
+// H loads in the epilogue leaves the latency exposed.
+static bool tcb_enabled(int MP) {
   const char* e = std::getenv("NTT_PASS");
-  return !(e && std::strcmp(e, "fma") == 0);
+  if (e && std::strcmp(e, "fma") == 0) return false;
+  if (MP <= 32) return e && std::strcmp(e, "tcb") == 0;
+  return true;
 }
 
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tc = 0;
   s->tcb = 0;
-  if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled()) {
+  if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP)) {
     s->tcb = 1;
     s->T = 128;
     const int64_t ntiles = (s->n + s->T - 1) / s->T;

@@ -279,9 +279,11 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16) {
   const int MP = group_mp_bucket((int)m), R = group_r_bucket(r);
   if (MP < 0 || R < 0) return false;
   if (xbf16 && (!gpass_bf16_supported(MP, R) || n % 8 != 0)) return false;
-  // BF16 stages the tensor-core pass covers stay on the single-problem path
+  // BF16 stages the tensor-core pass takes (128/256 rows by default, 16/32 rows
+  // with NTT_PASS=tcb) stay on the single-problem path
   const char* pe = std::getenv("NTT_PASS");
-  if (xbf16 && tcb_pass_supported(MP, R) && !(pe && std::strcmp(pe, "fma") == 0)) return false;
+  const bool fma = pe && std::strcmp(pe, "fma") == 0, tcb = pe && std::strcmp(pe, "tcb") == 0;
+  if (xbf16 && tcb_pass_supported(MP, R) && !fma && (MP >= 128 || tcb)) return false;
   const char* e = std::getenv("NTT_PLAN_ENGINE");
   if (e && std::strcmp(e, "pass") == 0) return false;
   if (e && std::strcmp(e, "group") == 0) return true;

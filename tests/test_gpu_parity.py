@@ -149,9 +149,9 @@ def test_mu_deterministic(ntt):
         assert np.array_equal(x, y)
 
 
-# All but the first run on the BF16 tensor-core pass: 16/32-row buckets (X and the
-# H_new terms stacked in one 128-row block) and 128/256-row buckets, ranks 16/32,
-# ragged last tiles, rows past m
+# (256, 4096, 16), (128, 10000, 32), (200, 4104, 20), (130, 1032, 16) run on the
+# BF16 tensor-core pass (128/256-row buckets, ranks 16/32, ragged last tiles,
+# rows past m); the 16/32-row shapes on the FMA passes by default
 @pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (256, 4096, 16), (16, 8192, 16), (128, 10000, 32),
                                    (200, 4104, 20), (130, 1032, 16), (32, 20008, 32), (12, 4096, 12)])
 def test_mu_bf16_x(ntt, m, n, r):
@@ -440,3 +440,21 @@ def test_mu_bf16_tensor_core_pass_long_accumulation(ntt):
         assert np.allclose(Hg[:, sel], H1c[:, sel - c0], rtol=1e-5, atol=1e-7 * H1c.max())
     W1 = np.maximum(0.0, W0 * P / (W0 @ Q + 1e-12))
     assert _fro_rel(Wd.cpu().numpy(), W1) <= REL_ITERATE
+
+
+@pytest.mark.parametrize("m,n,r", [(16, 8192, 16), (32, 20008, 32), (12, 4096, 12), (24, 40960, 20)])
+def test_mu_bf16_stacked_tensor_core_form(ntt, monkeypatch, m, n, r):
+    """The stacked form of the BF16 tensor-core pass (16/32 rows; opt-in with
+    NTT_PASS=tcb) against the oracle on the BF16-rounded X, 10 iterations."""
+    monkeypatch.setenv("NTT_PASS", "tcb")
+    X = _x_matrix("lowrank", m, n, 31)
+    Xb = torch.from_numpy(X).to(torch.bfloat16)
+    W0 = synth.uniform_matrix((m, r), 32)
+    H0 = synth.uniform_matrix((r, n), 33)
+    Wd = torch.from_numpy(W0).cuda()
+    Hd = torch.from_numpy(H0).cuda()
+    ntt.nmf_mu_step(Xb.cuda(), Wd, Hd, 10)
+    torch.cuda.synchronize()
+    Wo, Ho, _ = oracle.nmf_mu(Xb.to(torch.float64).numpy(), W0, H0, 10)
+    assert _fro_rel(Wd.cpu().numpy(), Wo) <= REL_ITERATE
+    assert _fro_rel(Hd.cpu().numpy(), Ho) <= REL_ITERATE
