@@ -233,15 +233,20 @@ def run_stage1_small(args):
     from paper_2008_01340_gb300 import _build
 
     _build.build()
-    m, n, r = 32, 1 << 22, 8
-    X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
+    if args.case == "tcb_small":
+        # stage-2 shape of the precision form on BF16 X: the tensor-core pass
+        m, n, r = 256, 1 << 21, 32
+        X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).to(torch.bfloat16).cuda()
+    else:
+        m, n, r = 32, 1 << 22, 8
+        X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
     W = torch.from_numpy(synth.uniform_matrix((m, r), 2)).cuda()
     H = torch.from_numpy(synth.uniform_matrix((r, n), 3)).cuda()
     if args.engine == "group":
         ws = ntt.empty_workspace(ntt.nmf_mu_many_workspace_size([(m, n, r)]))
         run = lambda k: ntt.nmf_mu_many([X], [W], [H], k, workspace=ws)
     else:
-        ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r))
+        ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r, "bf16" if X.dtype == torch.bfloat16 else "f32"))
         run = lambda k: ntt.nmf_mu_step(X, W, H, k, workspace=ws)
     for _ in range(args.warmup):
         run(1)
@@ -252,8 +257,8 @@ def run_stage1_small(args):
     e1.record()
     torch.cuda.synchronize()
     it = e0.elapsed_time(e1) / args.steps / 1e3
-    gb = (m * n * 4 + 8 * r * n) / it / 1e9
-    print(json.dumps({"case": "stage1_small", "engine": args.engine, "m": m, "n": n, "r": r, "ms_per_iter": it * 1e3,
+    gb = (m * n * X.element_size() + 8 * r * n) / it / 1e9
+    print(json.dumps({"case": args.case, "engine": args.engine, "m": m, "n": n, "r": r, "ms_per_iter": it * 1e3,
                       "alg_GBps": round(gb, 1)}), flush=True)
     return 0
 
@@ -445,14 +450,14 @@ def main():
                          "c5_serving: 1000 Poisson requests through the serving form")
     ap.add_argument("--engine", default="pass", choices=["pass", "group"],
                     help="stage1_small: single-problem pass or grouped engine")
-    ap.add_argument("--case", default="full", choices=["full", "stage1_small"],
+    ap.add_argument("--case", default="full", choices=["full", "stage1_small", "tcb_small"],
                     help="stage1_small: MU iterations of the stage-1 shape on 32 x 4194304 "
                          "(512 MB, larger than L2) for profiler captures")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
-    if args.case == "stage1_small":
+    if args.case in ("stage1_small", "tcb_small"):
         return run_stage1_small(args)
     if args.workload == "c4_batched":
         return run_batched(args)
