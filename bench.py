@@ -47,8 +47,9 @@ WORKLOAD = "c2_32x6"
 FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 flop x max SM clock
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture, valid
-# only for the kernel source it was measured on (hash of mu_pass_impl.cuh).
-NCU_TRAFFIC = {"kernel_sha": "194b83740c3bc425", "bytes_per_launch": 6.31e9}   # 188 B/column on 32 x 4194304, x 33554432 columns
+# only for the engine and kernel source it was measured on (hash of that file).
+NCU_TRAFFIC = {"engine": "fma_pass", "kernel_file": "mu_pass_impl.cuh", "kernel_sha": "194b83740c3bc425",
+               "bytes_per_launch": 6.31e9}   # 188 B/column on 32 x 4194304, x 33554432 columns
 
 
 def _env_int(name, default):
@@ -58,8 +59,8 @@ def _env_int(name, default):
         return default
 
 
-def _kernel_sha():
-    p = os.path.join(ROOT, "paper_2008_01340_gb300", "csrc", "mu_pass_impl.cuh")
+def _kernel_sha(fname):
+    p = os.path.join(ROOT, "paper_2008_01340_gb300", "csrc", fname)
     with open(p, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
@@ -565,10 +566,11 @@ def main():
     flops = 4.0 * st1["n"] * (st1["m"] * st1["r"] + st1["r"] ** 2)
     tflops = flops / per_iter_s / 1e12
     traffic = None
-    if NCU_TRAFFIC["kernel_sha"] == _kernel_sha() and wl == WORKLOAD:
+    if (NCU_TRAFFIC["engine"] == st1.get("engine") and wl == WORKLOAD
+            and NCU_TRAFFIC["kernel_sha"] == _kernel_sha(NCU_TRAFFIC["kernel_file"])):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     kernel_of = {"fma_pass": "mu_pass_kernel", "grouped": "gpass_kernel", "tc_bf16": "mu_pass_tcb_kernel",
-                 "tc_tf32": "mu_pass_tc_kernel"}
+                 "tc_tf32": "mu_pass_tc_kernel", "fma_narrow": "mu_pass_narrow_kernel"}
     kname = (f"{kernel_of.get(st1.get('engine'), st1.get('engine'))}<m={st1['m']},r={st1['r']},"
              f"{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
              f"stage {dom + 1} ({st1['m']} x {st1['n']}, r={st1['r']})")

@@ -94,6 +94,7 @@ typedef struct {
 #define NTT_ENGINE_GROUPED 1          /* grouped engine (register-tiled FMA pass) */
 #define NTT_ENGINE_TC_BF16 2          /* BF16-X tensor-core pass (tcgen05 kind::f16) */
 #define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (opt-in, NTT_PASS=tc) */
+#define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);

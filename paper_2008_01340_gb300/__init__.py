@@ -113,7 +113,7 @@ class _Stats(ctypes.Structure):
     ]
 
 
-ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32"}
+ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow"}
 
 
 _lib_handle = None

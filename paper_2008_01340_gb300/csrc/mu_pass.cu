@@ -113,10 +113,18 @@ static bool tcb_enabled(int MP) {
   return true;
 }
 
+// FP32 X with at most 32 rows at rank bucket 8 runs on the warp-streamed pass
+// (mu_pass_narrow.cu); NTT_PASS=wide keeps the generic pass.
+static bool narrow_enabled() {
+  const char* e = std::getenv("NTT_PASS");
+  return !(e && std::strcmp(e, "wide") == 0);
+}
+
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tc = 0;
   s->tcb = 0;
+  s->narrow = 0;
   if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP)) {
     s->tcb = 1;
     s->T = 128;
@@ -130,6 +138,16 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled()) {
     s->tc = 1;
     s->T = 128;
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+    return;
+  }
+  if (s->tma && !s->bf16 && narrow_pass_supported(s->MP, s->R) && narrow_enabled()) {
+    s->narrow = 1;
+    s->T = 256;   // 8 warps x 32-column boxes per CTA round
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
     int64_t grid = num_sms > 0 ? num_sms : 152;
     if (grid > ntiles) grid = ntiles;
@@ -169,22 +187,25 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.m};
     cuuint64_t strides[1] = {(cuuint64_t)(s.n * xb)};
-    // tensor-core pass: 32-column boxes (128 bytes), 128-byte swizzle of 32-byte chunks
-    cuuint32_t box[2] = {(cuuint32_t)(s.tc ? 32 : s.T), (cuuint32_t)br};
+    // tensor-core pass: 32-column boxes (128 bytes), 128-byte swizzle of 32-byte chunks;
+    // narrow pass: 32-column boxes, 128-byte swizzle of 16-byte chunks
+    cuuint32_t box[2] = {(cuuint32_t)(s.tc || s.narrow ? 32 : s.T), (cuuint32_t)br};
     cuuint32_t es[2] = {1, 1};
     CUresult e = fn(mx, s.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     2, const_cast<void*>(X), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    s.tc ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    s.tc ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B
+                         : (s.narrow ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE),
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
   }
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.r};
     cuuint64_t strides[1] = {(cuuint64_t)(s.n * 4)};
-    cuuint32_t box[2] = {(cuuint32_t)s.T, (cuuint32_t)s.R};
+    cuuint32_t box[2] = {(cuuint32_t)(s.narrow ? 32 : s.T), (cuuint32_t)s.R};
     cuuint32_t es[2] = {1, 1};
     CUresult e = fn(mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(H), dims, strides,
-                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    s.narrow ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
   }
@@ -195,6 +216,7 @@ cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CU
                            const CUtensorMap& mh, cudaStream_t st) {
   if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
   if (s.tc) return launch_mu_pass_tc(s, d, eps, mx, mh, st);
+  if (s.narrow) return launch_mu_pass_narrow(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \
   case MPV:                                                                 \
     return s.bf16 ? launch_pass_bf16_m##MPV(s.R, s, d, eps, mx, mh, st)    \

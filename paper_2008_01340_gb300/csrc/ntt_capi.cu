@@ -35,7 +35,9 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
   std::memset(&mh, 0, sizeof(mh));
   MuShape s = shp;
   mu_finalize_shape(&s, dev.X, dev.H, device_sms());
-  if (engine) *engine = s.tcb ? NTT_ENGINE_TC_BF16 : (s.tc ? NTT_ENGINE_TC_TF32 : NTT_ENGINE_FMA_PASS);
+  if (engine)
+    *engine = s.tcb ? NTT_ENGINE_TC_BF16
+                    : (s.tc ? NTT_ENGINE_TC_TF32 : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS));
   if (s.tma) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
   for (int t = 0; t < iters; ++t) {
     NTT_CUDA_TRY_NS(launch_mu_pass(s, dev, eps, mx, mh, st));

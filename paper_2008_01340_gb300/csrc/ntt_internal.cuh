@@ -282,6 +282,7 @@ struct MuShape {
   int tma = 0;       // X/H tiles loaded by TMA (else cooperative loads)
   int tc = 0;        // tensor-core (tcgen05) pass instead of the FMA pass
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
+  int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
   size_t smem = 0;   // dynamic shared memory of the pass kernel
   int part_stride() const { return (MP + R) * R; }
 };
@@ -323,6 +324,10 @@ cudaError_t launch_gram(const MuShape& s, const MuDev& d, cudaStream_t st);
 // BF16-X tensor-core pass (tcgen05 kind::f16) for 128 or 256 rows and rank buckets 16, 32.
 bool tcb_pass_supported(int MP, int R);
 cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
+// Warp-streamed FMA pass for 16/32-row buckets at rank bucket 8 (FP32 X, TMA-aligned).
+bool narrow_pass_supported(int MP, int R);
+cudaError_t launch_mu_pass_narrow(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
+                                  const CUtensorMap& mh, cudaStream_t st);
 
 cudaError_t launch_uniform(uint64_t key, int64_t count, float* out, cudaStream_t st);
 cudaError_t launch_cast_bf16(const float* in, __nv_bfloat16* out, int64_t count, cudaStream_t st);

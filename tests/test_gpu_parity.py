@@ -378,6 +378,40 @@ def test_tensor_core_and_fma_passes_agree(ntt, m, n, r, monkeypatch):
         assert _fro_rel(Hg, Ho) <= REL_ITERATE
 
 
+# (m, n, r): 32 and 16-row buckets, m and r below the bucket, a ragged last
+# 32-column box, fewer boxes than warps, and many boxes per warp
+@pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (20, 36004, 5), (16, 8196, 8), (9, 100, 2),
+                                   (32, 64, 8), (32, 2_000_000, 8), (1, 4096, 1)])
+def test_narrow_and_wide_passes_agree(ntt, m, n, r, monkeypatch):
+    """The warp-streamed pass (FP32 X, <= 32 rows, rank <= 8: the default there)
+    and the generic pass (NTT_PASS=wide) both match the oracle's iterates within
+    the FP32 tolerance, and the narrow pass repeats bitwise."""
+    X = _x_matrix("lowrank", m, n, 91 + m)
+    W0 = synth.uniform_matrix((m, r), 92)
+    H0 = synth.uniform_matrix((r, n), 93)
+    Wn, Hn, on = _run_gpu_mu(ntt, X, W0, H0, 10)
+    Wn2, Hn2, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    assert np.array_equal(Wn, Wn2) and np.array_equal(Hn, Hn2)
+    monkeypatch.setenv("NTT_PASS", "wide")
+    Ww, Hw, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    monkeypatch.delenv("NTT_PASS")
+    Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
+    for Wg, Hg in ((Wn, Hn), (Ww, Hw)):
+        assert _fro_rel(Wg, Wo) <= REL_ITERATE
+        assert _fro_rel(Hg, Ho) <= REL_ITERATE
+        assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    assert np.allclose(on, tr, rtol=2e-3, atol=1e-6 * float(np.sum(X.astype(np.float64) ** 2)))
+
+
+def test_narrow_pass_reported_for_first_stage(ntt):
+    """A 32-row, rank-8 first stage of a plan runs on the narrow pass and says so."""
+    dims, ranks = (32, 16, 16, 8), (1, 8, 8, 4, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=5)
+    cores, stats, *_ = _decompose(ntt, A, ranks, 5, 3)
+    assert stats["status"] == "NTT_OK"
+    assert stats["stages"][0]["engine"] == "fma_narrow"
+
+
 @pytest.mark.parametrize("x_dtype,refine", [("f32", 0), ("bf16", 3)])
 def test_plan_engine_routes_agree(ntt, monkeypatch, x_dtype, refine):
     """Stages with <= 256 rows and rank >= 16 run on the grouped engine by default;
