@@ -18,28 +18,35 @@
 //   * X and H boxes use the 128-byte swizzle (16-byte chunk index XOR row
 //     mod 8), so eight lanes reading one column quad of eight different rows
 //     touch eight different bank groups;
-//   * lane = (row split sa = lane & 7, column quad cq = lane >> 3).  A lane
-//     keeps W rows sa, sa + 8, ... in registers with its ranks in the order
-//     slot i -> rank i ^ sa; the reduce-scatter of Y over the eight row splits
-//     is then three shuffle steps (lane xor 4, 2, 1) that always keep the low
-//     half of the slots, and leaves lane sa with Y of rank sa for its four
-//     columns;
-//   * the H update of (rank sa, 4 columns) reads the eight H rows of those
+//   * lane = (row split sa = lane & 7, column group cq = lane >> 3, CPL
+//     columns per group).  A lane keeps W rows sa, sa + 8, ... in registers
+//     with its ranks in the order slot i -> rank i ^ sa; the reduce-scatter of
+//     Y over the eight row splits is then three shuffle steps (lane xor 4, 2,
+//     1) that always keep the low half of the slots, and leaves lane sa with Y
+//     of rank sa for its CPL columns;
+//   * the H update of (rank sa, CPL columns) reads the eight H rows of those
 //     columns from shared memory, stores H_new straight to global memory, and
 //     takes H_new of the other ranks from lanes sa ^ i by shuffles, so P and Q
-//     accumulate in registers without a second read of X.
+//     accumulate in registers without a second read of X;
+//   * packed FP32x2 FMAs pair slots (2j, 2j + 1), so the X value of a column
+//     is the one broadcast operand of both Y = W^T X and P = X H_new^T, and
+//     the P, Q partials take 2 x (4 RPL + 4) registers; at 168 registers a
+//     lane, 12 warps fit on an SM.
 #include "ntt_internal.cuh"
 
 namespace ntt {
 namespace {
 
-constexpr int kNarrowWarps = 8;
-constexpr int kNarrowThreads = kNarrowWarps * 32;
 constexpr int kBoxCols = 32;   // one 128-byte swizzle span of FP32
 
-template <int MP_>
+template <int MP_, int NW_, int CPL_>
 struct NarrowCfg {
   static constexpr int MP = MP_;
+  static constexpr int NW = NW_;                // warps per CTA
+  static constexpr int CPL = CPL_;              // columns per lane per step (2 or 4)
+  static constexpr int NSTEP = kBoxCols / (4 * CPL);   // steps per box
+  static constexpr int kNarrowWarps = NW;
+  static constexpr int kNarrowThreads = NW * 32;
   static constexpr int RPL = MP / 8;            // X rows per lane
   static constexpr int XBOX = MP * 128;         // bytes of one X box
   static constexpr int HBOX = 8 * 128;          // bytes of one H box (rank bucket 8)
@@ -52,6 +59,7 @@ struct NarrowCfg {
   static constexpr int RED_BYTES = kNarrowWarps * (MP + 8) * 8 * 4;
   static constexpr int SMEM = BAR_OFF + kNarrowWarps * STAGES * 8 + 1024;   // + alignment slack
   static_assert(MP == 16 || MP == 32, "row bucket");
+  static_assert(CPL == 2 || CPL == 4, "columns per lane");
   static_assert(STAGE % 1024 == 0, "swizzle atoms of 1024 bytes");
   static_assert(STAGES >= 2, "pipeline depth");
   static_assert(RED_BYTES <= BAR_OFF, "reduction scratch");
@@ -70,15 +78,35 @@ struct NarrowParams {
   float eps;
 };
 
+// CPL consecutive floats of shared memory (16- or 8-byte aligned) into registers.
+template <int N>
+__device__ __forceinline__ void lds_cols(const uint8_t* p, float* v) {
+  if constexpr (N == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void stg_cols(float* p, const float* v) {
+  if constexpr (N == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int mask) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
 }
 
 template <class C>
-__global__ void __launch_bounds__(kNarrowThreads, 1)
+__global__ void __launch_bounds__(C::kNarrowThreads, 1)
 mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmH,
                       const NarrowParams p) {
   constexpr int RPL = C::RPL, MP = C::MP, S = C::STAGES;
+  constexpr int kNarrowWarps = C::kNarrowWarps, kNarrowThreads = C::kNarrowThreads;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -130,10 +158,13 @@ mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
     }
   }
 
-  float2 accP[RPL][8];   // (even, odd column) partials of P[sa + 8 ii][sa ^ i]
-  float2 accQ[8];        // partials of Q[sa][sa ^ i]
+  // partials of (P[sa + 8 ii][sa ^ 2j], P[sa + 8 ii][sa ^ (2j + 1)]) in accP[ii][j],
+  // of (Q[sa][sa ^ 2j], Q[sa][sa ^ (2j + 1)]) in accQ[j]
+  constexpr int NA = 4, CPL = C::CPL;
+  float2 accP[RPL][NA];
+  float2 accQ[NA];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < NA; ++i) {
     accQ[i] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int ii = 0; ii < RPL; ++ii) accP[ii][i] = make_float2(0.0f, 0.0f);
@@ -151,79 +182,91 @@ mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
     const uint8_t* xs = wbuf + s * C::STAGE;
     const uint8_t* hs = xs + C::XBOX;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int q = 4 * half + cq;   // column quad within the box
-      // X rows sa + 8 ii (row mod 8 = sa: physical chunk q ^ sa)
-      float4 x[RPL];
+    for (int step = 0; step < C::NSTEP; ++step) {
+      // this lane's CPL columns: byte offset cb in a 128-byte row, 16-byte chunk cb >> 4
+      const int cb = (step * 4 + cq) * CPL * 4;
+      const int ch = cb >> 4, cw = cb & 15;
+      // X rows sa + 8 ii (row mod 8 = sa: physical chunk ch ^ sa)
+      float xr[RPL][CPL];
 #pragma unroll
       for (int ii = 0; ii < RPL; ++ii)
-        x[ii] = *reinterpret_cast<const float4*>(xs + (sa + 8 * ii) * 128 + ((q ^ sa) << 4));
-      // Y partials over this lane's rows: slot i = rank i ^ sa, columns (0,1) and (2,3)
-      float2 y[8][2];
+        lds_cols<CPL>(xs + (sa + 8 * ii) * 128 + ((ch ^ sa) << 4) + cw, xr[ii]);
+      // Y partials in rank pairs: y2[j][c] = (slot 2j, slot 2j + 1) at column c
+      float2 y2[4][CPL];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) y[i][0] = y[i][1] = make_float2(0.0f, 0.0f);
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int ii = 0; ii < RPL; ++ii) {
-        const float2 x01 = make_float2(x[ii].x, x[ii].y), x23 = make_float2(x[ii].z, x[ii].w);
+        for (int c = 0; c < CPL; ++c) y2[j][c] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float2 wi = make_float2(w[ii][i], w[ii][i]);
-          y[i][0] = __ffma2_rn(wi, x01, y[i][0]);
-          y[i][1] = __ffma2_rn(wi, x23, y[i][1]);
+      for (int ii = 0; ii < RPL; ++ii)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const float2 xb = make_float2(xr[ii][c], xr[ii][c]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            y2[j][c] = __ffma2_rn(make_float2(w[ii][2 * j], w[ii][2 * j + 1]), xb, y2[j][c]);
         }
-      }
       // reduce-scatter over the row splits: the partner's upper slots hold the
       // ranks of this lane's lower slots, in the same order
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) y[t][h] = __fadd2_rn(y[t][h], shfl_xor2(y[4 + t][h], 4));
-#pragma unroll
       for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) y[t][h] = __fadd2_rn(y[t][h], shfl_xor2(y[2 + t][h], 2));
+        for (int c = 0; c < CPL; ++c) y2[t][c] = __fadd2_rn(y2[t][c], shfl_xor2(y2[2 + t][c], 4));
 #pragma unroll
-      for (int h = 0; h < 2; ++h) y[0][h] = __fadd2_rn(y[0][h], shfl_xor2(y[1][h], 1));
+      for (int c = 0; c < CPL; ++c) y2[0][c] = __fadd2_rn(y2[0][c], shfl_xor2(y2[1][c], 2));
+      float yv[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) yv[c] = y2[0][c].x + __shfl_xor_sync(0xffffffffu, y2[0][c].y, 1);
 
-      // H rows sa ^ i of the four columns (rows < 8: physical chunk q ^ row)
-      float4 h0;
-      float2 gh01 = make_float2(0.0f, 0.0f), gh23 = make_float2(0.0f, 0.0f);
+      // G H for rank sa from H rows sa ^ i (rows < 8: physical chunk ch ^ row)
+      // (column pairs, even and odd i in separate chains)
+      float h0[CPL];
+      float2 ga[CPL / 2], gb[CPL / 2];
+#pragma unroll
+      for (int t = 0; t < CPL / 2; ++t) ga[t] = gb[t] = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int row = sa ^ i;
-        const float4 hv = *reinterpret_cast<const float4*>(hs + row * 128 + ((q ^ row) << 4));
-        if (i == 0) h0 = hv;
+        float hv[CPL];
+        lds_cols<CPL>(hs + row * 128 + ((ch ^ row) << 4) + cw, hv);
+        if (i == 0)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) h0[c] = hv[c];
         const float2 gi = make_float2(g[i], g[i]);
-        gh01 = __ffma2_rn(gi, make_float2(hv.x, hv.y), gh01);
-        gh23 = __ffma2_rn(gi, make_float2(hv.z, hv.w), gh23);
+#pragma unroll
+        for (int t = 0; t < CPL / 2; ++t) {
+          if (i & 1)
+            gb[t] = __ffma2_rn(gi, make_float2(hv[2 * t], hv[2 * t + 1]), gb[t]);
+          else
+            ga[t] = __ffma2_rn(gi, make_float2(hv[2 * t], hv[2 * t + 1]), ga[t]);
+        }
       }
-      float4 hn;
-      hn.x = fmaxf(0.0f, __fdividef(h0.x * y[0][0].x, gh01.x + p.eps));
-      hn.y = fmaxf(0.0f, __fdividef(h0.y * y[0][0].y, gh01.y + p.eps));
-      hn.z = fmaxf(0.0f, __fdividef(h0.z * y[0][1].x, gh23.x + p.eps));
-      hn.w = fmaxf(0.0f, __fdividef(h0.w * y[0][1].y, gh23.y + p.eps));
-      const int64_t col = (int64_t)box * kBoxCols + 4 * q;   // n % 4 == 0: whole quad in or out
-      if (sa < p.r && col < p.n)
-        *reinterpret_cast<float4*>(p.H + (int64_t)sa * p.n + col) = hn;
+      float hn[CPL];
+#pragma unroll
+      for (int t = 0; t < CPL / 2; ++t) {
+        const float2 gh = __fadd2_rn(ga[t], gb[t]);
+        hn[2 * t] = fmaxf(0.0f, __fdividef(h0[2 * t] * yv[2 * t], gh.x + p.eps));
+        hn[2 * t + 1] = fmaxf(0.0f, __fdividef(h0[2 * t + 1] * yv[2 * t + 1], gh.y + p.eps));
+      }
+      const int64_t col = (int64_t)box * kBoxCols + (cb >> 2);   // n % 4 == 0: whole group in or out
+      if (sa < p.r && col < p.n) stg_cols<CPL>(p.H + (int64_t)sa * p.n + col, hn);
 
-      // H_new of rank sa ^ i from lane ^ i; P and Q over these four columns
+      // H_new of ranks sa ^ 2j, sa ^ (2j + 1) from lanes ^ 2j, ^ (2j + 1); P and Q
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float4 hq = hn;
-        if (i > 0) {
-          hq.x = __shfl_xor_sync(0xffffffffu, hn.x, i);
-          hq.y = __shfl_xor_sync(0xffffffffu, hn.y, i);
-          hq.z = __shfl_xor_sync(0xffffffffu, hn.z, i);
-          hq.w = __shfl_xor_sync(0xffffffffu, hn.w, i);
-        }
-        const float2 q01 = make_float2(hq.x, hq.y), q23 = make_float2(hq.z, hq.w);
+      for (int j = 0; j < 4; ++j) {
+        float2 hp[CPL];
 #pragma unroll
-        for (int ii = 0; ii < RPL; ++ii) {
-          accP[ii][i] = __ffma2_rn(make_float2(x[ii].x, x[ii].y), q01, accP[ii][i]);
-          accP[ii][i] = __ffma2_rn(make_float2(x[ii].z, x[ii].w), q23, accP[ii][i]);
+        for (int c = 0; c < CPL; ++c) {
+          hp[c].x = j == 0 ? hn[c] : __shfl_xor_sync(0xffffffffu, hn[c], 2 * j);
+          hp[c].y = __shfl_xor_sync(0xffffffffu, hn[c], 2 * j + 1);
         }
-        accQ[i] = __ffma2_rn(make_float2(hn.x, hn.y), q01, accQ[i]);
-        accQ[i] = __ffma2_rn(make_float2(hn.z, hn.w), q23, accQ[i]);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+          for (int ii = 0; ii < RPL; ++ii)
+            accP[ii][j] = __ffma2_rn(make_float2(xr[ii][c], xr[ii][c]), hp[c], accP[ii][j]);
+          accQ[j] = __ffma2_rn(make_float2(hn[c], hn[c]), hp[c], accQ[j]);
+        }
       }
     }
     __syncwarp();   // every lane is done with this stage
@@ -251,14 +294,15 @@ mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
   constexpr int E = (MP + 8) * 8;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
+    const int ai = i / 2;   // slot i is half (i & 1) of pair i / 2
 #pragma unroll
     for (int ii = 0; ii < RPL; ++ii) {
-      float v = accP[ii][i].x + accP[ii][i].y;
+      float v = (i & 1) ? accP[ii][ai].y : accP[ii][ai].x;
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
       if (cq == 0) red[warp * E + (sa + 8 * ii) * 8 + (sa ^ i)] = v;
     }
-    float v = accQ[i].x + accQ[i].y;
+    float v = (i & 1) ? accQ[ai].y : accQ[ai].x;
     v += __shfl_xor_sync(0xffffffffu, v, 8);
     v += __shfl_xor_sync(0xffffffffu, v, 16);
     if (cq == 0) red[warp * E + (MP + sa) * 8 + (sa ^ i)] = v;
@@ -294,7 +338,7 @@ cudaError_t launch_narrow_cfg(const MuShape& s, const MuDev& d, float eps, const
   p.r = s.r;
   p.nbox = (int)((s.n + kBoxCols - 1) / kBoxCols);
   p.eps = eps;
-  mu_pass_narrow_kernel<C><<<s.grid, kNarrowThreads, C::SMEM, st>>>(mx, mh, p);
+  mu_pass_narrow_kernel<C><<<s.grid, C::kNarrowThreads, C::SMEM, st>>>(mx, mh, p);
   return cudaGetLastError();
 }
 
@@ -305,8 +349,12 @@ bool narrow_pass_supported(int MP, int R) { return (MP == 16 || MP == 32) && R =
 cudaError_t launch_mu_pass_narrow(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                                   const CUtensorMap& mh, cudaStream_t st) {
   if (s.R != 8) return cudaErrorInvalidValue;
-  if (s.MP == 16) return launch_narrow_cfg<NarrowCfg<16>>(s, d, eps, mx, mh, st);
-  if (s.MP == 32) return launch_narrow_cfg<NarrowCfg<32>>(s, d, eps, mx, mh, st);
+  // 32 rows: 12 warps x 4 columns per lane (168 registers); measured on
+  // 32 x 4,194,304 against 8 warps (0.193 vs 0.213 ms per iteration) and
+  // against 2 columns per lane at 12 or 16 warps (0.199, 0.206 ms).
+  // 16 rows: 16 warps x 2 columns per lane (128 registers).
+  if (s.MP == 16) return launch_narrow_cfg<NarrowCfg<16, 16, 2>>(s, d, eps, mx, mh, st);
+  if (s.MP == 32) return launch_narrow_cfg<NarrowCfg<32, 12, 4>>(s, d, eps, mx, mh, st);
   return cudaErrorInvalidValue;
 }
 
