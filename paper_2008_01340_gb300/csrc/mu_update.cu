@@ -1,7 +1,7 @@
 // Cross-CTA reduction of the pass partials and the W half of the MU iteration.
 //
 //   [P ; Q] = sum over pass CTAs of their partials            (fixed order)
-//   W      <- max(0, W o P / (W Q + eps))                     (spec W update)
+//   W      <- max(0, W o P / (W Q + eps))                     (Lee-Seung W update)
 //   G_W    <- W^T W                                           (Gram, Algorithm 4)
 //   f      <- 1/2 (||X||^2 - 2 <W, P> + <G_W, Q>)              (objective, FP64)
 //
@@ -34,20 +34,6 @@ struct CombineParams {
   int blk;   // > 0: W^T W and H H^T masked to diagonal blocks of this size
 };
 
-// Deterministic FP64 block sum of one value per thread (tree over smem).
-__device__ double block_sum_f64(double v, double* sh) {
-  const int tid = threadIdx.x;
-  sh[tid] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (tid < s) sh[tid] += sh[tid + s];
-    __syncthreads();
-  }
-  const double out = sh[0];
-  __syncthreads();
-  return out;
-}
-
 // G = W^T W (R x R, zero outside r x r) from W (m x r) by the whole block.
 // Eight independent partial sums per entry (fixed order) keep the FMA chain short.
 // blk > 0 keeps only the diagonal blk x blk blocks: the columns of W are then
@@ -71,6 +57,37 @@ __device__ void gram_block(const float* W, int m, int r, int R, float* G, float*
   }
 }
 
+// W <- max(0, W o P / (W Q + eps)) for the rows of W in shared memory (in place;
+// a thread owns whole rows).  RM bounds the rank so the rank loops unroll to the
+// padded bucket; the sum over j runs in index order.  blk > 0 keeps Q's diagonal
+// blk x blk blocks only.
+template <int RM>
+__device__ __forceinline__ void w_update_rows(const float* red_s, float* Wn, int m, int r, int R, int MP,
+                                              int blk, float eps) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    float w[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) w[k] = (k < r) ? Wn[i * r + k] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < RM; ++k) {
+      if (k < r) {
+        float wq = 0.0f;
+        if (blk <= 0) {
+#pragma unroll
+          for (int j = 0; j < RM; ++j)
+            if (j < r) wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
+        } else {
+          const int g = k / blk;
+#pragma unroll
+          for (int j = 0; j < RM; ++j)
+            if (j < r && j / blk == g) wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
+        }
+        Wn[i * r + k] = fmaxf(0.0f, __fdiv_rn(w[k] * red_s[i * R + k], wq + eps));
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombineParams p) {
   extern __shared__ float sm[];
   __shared__ float chunk[kChunks][kEntriesPerBlock];
@@ -89,16 +106,29 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
     const int b1 = min(p.nb, b0 + per);
     float s = 0.0f;
     if (e < E) {
-#pragma unroll 8
-      for (int b = b0; b < b1; ++b) s += __ldcg(&p.part[(size_t)b * E + e]);
+      // batches of eight independent loads, summed in partial order
+      constexpr int U = 8;
+      for (int bb = b0; bb < b1; bb += U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = bb + u < b1 ? __ldcg(&p.part[(size_t)(bb + u) * E + e]) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (bb + u < b1) s += v[u];
+      }
     }
     chunk[j][el] = s;
     __syncthreads();
     if (tid < kEntriesPerBlock && e < E) {
-      double tot = 0.0;
+      // pairwise FP64 sum of the eight chunks (fixed order)
+      double t[kChunks];
 #pragma unroll
-      for (int c = 0; c < kChunks; ++c) tot += (double)chunk[c][tid];
-      p.red[e] = (float)tot;
+      for (int c = 0; c < kChunks; ++c) t[c] = (double)chunk[c][tid];
+#pragma unroll
+      for (int w = 1; w < kChunks; w *= 2)
+#pragma unroll
+        for (int c = 0; c + w < kChunks; c += 2 * w) t[c] += t[c + w];
+      p.red[e] = (float)t[0];
     }
   }
   __threadfence();
@@ -111,44 +141,73 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
   // ---- 2. last block: W update, Gram, objective
   const int m = p.m, r = p.r, R = p.R, MP = p.MP;
   float* red_s = sm;                 // E
-  float* Wn = red_s + E;             // m * r
+  float* Wn = red_s + E;             // m * r: the current W, updated in place row by row
   float* Gs = Wn + m * r;            // R * R
-  for (int e = tid; e < E; e += blockDim.x) red_s[e] = __ldcg(&p.red[e]);
-  __syncthreads();
-  for (int i = tid; i < m; i += blockDim.x) {
-    float w[NTT_MAX_RANK];
+  // [P ; Q] and W into shared memory, eight independent loads per batch
+  {
+    constexpr int U = 8;
+    const int mr = m * r;
+    for (int e0 = tid; e0 < E; e0 += U * kAuxThreads) {
+      float v[U];
 #pragma unroll
-    for (int k = 0; k < NTT_MAX_RANK; ++k) w[k] = (k < r) ? p.W[i * r + k] : 0.0f;
+      for (int u = 0; u < U; ++u) v[u] = e0 + u * kAuxThreads < E ? __ldcg(&p.red[e0 + u * kAuxThreads]) : 0.0f;
 #pragma unroll
-    for (int k = 0; k < NTT_MAX_RANK; ++k) {
-      if (k < r) {
-        float wq = 0.0f;
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * kAuxThreads < E) red_s[e0 + u * kAuxThreads] = v[u];
+    }
+    for (int e0 = tid; e0 < mr; e0 += U * kAuxThreads) {
+      float v[U];
 #pragma unroll
-        for (int j = 0; j < NTT_MAX_RANK; ++j)
-          if (j < r && (p.blk <= 0 || j / p.blk == k / p.blk))
-            wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
-        Wn[i * r + k] = fmaxf(0.0f, __fdiv_rn(w[k] * red_s[i * R + k], wq + p.eps));
-      }
+      for (int u = 0; u < U; ++u) v[u] = e0 + u * kAuxThreads < mr ? p.W[e0 + u * kAuxThreads] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * kAuxThreads < mr) Wn[e0 + u * kAuxThreads] = v[u];
     }
   }
+  __syncthreads();
+  if (R <= 8)
+    w_update_rows<8>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
+  else if (R <= 16)
+    w_update_rows<16>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
+  else
+    w_update_rows<NTT_MAX_RANK>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
   __syncthreads();
   for (int e = tid; e < m * r; e += blockDim.x) p.W[e] = Wn[e];
   gram_block(Wn, m, r, R, p.G, Gs, p.blk);
   __syncthreads();
   if (p.obj) {
-    double a = 0.0, b = 0.0;
-    for (int e = tid; e < m * r; e += blockDim.x) {
-      const int i = e / r, k = e % r;
-      a += (double)Wn[e] * (double)red_s[i * R + k];
-    }
+    // <W, P> by rows (two FP64 chains), <G_W, Q> by entries; one reduction of both
+    double a0 = 0.0, a1 = 0.0, b = 0.0;
+    for (int i = tid; i < m; i += blockDim.x)
+      for (int k = 0; k < r; ++k) {
+        const double t = (double)Wn[i * r + k] * (double)red_s[i * R + k];
+        if (k & 1) a1 += t; else a0 += t;
+      }
     for (int kl = tid; kl < r * r; kl += blockDim.x) {
-      const int k = kl / r, l = kl % r;
+      const int k = kl / r, l = kl - k * r;
       if (p.blk <= 0 || k / p.blk == l / p.blk)
         b += (double)Gs[k * R + l] * (double)red_s[(MP + k) * R + l];
     }
-    const double A = block_sum_f64(a, dsh);
-    const double B = block_sum_f64(b, dsh);
-    if (tid == 0) p.obj[p.t] = 0.5 * (*p.xnorm2 - 2.0 * A + B);
+    double A = a0 + a1, B = b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the warp sum
+      A += __shfl_xor_sync(0xffffffffu, A, o);
+      B += __shfl_xor_sync(0xffffffffu, B, o);
+    }
+    const int nw = blockDim.x / 32;
+    if ((tid & 31) == 0) {
+      dsh[tid / 32] = A;
+      dsh[nw + tid / 32] = B;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double As = 0.0, Bs = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        As += dsh[w];
+        Bs += dsh[nw + w];
+      }
+      p.obj[p.t] = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
+    }
   }
   if (tid == 0) *p.ticket = 0u;
 }
