@@ -81,6 +81,34 @@ __global__ void __launch_bounds__(kAuxThreads) group_gram_kernel(const GComb* co
   group_gram(c.W, c.m, c.re, c.blk, c.R, c.G);
 }
 
+// W <- max(0, W o P / (W Q + eps)) of one problem, Q restricted to its diagonal
+// rank blocks; a thread owns whole rows; RM bounds the rank so the loops unroll
+// to the padded bucket; the sum over l runs in index order.
+template <int RM>
+__device__ __forceinline__ void group_w_update(const GComb& c, float eps) {
+  const int m = c.m, re = c.re, blk = c.blk, R = c.R, MP = c.MP;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    float w[RM], wn[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) w[k] = (k < re) ? c.W[i * re + k] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < RM; ++k) {
+      wn[k] = 0.0f;
+      if (k < re) {
+        const int lo = (k / blk) * blk, hi = min(re, lo + blk);
+        float wq = 0.0f;
+#pragma unroll
+        for (int l = 0; l < RM; ++l)
+          if (l >= lo && l < hi) wq = fmaf(w[l], __ldcg(&c.red[(MP + l) * R + k]), wq);
+        wn[k] = fmaxf(0.0f, __fdiv_rn(w[k] * __ldcg(&c.red[i * R + k]), wq + eps));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < re) c.W[i * re + k] = wn[k];
+  }
+}
+
 __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb* __restrict__ combs,
                                                                     const int* __restrict__ blk_comb,
                                                                     float eps, int t) {
@@ -96,15 +124,30 @@ __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb*
     const int per = (c.S + kChunks - 1) / kChunks;
     const int b0 = j * per, b1 = min(c.S, b0 + per);
     float s = 0.0f;
-    if (e < E)
-      for (int b = b0; b < b1; ++b) s += __ldcg(&c.part[(size_t)b * E + e]);
+    if (e < E) {
+      // batches of eight independent loads, summed in partial order
+      constexpr int U = 8;
+      for (int bb = b0; bb < b1; bb += U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = bb + u < b1 ? __ldcg(&c.part[(size_t)(bb + u) * E + e]) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (bb + u < b1) s += v[u];
+      }
+    }
     chunk[j][el] = s;
     __syncthreads();
     if (tid < kEntries && e < E) {
-      double tot = 0.0;
+      // pairwise FP64 sum of the chunks (fixed order)
+      double tq[kChunks];
 #pragma unroll
-      for (int q = 0; q < kChunks; ++q) tot += (double)chunk[q][tid];
-      c.red[e] = (float)tot;
+      for (int q = 0; q < kChunks; ++q) tq[q] = (double)chunk[q][tid];
+#pragma unroll
+      for (int w = 1; w < kChunks; w *= 2)
+#pragma unroll
+        for (int q = 0; q + w < kChunks; q += 2 * w) tq[q] += tq[q + w];
+      c.red[e] = (float)tq[0];
     }
   }
   __threadfence();
@@ -116,55 +159,48 @@ __global__ void __launch_bounds__(kAuxThreads) group_combine_kernel(const GComb*
 
   // last block of the problem: W update row by row (each row owned by one thread), then the Gram
   const int m = c.m, re = c.re, blk = c.blk, R = c.R, MP = c.MP;
-  for (int i = tid; i < m; i += blockDim.x) {
-    float w[NTT_MAX_RANK], wn[NTT_MAX_RANK];
-#pragma unroll
-    for (int k = 0; k < NTT_MAX_RANK; ++k) w[k] = (k < re) ? c.W[i * re + k] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < NTT_MAX_RANK; ++k) {
-      wn[k] = 0.0f;
-      if (k < re) {
-        const int lo = (k / blk) * blk, hi = min(re, lo + blk);
-        float wq = 0.0f;
-#pragma unroll
-        for (int l = 0; l < NTT_MAX_RANK; ++l)
-          if (l >= lo && l < hi) wq = fmaf(w[l], __ldcg(&c.red[(MP + l) * R + k]), wq);
-        wn[k] = fmaxf(0.0f, __fdiv_rn(w[k] * __ldcg(&c.red[i * R + k]), wq + eps));
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NTT_MAX_RANK; ++k)
-      if (k < re) c.W[i * re + k] = wn[k];
-  }
+  if (R <= 8)
+    group_w_update<8>(c, eps);
+  else if (R <= 16)
+    group_w_update<16>(c, eps);
+  else
+    group_w_update<NTT_MAX_RANK>(c, eps);
   __syncthreads();
   group_gram(c.W, m, re, blk, R, c.G);
   if (c.obj) {
     // f = 1/2 (||X||^2 - 2 <W, P> + <W^T W, Q>) on the rank blocks, FP64 sums in a fixed order
     __syncthreads();
-    double a = 0.0, b = 0.0;
-    for (int e = tid; e < m * re; e += blockDim.x) {
-      const int i = e / re, k = e % re;
-      a += (double)__ldcg(&c.W[e]) * (double)__ldcg(&c.red[i * R + k]);
-    }
+    // <W, P> by rows (two FP64 chains), <G_W, Q> by entries; one reduction of both
+    double a0 = 0.0, a1 = 0.0, b = 0.0;
+    for (int i = tid; i < m; i += blockDim.x)
+      for (int k = 0; k < re; ++k) {
+        const double v = (double)__ldcg(&c.W[i * re + k]) * (double)__ldcg(&c.red[i * R + k]);
+        if (k & 1) a1 += v; else a0 += v;
+      }
     for (int kl = tid; kl < re * re; kl += blockDim.x) {
-      const int k = kl / re, l = kl % re;
+      const int k = kl / re, l = kl - k * re;
       if (k / blk == l / blk) b += (double)__ldcg(&c.G[k * R + l]) * (double)__ldcg(&c.red[(MP + k) * R + l]);
     }
-    dsh[tid] = a;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (tid < s) dsh[tid] += dsh[tid + s];
-      __syncthreads();
+    double A = a0 + a1, B = b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the warp sum
+      A += __shfl_xor_sync(0xffffffffu, A, o);
+      B += __shfl_xor_sync(0xffffffffu, B, o);
     }
-    const double A = dsh[0];
-    __syncthreads();
-    dsh[tid] = b;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (tid < s) dsh[tid] += dsh[tid + s];
-      __syncthreads();
+    const int nw = blockDim.x / 32;
+    if ((tid & 31) == 0) {
+      dsh[tid / 32] = A;
+      dsh[nw + tid / 32] = B;
     }
-    if (tid == 0) c.obj[t] = 0.5 * (*c.xnorm2 - 2.0 * A + dsh[0]);
+    __syncthreads();
+    if (tid == 0) {
+      double As = 0.0, Bs = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        As += dsh[w];
+        Bs += dsh[nw + w];
+      }
+      c.obj[t] = 0.5 * (*c.xnorm2 - 2.0 * As + Bs);
+    }
   }
   if (tid == 0) *c.ticket = 0u;
 }
