@@ -16,6 +16,8 @@ of the paper it restates:
   Section IV (strong scaling, Fig. 7c); update order H then W, epsilon added to
   both denominators                                -> mu_update_H, mu_update_W, nmf_mu
 * objective 1/2 ||X - WH||_F^2 (Algorithm 3's objective)   -> objective
+* optional relative-change stopping test on that objective (tol = 0: the
+  fixed iteration count of Algorithm 3's loop)     -> stop_reached
 * counter-based SplitMix64 initialisation (the paper only says "rand") -> uniform01
 * precision form (not in the paper, whose experiments are FP32: each unfolding
   rounded to bfloat16, the MU iterations on it, then refinement iterations on
@@ -127,8 +129,22 @@ def objective(X, W, H):
     return 0.5 * float(np.sum(R * R))
 
 
-def nmf_mu(X, W0, H0, iters, eps=EPS_MU, record=True):
-    """Run `iters` full multiplicative-update iterations, H first then W.
+def stop_reached(trace, u, tol, check_every):
+    """Relative-change stopping test on the objective trace (the objective
+    1/2 ||X - WH||^2 that Algorithm 3 tracks; the paper iterates to a maximum
+    count, so the test is optional and tol = 0 keeps the fixed count).  After
+    iteration u (1-based), with u a multiple of K = check_every and u >= 2K,
+    stop when f_{u-K} - f_u <= tol |f_{u-K}|, where f_v = trace[v - 1]."""
+    K = int(check_every)
+    if tol <= 0.0 or K <= 0 or u % K != 0 or u < 2 * K:
+        return False
+    f0, f1 = trace[u - K - 1], trace[u - 1]
+    return f0 - f1 <= tol * abs(f0)
+
+
+def nmf_mu(X, W0, H0, iters, eps=EPS_MU, record=True, tol=0.0, check_every=10):
+    """Run up to `iters` full multiplicative-update iterations, H first then W
+    (fewer when tol > 0 and stop_reached says so; that needs record=True).
 
     Returns (W, H, trace) where trace[t] = 1/2 ||X - W_{t+1} H_{t+1}||^2.
     """
@@ -136,11 +152,13 @@ def nmf_mu(X, W0, H0, iters, eps=EPS_MU, record=True):
     W = np.array(W0, dtype=np.float64)
     H = np.array(H0, dtype=np.float64)
     trace = []
-    for _ in range(int(iters)):
+    for u in range(1, int(iters) + 1):
         H = mu_update_H(X, W, H, eps)
         W = mu_update_W(X, W, H, eps)
-        if record:
+        if record or tol > 0.0:
             trace.append(objective(X, W, H))
+        if stop_reached(trace, u, tol, check_every):
+            break
     return W, H, np.array(trace)
 
 
@@ -191,7 +209,7 @@ def unfold(T, m):
 
 
 def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, x_precision="f32",
-                  refine=0):
+                  refine=0, tol=0.0, check_every=10):
     """Non-negative tensor train of A with given TT ranks (Algorithm 2).
 
     Stage l (0-based s = l-1): X = reshape(current, r_{l-1} n_l, rest); NMF of
@@ -201,6 +219,8 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
     x_precision="bf16": the stage's `iters` iterations run on bf16_round(X),
     then `refine` more on X itself (the precision form); the objective that
     picks the restart is on X.
+    tol > 0: each stage's main loop stops early under stop_reached (the
+    refinement iterations always run).
     Returns (cores, traces), traces[s] = objective trace of the kept restart
     (with record=False only the final objective of each stage).
     """
@@ -223,7 +243,7 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
         Xi = bf16_round(X) if x_precision == "bf16" else X
         for rs in range(restarts):
             W0, H0 = init_factors(m, n, r, seed, s, rs)
-            W, H, tr = nmf_mu(Xi, W0, H0, iters, eps, record=record)
+            W, H, tr = nmf_mu(Xi, W0, H0, iters, eps, record=record, tol=tol, check_every=check_every)
             if refine:
                 W, H, tr2 = nmf_mu(X, W, H, refine, eps, record=record)
                 tr = np.concatenate([tr, tr2])

@@ -179,6 +179,61 @@ def test_full_rank_stage_error_goes_to_zero():
     assert tr[-1] <= 1e-3 * tr[0]
 
 
+def test_stopping_test_limits():
+    """The optional relative-change test: with tol = 0 the loop is the fixed
+    count (bitwise); with tol >= 1 it must fire at its first opportunity u = 2K,
+    because MU never raises the objective (Lee-Seung) and the objective is >= 0,
+    so f_{u-K} - f_u <= f_{u-K} always holds; a stopped run equals a fixed-count
+    run of the same length."""
+    X = _rand((20, 150), 30) ** 2
+    W0, H0 = _rand((20, 3), 31), _rand((3, 150), 32)
+    Wf, Hf, trf = oracle.nmf_mu(X, W0, H0, 60)
+    Wz, Hz, trz = oracle.nmf_mu(X, W0, H0, 60, tol=0.0, check_every=7)
+    assert np.array_equal(Wf, Wz) and np.array_equal(Hf, Hz) and np.array_equal(trf, trz)
+    for K in (1, 5, 7):
+        Ws, Hs, trs = oracle.nmf_mu(X, W0, H0, 60, tol=1.0, check_every=K)
+        assert len(trs) == 2 * K
+        Wk, Hk, trk = oracle.nmf_mu(X, W0, H0, 2 * K)
+        assert np.array_equal(Ws, Wk) and np.array_equal(Hs, Hk) and np.array_equal(trs, trk)
+    # a stop needs a completed check: fewer than 2K iterations never stop early
+    _, _, tr = oracle.nmf_mu(X, W0, H0, 9, tol=1.0, check_every=5)
+    assert len(tr) == 9
+
+
+def test_stopping_test_stops_where_decrease_falls_below_tol():
+    """On a monotone trace the test stops at the first check whose K-iteration
+    relative decrease is <= tol; a tol between two consecutive checks' decreases
+    separates them, and a run to convergence of the exact-recovery case (the
+    decrease shrinks towards 0) stops before the iteration cap."""
+    X = _rand((20, 150), 33) ** 2
+    W0, H0 = _rand((20, 3), 34), _rand((3, 150), 35)
+    K = 10
+    _, _, full = oracle.nmf_mu(X, W0, H0, 200)
+    dec = {u: (full[u - K - 1] - full[u - 1]) / full[u - K - 1] for u in range(2 * K, 201, K)}
+    # decreases of a converging MU trace shrink: pick tol between two checks
+    us = sorted(dec)
+    i = next(j for j in range(1, len(us)) if dec[us[j]] < 0.5 * dec[us[j - 1]])
+    tol = math.sqrt(dec[us[i]] * dec[us[i - 1]])
+    first = next(u for u in us if dec[u] <= tol)
+    _, _, tr = oracle.nmf_mu(X, W0, H0, 200, tol=tol, check_every=K)
+    assert len(tr) == first
+    # noise-free rank-2 product: f -> 0, so a small tol still stops early
+    Wt, Ht = _rand((12, 2), 36) + 0.1, _rand((2, 40), 37) + 0.1
+    _, _, tr = oracle.nmf_mu(Wt @ Ht, _rand((12, 2), 38), _rand((2, 40), 39), 20000, tol=1e-6, check_every=K)
+    assert 2 * K <= len(tr) < 20000 and len(tr) % K == 0
+
+
+def test_ntt_stopping_test_per_stage():
+    """Each stage's main loop stops under the test on its own trace; the
+    refinement iterations of the precision form always run."""
+    A = _rand((6, 5, 4), 40)
+    cores, traces = oracle.ntt_decompose(A, (1, 3, 2, 1), iters=100, seed=3, tol=1.0, check_every=4)
+    assert [len(t) for t in traces] == [8, 8]
+    cores, traces = oracle.ntt_decompose(A, (1, 3, 2, 1), iters=100, seed=3, tol=1.0, check_every=4,
+                                         x_precision="bf16", refine=3)
+    assert [len(t) for t in traces] == [11, 11]
+
+
 # ---------------------------------------------------------------- hand-off and Algorithm 2
 
 def test_handoff_normalize_keeps_product():
