@@ -69,13 +69,21 @@ typedef struct {
                             iterated with FP32 accumulation, then refined in FP32 */
   int refine_iters;      /* FP32 iterations after the BF16 ones (BF16 form only) */
   uint64_t seed;         /* seed of the counter-based initialisation */
+  double tol;            /* stopping test of each stage's main MU loop (Algorithm 3's loop
+                            tracks the objective f = 1/2||X-WH||^2 and runs to a maximum
+                            count): 0 runs `iters` iterations; > 0 stops after iteration u,
+                            u a multiple of check_every and u >= 2 check_every, once
+                            f_{u-K} - f_u <= tol |f_{u-K}| (f in FP64, Gram form).  The
+                            refinement iterations always run.  >= 0. */
+  int check_every;       /* K of that test; >= 1 when tol > 0 */
 } ntt_plan_desc;
 
 /* Per-stage statistics, filled by ntt_plan_get_stats after the last call. */
 typedef struct {
   int d;                            /* tensor order of the plan */
   int status;                       /* device status word (ntt_status) */
-  int iters[NTT_MAX_D];             /* MU iterations run per stage (BF16 + FP32) */
+  int iters[NTT_MAX_D];             /* MU iterations run per stage (BF16 + FP32; fewer than
+                                       iters + refine_iters when the stopping test fired) */
   int64_t m[NTT_MAX_D], n[NTT_MAX_D], r[NTT_MAX_D];   /* unfolding shapes */
   double xnorm2[NTT_MAX_D];         /* ||X_l||_F^2 (FP64 reduction) */
   double obj_first[NTT_MAX_D];      /* 1/2||X-WH||^2 after the first iteration (Gram form) */

@@ -68,6 +68,8 @@ class _PlanDesc(ctypes.Structure):
         ("x_dtype", ctypes.c_int),
         ("refine_iters", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("tol", ctypes.c_double),
+        ("check_every", ctypes.c_int),
     ]
 
 
@@ -238,7 +240,8 @@ class Plan:
             pass
 
 
-def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0):
+def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, tol=0.0,
+                    check_every=10):
     dims = tuple(int(n) for n in dims)
     ranks = tuple(int(r) for r in ranks) if ranks is not None else None
     d_arr = _i64arr(dims)
@@ -252,6 +255,8 @@ def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iter
     desc.x_dtype = NTT_BF16 if x_dtype == "bf16" else NTT_F32
     desc.refine_iters = int(refine_iters)
     desc.seed = int(seed)
+    desc.tol = float(tol)
+    desc.check_every = int(check_every)
     h = ctypes.c_void_p()
     _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
     return Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
@@ -593,10 +598,11 @@ def ntt_compression_ratio(dims, ranks):
     return lib().ntt_compression_ratio(len(dims), _i64arr(dims), _i64arr(ranks))
 
 
-def decompose(A, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, stream=None):
+def decompose(A, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, stream=None, tol=0.0,
+              check_every=10):
     """Convenience wrapper: returns (cores, stats) for a CUDA float32 tensor A."""
     import torch
-    plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed)
+    plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed, tol, check_every)
     ws = empty_workspace(plan.workspace_size(), A.device)
     cores = [torch.empty(s, dtype=torch.float32, device=A.device) for s in plan.core_shapes()]
     ntt_decompose(plan, A.contiguous(), cores, ws, stream)

@@ -123,6 +123,7 @@ struct PassParams {
   const float* G;      // R x R
   float* part;         // grid x (MP+R) x R
   int* status;
+  const int* stop;     // nullable: the stage's stop word; a set word makes the launch a no-op
   int64_t n;
   int m, r;
   int ntiles;
@@ -136,6 +137,7 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
                const PassParams p) {
   using XT = typename XLoad<C::BF16>::T;
   constexpr int T = C::T, R = C::R, MP = C::MP, NT = C::NT;
+  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   constexpr int HNF = C::HN_BUF / 4;   // floats per H_new buffer
 
   extern __shared__ uint8_t smem_raw[];
@@ -438,6 +440,7 @@ cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const C
   p.G = d.G;
   p.part = d.part;
   p.status = d.status;
+  p.stop = d.stop;
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;

@@ -72,6 +72,7 @@ struct NarrowParams {
   const float* G;      // 8 x 8 Gram of W, zero padded
   float* part;         // grid x (MP + 8) x 8
   int* status;
+  const int* stop;     // nullable: the stage's stop word; a set word makes the launch a no-op
   int64_t n;
   int m, r;
   int nbox;            // ceil(n / 32)
@@ -107,6 +108,7 @@ mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
                       const NarrowParams p) {
   constexpr int RPL = C::RPL, MP = C::MP, S = C::STAGES;
   constexpr int kNarrowWarps = C::kNarrowWarps, kNarrowThreads = C::kNarrowThreads;
+  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -333,6 +335,7 @@ cudaError_t launch_narrow_cfg(const MuShape& s, const MuDev& d, float eps, const
   p.G = d.G;
   p.part = d.part;
   p.status = d.status;
+  p.stop = d.stop;
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;

@@ -102,6 +102,7 @@ struct TcParams {
   const float* G;
   float* part;
   int* status;
+  const int* stop;     // nullable: the stage's stop word; a set word makes the launch a no-op
   int64_t n;
   int m, r;
   int ntiles;
@@ -126,6 +127,7 @@ mu_pass_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
                   const TcParams p) {
   constexpr int MP = C::MP, R = C::R, T = C::T, N2 = C::N2, S = C::STAGES;
   constexpr int KH = R / 2;          // ranks per worker thread (two threads per column)
+  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   constexpr int NW = kTcThreads;     // worker threads
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -447,6 +449,7 @@ cudaError_t launch_tc_cfg(const MuShape& s, const MuDev& d, float eps, const CUt
   p.G = d.G;
   p.part = d.part;
   p.status = d.status;
+  p.stop = d.stop;
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;

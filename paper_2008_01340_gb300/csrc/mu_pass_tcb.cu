@@ -120,6 +120,7 @@ struct TbParams {
   const float* G;           // R x R
   float* part;              // grid x (MP + R) x R
   int* status;
+  const int* stop;     // nullable: the stage's stop word; a set word makes the launch a no-op
   int64_t n;
   int m, r, ntiles;
   float eps;
@@ -128,6 +129,7 @@ struct TbParams {
 template <class C>
 __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbParams p) {
   constexpr int MP = C::MP, R = C::R, T = C::T, N3 = C::N3, KH = C::KH;
+  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -394,6 +396,7 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.G = d.G;
   p.part = d.part;
   p.status = d.status;
+  p.stop = d.stop;
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;

@@ -32,6 +32,9 @@ struct CombineParams {
   const double* xnorm2;
   float eps;
   int blk;   // > 0: W^T W and H H^T masked to diagonal blocks of this size
+  int* stop;   // nullable stop word of the loop (see MuDev)
+  double tol;
+  int check, t0;
 };
 
 // G = W^T W (R x R, zero outside r x r) from W (m x r) by the whole block.
@@ -95,6 +98,7 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
   __shared__ int s_last;
   const int tid = threadIdx.x;
   const int E = (p.MP + p.R) * p.R;
+  if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
 
   // ---- 1. reduce 32 entries over all partials: 8 chunks x FP32, then FP64
   {
@@ -206,7 +210,15 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
         As += dsh[w];
         Bs += dsh[nw + w];
       }
-      p.obj[p.t] = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
+      const double f = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
+      p.obj[p.t] = f;
+      // stopping test after iteration u = t - t0 + 1 (u a multiple of K, u >= 2K):
+      // f_{u-K} - f_u <= tol |f_{u-K}|; the earlier value is this loop's own
+      const int u = p.t - p.t0 + 1, K = p.check;
+      if (p.stop && p.tol > 0.0 && K > 0 && u % K == 0 && u >= 2 * K) {
+        const double f0 = p.obj[p.t - K];
+        if (f0 - f <= p.tol * fabs(f0)) *p.stop = u;
+      }
     }
   }
   if (tid == 0) *p.ticket = 0u;
@@ -243,6 +255,10 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
   p.xnorm2 = d.xnorm2;
   p.eps = eps;
   p.blk = d.blk;
+  p.stop = d.stop;
+  p.tol = d.tol;
+  p.check = d.check;
+  p.t0 = d.loop_t0;
   const int E = s.part_stride();
   const int blocks = (E + kEntriesPerBlock - 1) / kEntriesPerBlock;
   const size_t smem = (size_t)(E + s.m * s.r + s.R * s.R) * sizeof(float);

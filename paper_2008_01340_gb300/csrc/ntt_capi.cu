@@ -219,6 +219,9 @@ struct ntt_plan_s {
   ntt_dtype xdt = NTT_F32;
   int refine = 0;
   uint64_t seed = 0;
+  double tol = 0.0;              // stopping test of each stage's main loop (0: fixed count)
+  int check = 0;
+  size_t off_stop = 0;           // one stop word per stage
 
   // A stage's MU loop runs either on the single-problem pass (TMA, phase
   // split) or on the grouped engine with this one problem, whichever measured
@@ -301,6 +304,8 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
   double* obj = reinterpret_cast<double*>(ws + p->off_obj);
   NTT_CUDA_TRY(cudaMemsetAsync(status, 0, 64, st));
   NTT_CUDA_TRY(cudaMemsetAsync(tickets, 0, 64, st));
+  int* stop = reinterpret_cast<int*>(ws + p->off_stop);
+  NTT_CUDA_TRY(cudaMemsetAsync(stop, 0, NTT_MAX_D * sizeof(int), st));
   const int d = p->d;
   int64_t launches = 0;
   // External event nodes: a plain record on a capturing stream would only
@@ -339,6 +344,10 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
       const bool main_loop = t0 == 0;
       if (!rt.on) {
         dev.X = Xv;
+        dev.stop = main_loop && p->tol > 0.0 ? stop + s : nullptr;
+        dev.tol = p->tol;
+        dev.check = p->check;
+        dev.loop_t0 = t0;
         int eng = NTT_ENGINE_FMA_PASS;
         const ntt_status e = run_mu_iters(shp, dev, p->eps, iters, t0, st, &eng);
         if (main_loop) p->st[s].engine = eng;
@@ -423,6 +432,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (desc->iters < 1 || !(desc->eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
   if (desc->x_dtype != NTT_F32 && desc->x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
   if (desc->refine_iters < 0) return NTT_ERR_INVALID_ARG;
+  if (!(desc->tol >= 0.0) || desc->tol > 1e300) return NTT_ERR_INVALID_ARG;
+  if (desc->tol > 0.0 && desc->check_every < 1) return NTT_ERR_INVALID_ARG;
   const int64_t* dims = desc->dims;
   const int64_t* ranks = desc->ranks;
   if (ranks[0] != 1 || ranks[d] != 1) return NTT_ERR_INVALID_ARG;
@@ -445,6 +456,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->xdt = desc->x_dtype;
   p->refine = desc->x_dtype == NTT_BF16 ? desc->refine_iters : 0;
   p->seed = desc->seed;
+  p->tol = desc->tol;
+  p->check = desc->tol > 0.0 ? desc->check_every : 0;
   const int sms = device_sms();
   size_t max_part = 1, max_red = 1, maxH[2] = {1, 1}, max_xb = 1;
   for (int s = 0; s < d - 1; ++s) {
@@ -480,6 +493,9 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
       if (xb && p->xdt != NTT_BF16) continue;
       if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
       if (!plan_route_group(S.m, S.n, S.r, xb != 0)) continue;
+      // a main loop with a stopping test runs on the single-problem passes
+      const bool main_loop = xb != 0 || p->xdt != NTT_BF16;
+      if (main_loop && p->tol > 0.0) continue;
       GroupShape sh;
       sh.n = S.n;
       sh.m = (int)S.m;
@@ -496,6 +512,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   Arena ar;
   p->off_status = ar.take(64);
   p->off_tickets = ar.take(64);
+  p->off_stop = ar.take(NTT_MAX_D * sizeof(int));
   p->off_scal = ar.take(4 * NTT_MAX_D * sizeof(double));
   p->off_obj = ar.take(p->obj_total * sizeof(double));
   p->off_G = ar.take(NTT_MAX_RANK * NTT_MAX_RANK * 4);
@@ -655,12 +672,17 @@ ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
   std::vector<double> obj(p->obj_total ? p->obj_total : 1);
   if (p->obj_total)
     NTT_CUDA_TRY(cudaMemcpy(obj.data(), ws + p->off_obj, p->obj_total * 8, cudaMemcpyDeviceToHost));
+  int stopw[NTT_MAX_D];
+  NTT_CUDA_TRY(cudaMemcpy(stopw, ws + p->off_stop, sizeof(stopw), cudaMemcpyDeviceToHost));
   for (int s = 0; s < p->d - 1; ++s) {
     out->xnorm2[s] = scal[s];
     out->resid[s] = scal[NTT_MAX_D + s];
     const auto& S = p->st[s];
+    // iterations run: the main loop's count (cut by the stopping test) + refinement
+    const int main_run = (p->tol > 0.0 && stopw[s] > 0) ? stopw[s] : p->iters;
+    out->iters[s] = main_run + p->refine;
     out->obj_first[s] = obj[S.obj_off];
-    out->obj_last[s] = obj[S.obj_off + S.iters_total - 1];
+    out->obj_last[s] = obj[S.obj_off + (p->refine > 0 ? S.iters_total : main_run) - 1];
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, p->ev[4 * s], p->ev[4 * s + 1]) == cudaSuccess)
       out->stage_ms[s] = ms;

@@ -300,6 +300,14 @@ struct MuDev {
   const double* xnorm2 = nullptr;
   int* status = nullptr;
   int blk = 0;                   // > 0: independent restarts of rank blk side by side
+  // optional stopping test of the loop (the plan's main MU loop of a stage):
+  // the combine of iteration t writes t - loop_t0 + 1 to *stop once the
+  // objective's relative decrease over `check` iterations is <= tol, and every
+  // later pass / combine launch with this stop word returns at entry
+  int* stop = nullptr;
+  double tol = 0.0;
+  int check = 0;
+  int loop_t0 = 0;
 };
 
 // Pick template bucket, tile width and grid for an m x n x r problem.

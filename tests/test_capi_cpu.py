@@ -76,6 +76,13 @@ def test_plan_validation(lib):
     with pytest.raises(ntt.NTTError) as e:
         ntt.ntt_plan_create((8, 8), None, 10)
     assert e.value.code == 6
+    # stopping test: tol >= 0 (not NaN), check_every >= 1 when tol > 0
+    for tol, k in ((-1e-3, 10), (float("nan"), 10), (1e-3, 0)):
+        with pytest.raises(ntt.NTTError) as e:
+            ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, tol=tol, check_every=k)
+        assert e.value.code == 1
+    ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, tol=1e-3, check_every=5).destroy()
+    ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, tol=0.0, check_every=0).destroy()
 
 
 def test_workspace_sizes(lib):

@@ -177,9 +177,9 @@ def test_mu_bf16_x(ntt, m, n, r):
 
 # ------------------------------------------------------------------ whole nTT
 
-def _decompose(ntt, A, ranks, iters, seed, x_dtype="f32", refine=0):
+def _decompose(ntt, A, ranks, iters, seed, x_dtype="f32", refine=0, tol=0.0, check_every=10):
     dims = A.shape
-    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, seed)
+    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, seed, tol, check_every)
     ws = ntt.empty_workspace(plan.workspace_size())
     cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -235,6 +235,55 @@ def test_ntt_bf16_form_small(ntt):
     print(f"bf16 form rel error gpu {eg:.6f} fp64 oracle (105 FP32 iterations) {eo:.6f}")
     assert abs(eg - eo) <= REL_BF16_VS_FP64
     assert stats["status"] == "NTT_OK"
+
+
+def _clear_stops(traces, tol, K, iters, margin=1.1):
+    """True when every stage's stopping decision under the oracle's trace is
+    clear by `margin` on both sides of tol (so FP32 rounding cannot flip it)."""
+    for tr in traces:
+        u = len(tr)
+        for v in range(2 * K, u + 1, K):
+            dec = (tr[v - K - 1] - tr[v - 1]) / abs(tr[v - K - 1])
+            if v < u and not dec > margin * tol:
+                return False
+            if v == u and u < iters and not dec < tol / margin:
+                return False
+    return any(len(t) < iters for t in traces)
+
+
+@pytest.mark.parametrize("x_dtype,refine", [("f32", 0), ("bf16", 4)])
+def test_ntt_stopping_test_matches_oracle(ntt, x_dtype, refine):
+    """With tol > 0 each stage's main loop stops at the check where the
+    objective's relative decrease over K iterations first falls below tol:
+    the same iteration as the oracle's rule on its FP64 trace (tol chosen so
+    that every decision is clear of rounding), refinement iterations run in
+    full, and the result's Eq. (3) error matches the oracle's within 1e-3.
+    Uniform (not low-rank) data keeps the objective a sizeable fraction of
+    ||X||^2, where the FP64 Gram-form objective resolves small decreases."""
+    dims, ranks = (12, 10, 48), (1, 3, 2, 1)
+    A = synth.uniform_matrix((1, int(np.prod(dims))), 71).reshape(dims)
+    K, iters = 10, 400
+    chosen = None
+    for tol in np.geomspace(1e-4, 3e-3, 40):
+        cores_o, traces = oracle.ntt_decompose(A, ranks, iters, seed=4, tol=tol, check_every=K,
+                                               x_precision=x_dtype, refine=refine)
+        main = [t[:len(t) - refine] for t in traces]
+        if _clear_stops(main, tol, K, iters):
+            chosen = tol
+            break
+    assert chosen is not None, "no tol with clear stopping decisions"
+    cores_g, stats, plan, Ad, ws = _decompose(ntt, A, ranks, iters, 4, x_dtype=x_dtype, refine=refine,
+                                              tol=chosen, check_every=K)
+    assert stats["status"] == "NTT_OK"
+    assert [st["iters"] for st in stats["stages"]] == [len(t) for t in traces]
+    err = torch.zeros(3, dtype=torch.float64, device="cuda")
+    cg = [torch.from_numpy(c).cuda() for c in cores_g]
+    ntt.ntt_rel_error(dims, ranks, cg, Ad, err)
+    e_o = oracle.rel_error(A.astype(np.float64), cores_o)
+    assert abs(err[0].item() - e_o) <= ABS_FINAL_EPS
+    # tol = 0: every stage runs the fixed count
+    _, stats0, *_ = _decompose(ntt, A, ranks, iters, 4, x_dtype=x_dtype, refine=refine)
+    assert [st["iters"] for st in stats0["stages"]] == [iters + refine] * 2
 
 
 def test_ntt_host_variant_equals_device(ntt):
