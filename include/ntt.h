@@ -119,7 +119,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out);
 /* Device workspace bytes needed by ntt_decompose with this plan. */
 ntt_status ntt_plan_workspace_size(ntt_plan plan, size_t* bytes);
 
-/* Device workspace bytes needed by ntt_decompose_host (adds room for A). */
+/* Device workspace bytes needed by ntt_decompose_host (adds room for two
+ * copies of A, the cores and the Eq. (3) scratch). */
 ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes);
 
 /* Algorithm 2 on the device.
@@ -140,7 +141,12 @@ ntt_status ntt_decompose(ntt_plan plan, const float* A, float* const* cores,
  * the workspace, the decomposition runs, the cores are copied back, all on
  * `stream` (asynchronous with pinned host memory; sync before reading).
  * err_host (nullable, 3 doubles) receives Eq. (3) of the result as
- * ntt_rel_error reports it.  workspace: ntt_plan_workspace_size_host bytes. */
+ * ntt_rel_error reports it.  workspace: ntt_plan_workspace_size_host bytes.
+ * Successive calls alternate between two input slots of the workspace: a
+ * call's host-to-device copy runs on the plan's own copy stream, waits only
+ * for the call two back to finish reading that slot, and so overlaps the
+ * previous call's decomposition; the decomposition waits for its copy.
+ * A_host must stay unchanged until `stream` has passed the call. */
 ntt_status ntt_decompose_host(ntt_plan plan, const float* A_host, float* const* cores_host,
                               double* err_host, void* workspace, void* stream);
 

@@ -245,15 +245,23 @@ struct ntt_plan_s {
   // workspace layout
   size_t off_status = 0, off_tickets = 0, off_scal = 0, off_obj = 0, off_G = 0, off_red = 0,
          off_part = 0, off_part64 = 0, off_hs = 0, off_H[2] = {0, 0}, off_xb = 0, ws_bytes = 0;
-  size_t off_A = 0, off_cores = 0, ws_bytes_host = 0;
+  size_t off_A[2] = {0, 0}, off_cores = 0, ws_bytes_host = 0;   // two input slots (host variant)
   std::vector<size_t> core_off;
   size_t obj_total = 0;
-  // graph cache
-  cudaGraphExec_t exec = nullptr;
+  // graph cache: two entries, so the host variant's two input slots both stay captured
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    const void* A = nullptr;
+    void* ws = nullptr;
+    std::vector<float*> cores;
+  };
+  Graph graphs[2];
+  int graph_victim = 0;
   cudaStream_t cap = nullptr;
-  const void* gA = nullptr;
-  void* gws = nullptr;
-  std::vector<float*> gcores;
+  // host variant: the copy of the next call's input overlaps this call's compute
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t slot_ready[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
+  int host_slot = 0;
   std::vector<cudaEvent_t> ev;   // 4 per stage + 2 total
   int64_t launches = 0;          // kernels per decomposition
   size_t off_chain = 0, off_err = 0;
@@ -265,8 +273,14 @@ struct ntt_plan_s {
   bool ran = false;
 
   ~ntt_plan_s() {
-    if (exec) cudaGraphExecDestroy(exec);
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     if (cap) cudaStreamDestroy(cap);
+    if (copy_st) cudaStreamDestroy(copy_st);
+    for (int i = 0; i < 2; ++i) {
+      if (slot_ready[i]) cudaEventDestroy(slot_ready[i]);
+      if (slot_free[i]) cudaEventDestroy(slot_free[i]);
+    }
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
     if (h_tables) cudaFreeHost(h_tables);
@@ -525,7 +539,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (p->xdt == NTT_BF16) p->off_xb = ar.take(max_xb * 2);
   if (grp) p->off_grp = ar.take(grp);
   p->ws_bytes = ar.off;
-  p->off_A = ar.take((size_t)prod(dims, 0, d) * 4);
+  p->off_A[0] = ar.take((size_t)prod(dims, 0, d) * 4);
+  p->off_A[1] = ar.take((size_t)prod(dims, 0, d) * 4);
   for (int k = 0; k < d; ++k)
     p->core_off.push_back(ar.take((size_t)ranks[k] * dims[k] * ranks[k + 1] * 4));
   p->off_err = ar.take(8 * sizeof(double));
@@ -584,13 +599,18 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
     if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
     NTT_TRY(enqueue_decompose(p, A, cores, ws, st));
   } else {
-    bool hit = p->exec && p->gA == A && p->gws == workspace &&
-               p->gcores.size() == (size_t)d;
-    for (int k = 0; hit && k < d; ++k) hit = p->gcores[k] == cores[k];
-    if (!hit) {
-      if (p->exec) {
-        cudaGraphExecDestroy(p->exec);
-        p->exec = nullptr;
+    ntt_plan_s::Graph* G = nullptr;
+    for (auto& g : p->graphs) {
+      bool hit = g.exec && g.A == A && g.ws == workspace && g.cores.size() == (size_t)d;
+      for (int k = 0; hit && k < d; ++k) hit = g.cores[k] == cores[k];
+      if (hit) G = &g;
+    }
+    if (!G) {
+      G = &p->graphs[p->graph_victim];
+      p->graph_victim ^= 1;
+      if (G->exec) {
+        cudaGraphExecDestroy(G->exec);
+        G->exec = nullptr;
       }
       if (!p->cap) NTT_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
       cudaGraph_t g = nullptr;
@@ -605,18 +625,18 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
         cudaGetLastError();
         return NTT_ERR_CUDA;
       }
-      cudaError_t ie = cudaGraphInstantiate(&p->exec, g, 0);
+      cudaError_t ie = cudaGraphInstantiate(&G->exec, g, 0);
       cudaGraphDestroy(g);
       if (ie != cudaSuccess) {
         cudaGetLastError();
-        p->exec = nullptr;
+        G->exec = nullptr;
         return NTT_ERR_CUDA;
       }
-      p->gA = A;
-      p->gws = workspace;
-      p->gcores.assign(cores, cores + d);
+      G->A = A;
+      G->ws = workspace;
+      G->cores.assign(cores, cores + d);
     }
-    NTT_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    NTT_CUDA_TRY(cudaGraphLaunch(G->exec, st));
   }
   p->last_stream = st;
   p->last_ws = workspace;
@@ -630,11 +650,26 @@ ntt_status ntt_decompose_host(ntt_plan p, const float* A_host, float* const* cor
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
   const int d = p->d;
-  float* A_dev = reinterpret_cast<float*>(ws + p->off_A);
+  // Two input slots alternate: this call's copy runs on the plan's copy stream
+  // and waits only until the call two back has finished reading its slot, so
+  // it overlaps the previous call's compute; the compute waits for the copy.
+  if (!p->copy_st) {
+    NTT_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      NTT_CUDA_TRY(cudaEventCreateWithFlags(&p->slot_ready[i], cudaEventDisableTiming));
+      NTT_CUDA_TRY(cudaEventCreateWithFlags(&p->slot_free[i], cudaEventDisableTiming));
+    }
+  }
+  const int slot = p->host_slot;
+  p->host_slot ^= 1;
+  float* A_dev = reinterpret_cast<float*>(ws + p->off_A[slot]);
   std::vector<float*> cdev(d);
   for (int k = 0; k < d; ++k) cdev[k] = reinterpret_cast<float*>(ws + p->core_off[k]);
   const size_t abytes = (size_t)prod(p->dims.data(), 0, d) * 4;
-  NTT_CUDA_TRY(cudaMemcpyAsync(A_dev, A_host, abytes, cudaMemcpyHostToDevice, st));
+  NTT_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->slot_free[slot], 0));   // never recorded: no wait
+  NTT_CUDA_TRY(cudaMemcpyAsync(A_dev, A_host, abytes, cudaMemcpyHostToDevice, p->copy_st));
+  NTT_CUDA_TRY(cudaEventRecord(p->slot_ready[slot], p->copy_st));
+  NTT_CUDA_TRY(cudaStreamWaitEvent(st, p->slot_ready[slot], 0));
   NTT_TRY(ntt_decompose(p, A_dev, cdev.data(), workspace, stream));
   if (err_host) {
     double* err_dev = reinterpret_cast<double*>(ws + p->off_err);
@@ -646,6 +681,7 @@ ntt_status ntt_decompose_host(ntt_plan p, const float* A_host, float* const* cor
     const size_t cb = (size_t)p->ranks[k] * p->dims[k] * p->ranks[k + 1] * 4;
     NTT_CUDA_TRY(cudaMemcpyAsync(cores_host[k], cdev[k], cb, cudaMemcpyDeviceToHost, st));
   }
+  NTT_CUDA_TRY(cudaEventRecord(p->slot_free[slot], st));   // slot read by the graph and Eq. (3)
   return NTT_OK;
 }
 

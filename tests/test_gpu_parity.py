@@ -287,17 +287,25 @@ def test_ntt_stopping_test_matches_oracle(ntt, x_dtype, refine):
 
 
 def test_ntt_host_variant_equals_device(ntt):
+    """Host-buffer calls issued back to back (A1, A2, A1, no sync between them:
+    the input copies alternate between two slots and overlap the previous
+    call's compute) each give exactly the device-buffer result of their input."""
     dims, ranks = (8, 9, 10, 7), (1, 4, 5, 3, 1)
-    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=8)
-    cores_d, *_ = _decompose(ntt, A, ranks, 30, 5)
+    A1, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=8)
+    A2, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=9)
+    ref = [_decompose(ntt, A, ranks, 30, 5)[0] for A in (A1, A2)]
     plan = ntt.ntt_plan_create(dims, ranks, 30, 1e-12, "f32", 0, 5)
     ws = ntt.empty_workspace(plan.workspace_size_host())
-    Ah = torch.from_numpy(A).pin_memory()
-    ch = [torch.empty(s, dtype=torch.float32).pin_memory() for s in plan.core_shapes()]
-    ntt.ntt_decompose_host(plan, Ah, ch, ws)
+    Ah = [torch.from_numpy(A).pin_memory() for A in (A1, A2)]
+    outs = []
+    for which in (0, 1, 0):
+        ch = [torch.empty(s, dtype=torch.float32).pin_memory() for s in plan.core_shapes()]
+        ntt.ntt_decompose_host(plan, Ah[which], ch, ws)
+        outs.append((which, ch))
     torch.cuda.synchronize()
-    for a, b in zip(cores_d, ch):
-        assert np.array_equal(a, b.numpy())
+    for which, ch in outs:
+        for a, b in zip(ref[which], ch):
+            assert np.array_equal(a, b.numpy())
 
 
 def test_ntt_repeat_is_bitwise_identical(ntt):
