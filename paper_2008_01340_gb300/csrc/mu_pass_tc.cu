@@ -36,7 +36,6 @@ struct TcCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
   static constexpr int N2 = 2 * R;                 // MMA N: [hi | lo] columns
-  static constexpr int NT = kTcThreads;
   static constexpr int T = 128;                    // columns per tile = M of phase A
   static constexpr int NCH = T / 32;               // 32-column swizzle chunks
   // chunk rows: X_hi [0,MP) | Hn_hi [MP,MP+R) | Hn_lo [MP+R,MP+2R) | X_lo [MP+2R, 2MP+2R)
