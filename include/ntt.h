@@ -58,6 +58,25 @@ typedef enum { NTT_F32 = 0, NTT_BF16 = 1 } ntt_dtype;
 
 typedef struct ntt_plan_s* ntt_plan;
 
+/* Kernel routing of the MU loops.  NTT_ROUTE_AUTO takes, per unfolding shape,
+ * the kernel measured fastest on GB300; the others restrict the choice (for
+ * comparisons and tests).  A route that does not apply to a stage's shape
+ * leaves that stage on the automatic choice among what remains allowed. */
+typedef enum {
+  NTT_ROUTE_AUTO = 0,      /* measured-fastest kernel per stage */
+  NTT_ROUTE_PASS = 1,      /* single-problem passes only (no grouped engine) */
+  NTT_ROUTE_GROUPED = 2,   /* the grouped engine wherever it applies */
+  NTT_ROUTE_FMA = 3,       /* CUDA-core (FMA) kernels only: no tensor-core pass */
+  NTT_ROUTE_GENERIC = 4,   /* the generic FMA pass only */
+  NTT_ROUTE_TC = 5         /* a tensor-core pass wherever one applies, including the
+                              forms that are slower than the FMA kernels on GB300 */
+} ntt_route;
+
+/* ntt_plan_desc.flags */
+#define NTT_PLAN_EAGER 1u   /* enqueue every launch on each call instead of replaying a
+                               cached CUDA graph (debugging; each call then first waits for
+                               the previous call of the plan to finish) */
+
 /* Plan description (Algorithm 2's inputs with fixed ranks). */
 typedef struct {
   int d;                 /* tensor order, 2 <= d <= NTT_MAX_D */
@@ -76,6 +95,8 @@ typedef struct {
                             f_{u-K} - f_u <= tol |f_{u-K}| (f in FP64, Gram form).  The
                             refinement iterations always run.  >= 0. */
   int check_every;       /* K of that test; >= 1 when tol > 0 */
+  int route;             /* ntt_route of every stage (0 = NTT_ROUTE_AUTO) */
+  unsigned flags;        /* NTT_PLAN_* bits (0: cached CUDA graph) */
 } ntt_plan_desc;
 
 /* Per-stage statistics, filled by ntt_plan_get_stats after the last call. */
@@ -101,7 +122,7 @@ typedef struct {
 #define NTT_ENGINE_FMA_PASS 0         /* single-problem fused pass, packed FP32 FMAs */
 #define NTT_ENGINE_GROUPED 1          /* grouped engine (register-tiled FMA pass) */
 #define NTT_ENGINE_TC_BF16 2          /* BF16-X tensor-core pass (tcgen05 kind::f16) */
-#define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (opt-in, NTT_PASS=tc) */
+#define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (only with NTT_ROUTE_TC) */
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 
 /* Human-readable name of a status code (static string). */
@@ -132,8 +153,10 @@ ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes);
  * Stage l uses W = core l as its m x r factor and H in the workspace (the
  * last stage writes H straight into the last core), so no reshape copies are
  * made: each reshape of Algorithm 1/2 is a C-order view.  The whole
- * decomposition is one cached CUDA graph per (A, cores, workspace) triple,
- * launched on `stream`. */
+ * decomposition is one cached CUDA graph per (A, cores, workspace) triple
+ * (two triples are kept), launched on `stream`; the graph contains kernel
+ * nodes only.  Capturing a third triple first waits for the last launch of
+ * the graph it replaces. */
 ntt_status ntt_decompose(ntt_plan plan, const float* A, float* const* cores,
                          void* workspace, void* stream);
 
@@ -146,6 +169,8 @@ ntt_status ntt_decompose(ntt_plan plan, const float* A, float* const* cores,
  * call's host-to-device copy runs on the plan's own copy stream, waits only
  * for the call two back to finish reading that slot, and so overlaps the
  * previous call's decomposition; the decomposition waits for its copy.
+ * The slot events belong to the plan: successive host calls of one plan must
+ * use the same workspace (or synchronise `stream` before switching).
  * A_host must stay unchanged until `stream` has passed the call. */
 ntt_status ntt_decompose_host(ntt_plan plan, const float* A_host, float* const* cores_host,
                               double* err_host, void* workspace, void* stream);
@@ -171,6 +196,14 @@ ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype,
 ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
                        float* W, float* H, int iters, float eps_mu, double* obj_dev,
                        void* ws, void* stream);
+
+/* nmf_mu_step with its kernel choice restricted by `route` (ntt_route; the
+ * plan's routes other than NTT_ROUTE_GROUPED, which is a plan-level choice and
+ * acts here as NTT_ROUTE_AUTO).  *engine_out (nullable) receives the
+ * NTT_ENGINE_* of the pass that ran.  Other arguments as for nmf_mu_step. */
+ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
+                             float* W, float* H, int iters, float eps_mu, double* obj_dev,
+                             void* ws, void* stream, int route, int* engine_out);
 
 /* nmf_mu_step without a workspace argument, for callers that cannot allocate
  * device memory (for instance a plugin running inside a host process whose own
@@ -214,6 +247,18 @@ ntt_status nmf_mu_many(int count, const int64_t* m, const int64_t* n, const int*
 
 /* Device status word left in an nmf_mu_step workspace (sync first). */
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out);
+
+/* Failure-detection probe of the bounded device waits (Section III's
+ * distributed design has no counterpart; every kernel of this library bounds
+ * its waits so that a stuck copy or peer ends the kernel with a status word
+ * instead of a hang).  Enqueues one single-CTA kernel on `stream` that starts
+ * a real 256-byte bulk copy from `ws`, waits at most limit_ns (>= 0) for an
+ * mbarrier phase that nothing completes, drains its own copy (bounded by 2 s)
+ * and writes NTT_ERR_TIMEOUT into the workspace's status word -- the path a
+ * pass kernel takes when one of its waits gives up.  ws: an nmf_mu_step
+ * workspace (>= 256 bytes, 256-byte aligned).  A later nmf_mu_step on the
+ * same workspace clears the word. */
+ntt_status ntt_wait_probe(void* ws, int64_t limit_ns, void* stream);
 
 /* Counter-based U[0,1) fill: out[i] = (SplitMix64(key) output i >> 40) * 2^-24
  * with key = SplitMix64(seed) output (stage * 2^20 + restart * 2 + matrix)

@@ -38,11 +38,22 @@ STATUS = {
 }
 NTT_F32, NTT_BF16 = 0, 1
 
+# ntt_route: kernel routing of the MU loops (include/ntt.h)
+ROUTES = {"auto": 0, "pass": 1, "grouped": 2, "fma": 3, "generic": 4, "tc": 5}
+NTT_PLAN_EAGER = 1
+
+
+def _route(route):
+    if route not in ROUTES:
+        raise ValueError(f"route must be one of {sorted(ROUTES)}")
+    return ROUTES[route]
+
 # Every symbol include/ntt.h declares.
 EXPORTS = (
     "ntt_status_string", "ntt_version", "ntt_plan_create", "ntt_plan_workspace_size",
     "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
+    "nmf_mu_step_route", "ntt_wait_probe",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
@@ -70,6 +81,8 @@ class _PlanDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("tol", ctypes.c_double),
         ("check_every", ctypes.c_int),
+        ("route", ctypes.c_int),
+        ("flags", ctypes.c_uint),
     ]
 
 
@@ -145,8 +158,11 @@ def lib():
     L.ntt_plan_destroy.argtypes = [vp]
     L.nmf_mu_workspace_size.argtypes = [i64, i64, i32, i32, psz]
     L.nmf_mu_step.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.nmf_mu_step_route.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp, i32,
+                                    ctypes.POINTER(ctypes.c_int)]
     L.nmf_mu_step_noalloc.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp]
     L.ntt_status_of_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.ntt_wait_probe.argtypes = [vp, i64, vp]
     L.ntt_uniform_init.argtypes = [ctypes.c_uint64, i32, i32, i32, i64, vp, vp]
     L.ntt_reconstruct_workspace_size.argtypes = [i32, p64, p64, psz]
     L.ntt_reconstruct.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp]
@@ -241,7 +257,8 @@ class Plan:
 
 
 def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, tol=0.0,
-                    check_every=10):
+                    check_every=10, route="auto", eager=False):
+    """route: one of ROUTES (ntt_route); eager: enqueue every call instead of a cached graph."""
     dims = tuple(int(n) for n in dims)
     ranks = tuple(int(r) for r in ranks) if ranks is not None else None
     d_arr = _i64arr(dims)
@@ -257,6 +274,8 @@ def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iter
     desc.seed = int(seed)
     desc.tol = float(tol)
     desc.check_every = int(check_every)
+    desc.route = _route(route)
+    desc.flags = NTT_PLAN_EAGER if eager else 0
     h = ctypes.c_void_p()
     _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
     return Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
@@ -317,8 +336,11 @@ def nmf_mu_workspace_size(m, n, r, x_dtype="f32"):
     return b.value
 
 
-def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=None):
-    """`iters` MU iterations on W (m x r) and H (r x n) in place; X is float32 or bfloat16."""
+def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=None, route="auto",
+                engine=None):
+    """`iters` MU iterations on W (m x r) and H (r x n) in place; X is float32 or bfloat16.
+    route: one of ROUTES (nmf_mu_step_route); engine: optional list that receives
+    the name of the pass that ran."""
     import torch
     if X.dim() != 2 or W.dim() != 2 or H.dim() != 2:
         raise ValueError("X, W, H must be matrices")
@@ -330,11 +352,14 @@ def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=N
     if workspace is None:
         workspace = empty_workspace(nmf_mu_workspace_size(m, n, r, xd), X.device)
     optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
-    _check(lib().nmf_mu_step(m, n, r, _dev_ptr(X, None, "X"),
-                             NTT_BF16 if xd == "bf16" else NTT_F32,
-                             _dev_ptr(W, torch.float32, "W"), _dev_ptr(H, torch.float32, "H"),
-                             int(iters), float(eps_mu), optr, _dev_ptr(workspace, None, "ws"),
-                             _stream_ptr(stream)), "nmf_mu_step")
+    eng = ctypes.c_int(-1)
+    _check(lib().nmf_mu_step_route(m, n, r, _dev_ptr(X, None, "X"),
+                                   NTT_BF16 if xd == "bf16" else NTT_F32,
+                                   _dev_ptr(W, torch.float32, "W"), _dev_ptr(H, torch.float32, "H"),
+                                   int(iters), float(eps_mu), optr, _dev_ptr(workspace, None, "ws"),
+                                   _stream_ptr(stream), _route(route), ctypes.byref(eng)), "nmf_mu_step")
+    if engine is not None:
+        engine.append(ENGINES.get(eng.value, eng.value))
     return workspace
 
 
@@ -404,6 +429,13 @@ def ntt_status_of_workspace(workspace):
     _check(lib().ntt_status_of_workspace(_dev_ptr(workspace, None, "ws"), ctypes.byref(v)),
            "ntt_status_of_workspace")
     return STATUS.get(v.value, v.value)
+
+
+def ntt_wait_probe(workspace, limit_ns, stream=None):
+    """Enqueue the bounded-wait probe on an nmf_mu_step workspace: its status
+    word reads NTT_ERR_TIMEOUT once the stream has run it (include/ntt.h)."""
+    _check(lib().ntt_wait_probe(_dev_ptr(workspace, None, "ws"), int(limit_ns), _stream_ptr(stream)),
+           "ntt_wait_probe")
 
 
 def ntt_uniform_init(seed, stage, restart, matrix, out, stream=None):
@@ -599,10 +631,11 @@ def ntt_compression_ratio(dims, ranks):
 
 
 def decompose(A, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, stream=None, tol=0.0,
-              check_every=10):
+              check_every=10, route="auto"):
     """Convenience wrapper: returns (cores, stats) for a CUDA float32 tensor A."""
     import torch
-    plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed, tol, check_every)
+    plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed, tol, check_every,
+                           route)
     ws = empty_workspace(plan.workspace_size(), A.device)
     cores = [torch.empty(s, dtype=torch.float32, device=A.device) for s in plan.core_shapes()]
     ntt_decompose(plan, A.contiguous(), cores, ws, stream)

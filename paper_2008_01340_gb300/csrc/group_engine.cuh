@@ -129,9 +129,19 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
 // Engine scratch of one problem under fixed_split (bytes, 256-byte multiple).
 size_t group_problem_scratch(const GroupShape& shape, int sms);
 
+// Write the device tables of a run (pointers into `scratch` and the problems'
+// buffers) into host memory of plan.table_bytes.  Host only.
+void group_fill_tables(const GroupPlan& plan, const GroupPtrs* ptrs, char* scratch, void* host_tables);
+
+// The Gram launch and `iters` MU iterations of every problem, with the tables
+// already on the device at `dev_tables` (plan.table_bytes).
+ntt_status group_launch(const GroupPlan& plan, char* scratch, const char* dev_tables, int iters, float eps,
+                        cudaStream_t st, int t0 = 0);
+
 // `iters` MU iterations of every problem of the plan.  W and H hold the
 // initial factors; `host_tables` is pinned host memory of plan.table_bytes
 // that must stay untouched until the stream has passed this call's copy.
+// (group_fill_tables, one host-to-device copy into the scratch, group_launch.)
 ntt_status group_run(const GroupPlan& plan, const GroupPtrs* ptrs, char* scratch, void* host_tables,
                      int iters, float eps, cudaStream_t st, int t0 = 0);
 

@@ -393,10 +393,9 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
   return NTT_OK;
 }
 
-ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, void* host_tables,
-                     int iters, float eps, cudaStream_t st, int t0) {
+void group_fill_tables(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, void* host_tables) {
   const int np = (int)pl.probs.size();
-  if (np == 0) return NTT_OK;
+  if (np == 0) return;
   char* h = reinterpret_cast<char*>(host_tables);
   GProb* hp = reinterpret_cast<GProb*>(h + pl.o_prob);
   GComb* hc = reinterpret_cast<GComb*>(h + pl.o_comb);
@@ -489,10 +488,14 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
       ++ti;
     }
   }
-  char* d = scratch + pl.off_tables;
-  if (cudaMemcpyAsync(d, h, pl.table_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(tickets, 0, (size_t)np * sizeof(unsigned), st) != cudaSuccess)
-    return NTT_ERR_CUDA;
+}
+
+ntt_status group_launch(const GroupPlan& pl, char* scratch, const char* d, int iters, float eps,
+                        cudaStream_t st, int t0) {
+  const int np = (int)pl.probs.size();
+  if (np == 0) return NTT_OK;
+  unsigned* tickets = reinterpret_cast<unsigned*>(scratch + pl.off_tickets);
+  if (launch_zero(tickets, (size_t)np * sizeof(unsigned), st) != cudaSuccess) return NTT_ERR_CUDA;
   const GProb* dp = reinterpret_cast<const GProb*>(d + pl.o_prob);
   const GComb* dc = reinterpret_cast<const GComb*>(d + pl.o_comb);
   const GTall* dt = reinterpret_cast<const GTall*>(d + pl.o_tall);
@@ -516,6 +519,16 @@ ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, 
     if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
   }
   return NTT_OK;
+}
+
+ntt_status group_run(const GroupPlan& pl, const GroupPtrs* ptrs, char* scratch, void* host_tables,
+                     int iters, float eps, cudaStream_t st, int t0) {
+  if (pl.probs.empty()) return NTT_OK;
+  group_fill_tables(pl, ptrs, scratch, host_tables);
+  if (cudaMemcpyAsync(scratch + pl.off_tables, host_tables, pl.table_bytes, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return NTT_ERR_CUDA;
+  return group_launch(pl, scratch, scratch + pl.off_tables, iters, eps, st, t0);
 }
 
 }  // namespace ntt

@@ -1,7 +1,6 @@
 // Host side of the fused MU pass: bucket choice, TMA tensor maps, dispatch.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -89,43 +88,38 @@ ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, M
   return NTT_OK;
 }
 
-// The tensor-core pass (FP32 X, m <= 32, r <= 16, TMA-aligned tiles) is
-// selected with NTT_PASS=tc in the environment; the packed-FMA pass is the
-// default.  Measured on GB300: a kind::tf32 M=128 K=8 MMA costs ~56 cycles for
-// any N <= 64, so the 3xTF32 form needs >= 10.5 tensor-pipe cycles per column
-// of a 32-row unfolding against a 9-cycle HBM budget, and the FMA pass is faster.
-static bool tc_enabled() {
-  const char* e = std::getenv("NTT_PASS");
-  return e && std::strcmp(e, "tc") == 0;
-}
-
-// BF16 X with 128 or 256 rows and rank bucket 16 or 32 runs on the BF16
-// tensor-core pass (kind::f16, FP32 accumulation, factors split in three BF16
-// terms); NTT_PASS=fma keeps the packed-FMA pass.  Its stacked form for 16 and
-// 32 rows is selected only with NTT_PASS=tcb: on 16 x 268,435,456 (rank 16) it
-// ran 30.8 iterations/s against 52.3 for the grouped FMA pass -- that shape
-// moves 160 B of H per column against 32 B of X, and one CTA per SM with its
-// H loads in the epilogue leaves the latency exposed.
-static bool tcb_enabled(int MP) {
-  const char* e = std::getenv("NTT_PASS");
-  if (e && std::strcmp(e, "fma") == 0) return false;
-  if (MP <= 32) return e && std::strcmp(e, "tcb") == 0;
+// Which single-problem pass runs an m x n x r problem, by route:
+//  - BF16 X with 128 or 256 rows at rank bucket 16 or 32 runs on the BF16
+//    tensor-core pass (kind::f16, FP32 accumulation, factors split in three
+//    BF16 terms).  Its stacked form for 16 and 32 rows runs only with
+//    NTT_ROUTE_TC: on 16 x 268,435,456 (rank 16) it ran 30.8 iterations/s
+//    against 52.3 for the grouped FMA pass -- that shape moves 160 B of H per
+//    column against 32 B of X, and one CTA per SM with its H loads in the
+//    epilogue leaves the latency exposed.  NTT_ROUTE_FMA / _GENERIC keep the
+//    packed-FMA pass.
+//  - The 3xTF32 tensor-core pass (FP32 X, m <= 64, r <= 16) runs only with
+//    NTT_ROUTE_TC.  Measured on GB300: a kind::tf32 M=128 K=8 MMA costs ~56
+//    cycles for any N <= 64, so the 3xTF32 form needs >= 10.5 tensor-pipe
+//    cycles per column of a 32-row unfolding against a 9-cycle HBM budget, and
+//    the FMA pass is faster.
+//  - FP32 X with at most 32 rows at rank bucket 8 runs on the warp-streamed
+//    pass (mu_pass_narrow.cu) unless the route is NTT_ROUTE_GENERIC.
+static bool tcb_enabled(int MP, int route) {
+  if (route == NTT_ROUTE_FMA || route == NTT_ROUTE_GENERIC) return false;
+  if (MP <= 32) return route == NTT_ROUTE_TC;
   return true;
 }
 
-// FP32 X with at most 32 rows at rank bucket 8 runs on the warp-streamed pass
-// (mu_pass_narrow.cu); NTT_PASS=wide keeps the generic pass.
-static bool narrow_enabled() {
-  const char* e = std::getenv("NTT_PASS");
-  return !(e && std::strcmp(e, "wide") == 0);
-}
+static bool tc_enabled(int route) { return route == NTT_ROUTE_TC; }
+
+static bool narrow_enabled(int route) { return route != NTT_ROUTE_GENERIC; }
 
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tc = 0;
   s->tcb = 0;
   s->narrow = 0;
-  if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP)) {
+  if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP, s->route)) {
     s->tcb = 1;
     s->T = 128;
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
@@ -135,7 +129,7 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
     s->grid = (int)grid;
     return;
   }
-  if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled()) {
+  if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled(s->route)) {
     s->tc = 1;
     s->T = 128;
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
@@ -145,7 +139,7 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
     s->grid = (int)grid;
     return;
   }
-  if (s->tma && !s->bf16 && narrow_pass_supported(s->MP, s->R) && narrow_enabled()) {
+  if (s->tma && !s->bf16 && narrow_pass_supported(s->MP, s->R) && narrow_enabled(s->route)) {
     s->narrow = 1;
     s->T = 256;   // 8 warps x 32-column boxes per CTA round
     const int64_t ntiles = (s->n + s->T - 1) / s->T;

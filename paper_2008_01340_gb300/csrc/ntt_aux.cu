@@ -6,6 +6,8 @@
 //                    split-chain product
 //   small_mm_kernel  C = A B with K <= 32 (chain products of TT cores)
 //   handoff kernels  column L1 normalisation of W folded into H
+//   zero / copy      word fills and copies as kernels (graph nodes that use
+//                    no copy engine)
 #include "ntt_internal.cuh"
 
 namespace ntt {
@@ -16,6 +18,34 @@ __global__ void uniform_kernel(uint64_t key, int64_t count, float* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
     out[i] = uniform24(key, (uint64_t)i);
+}
+
+__global__ void zero_words_kernel(uint32_t* dst, int64_t words) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) dst[i] = 0u;
+}
+
+__global__ void copy_words_kernel(uint32_t* dst, const uint32_t* src, int64_t words) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) dst[i] = src[i];
+}
+
+// One thread: barrier `never` expects an arrival nobody makes; barrier `copy`
+// tracks a real 256-byte bulk copy.  The wait on `never` gives up after
+// limit_ns, the copy is drained, and the timeout is recorded.
+__global__ void wait_probe_kernel(const void* src, int* status, long long limit_ns) {
+  __shared__ __align__(128) uint8_t buf[256];
+  __shared__ __align__(8) uint64_t bars[2];
+  if (threadIdx.x != 0) return;
+  const uint32_t never = smem_u32(&bars[0]), copy = smem_u32(&bars[1]);
+  mbar_init(never, 1);
+  mbar_init(copy, 1);
+  fence_mbar_init();
+  mbar_arrive_expect_tx(copy, 256);
+  bulk_load(smem_u32(buf), src, 256, copy);
+  const bool ok = mbar_wait_bounded(never, 0, limit_ns);
+  const bool drained = mbar_wait_bounded(copy, 0);   // the copy completes by itself
+  if (!ok || !drained) atomicExch(status, kStatusTimeout);
 }
 
 __global__ void cast_bf16_kernel(const float* in, __nv_bfloat16* out, int64_t count) {
@@ -270,6 +300,31 @@ int grid_for(int64_t work, int per_block_items) {
 cudaError_t launch_uniform(uint64_t key, int64_t count, float* out, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   uniform_kernel<<<grid_for(count, kAuxThreads * 4), kAuxThreads, 0, st>>>(key, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* dst, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if ((bytes & 3) || (reinterpret_cast<uintptr_t>(dst) & 3)) return cudaErrorInvalidValue;
+  const int64_t words = (int64_t)(bytes / 4);
+  zero_words_kernel<<<grid_for(words, kAuxThreads * 4), kAuxThreads, 0, st>>>(
+      reinterpret_cast<uint32_t*>(dst), words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if ((bytes & 3) || (reinterpret_cast<uintptr_t>(dst) & 3) || (reinterpret_cast<uintptr_t>(src) & 3))
+    return cudaErrorInvalidValue;
+  const int64_t words = (int64_t)(bytes / 4);
+  copy_words_kernel<<<grid_for(words, kAuxThreads * 4), kAuxThreads, 0, st>>>(
+      reinterpret_cast<uint32_t*>(dst), reinterpret_cast<const uint32_t*>(src), words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(const void* src, int* status, long long limit_ns, cudaStream_t st) {
+  if (reinterpret_cast<uintptr_t>(src) & 15) return cudaErrorInvalidValue;
+  wait_probe_kernel<<<1, 32, 0, st>>>(src, status, limit_ns);
   return cudaGetLastError();
 }
 

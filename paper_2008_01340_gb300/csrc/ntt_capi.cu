@@ -2,7 +2,6 @@
 // CUDA-graph capture of the whole decomposition, statistics, and the
 // reconstruction / relative-error entry points (Eq. (2)-(4)).
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -221,6 +220,8 @@ struct ntt_plan_s {
   uint64_t seed = 0;
   double tol = 0.0;              // stopping test of each stage's main loop (0: fixed count)
   int check = 0;
+  int route = NTT_ROUTE_AUTO;    // ntt_route of every stage
+  bool eager = false;            // NTT_PLAN_EAGER: enqueue every call, no graph
   size_t off_stop = 0;           // one stop word per stage
 
   // A stage's MU loop runs either on the single-problem pass (TMA, phase
@@ -248,12 +249,20 @@ struct ntt_plan_s {
   size_t off_A[2] = {0, 0}, off_cores = 0, ws_bytes_host = 0;   // two input slots (host variant)
   std::vector<size_t> core_off;
   size_t obj_total = 0;
-  // graph cache: two entries, so the host variant's two input slots both stay captured
+  // graph cache: two entries, so the host variant's two input slots both stay
+  // captured.  Each entry owns the mapped pinned host tables of its routed
+  // stages (written once, at capture; a kernel node of its graph uploads them
+  // into the workspace on every launch) and an event recorded after its last
+  // launch, waited for before the entry is recaptured.
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     const void* A = nullptr;
     void* ws = nullptr;
     std::vector<float*> cores;
+    char* h_tab = nullptr;         // host address of the tables
+    char* h_tab_dev = nullptr;     // device address of the same memory
+    cudaEvent_t done = nullptr;
+    bool launched = false;
   };
   Graph graphs[2];
   int graph_victim = 0;
@@ -266,15 +275,19 @@ struct ntt_plan_s {
   int64_t launches = 0;          // kernels per decomposition
   size_t off_chain = 0, off_err = 0;
   size_t off_grp = 0;            // grouped-engine scratch shared by the routed stages
-  char* h_tables = nullptr;      // pinned host tables of the routed stages
-  size_t h_bytes = 0;
+  char* h_eager = nullptr;       // tables of the eager path (host / device address)
+  char* h_eager_dev = nullptr;
+  size_t h_bytes = 0;            // table bytes of all routed stages
   cudaStream_t last_stream = nullptr;
   void* last_ws = nullptr;
   bool ran = false;
 
   ~ntt_plan_s() {
-    for (auto& g : graphs)
+    for (auto& g : graphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.done) cudaEventDestroy(g.done);
+      if (g.h_tab) cudaFreeHost(g.h_tab);
+    }
     if (cap) cudaStreamDestroy(cap);
     if (copy_st) cudaStreamDestroy(copy_st);
     for (int i = 0; i < 2; ++i) {
@@ -283,7 +296,7 @@ struct ntt_plan_s {
     }
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
-    if (h_tables) cudaFreeHost(h_tables);
+    if (h_eager) cudaFreeHost(h_eager);
     cudaGetLastError();
   }
 };
@@ -292,36 +305,35 @@ namespace {
 
 // Which MU loop a stage runs: the grouped engine when its height bucket is at
 // most 256 rows and its rank bucket at least 16 (where it measured faster than
-// the single-problem pass on GB300), else the pass.  NTT_PLAN_ENGINE=pass or
-// =group forces one of them where both apply.
-bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16) {
+// the single-problem pass on GB300), else the pass; BF16 stages the tensor-core
+// pass takes (128/256 rows; with NTT_ROUTE_TC also 16/32 rows) stay on the
+// single-problem path.  The plan's route restricts the choice (ntt_route).
+bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route) {
   const int MP = group_mp_bucket((int)m), R = group_r_bucket(r);
   if (MP < 0 || R < 0) return false;
   if (xbf16 && (!gpass_bf16_supported(MP, R) || n % 8 != 0)) return false;
-  // BF16 stages the tensor-core pass takes (128/256 rows by default, 16/32 rows
-  // with NTT_PASS=tcb) stay on the single-problem path
-  const char* pe = std::getenv("NTT_PASS");
-  const bool fma = pe && std::strcmp(pe, "fma") == 0, tcb = pe && std::strcmp(pe, "tcb") == 0;
-  if (xbf16 && tcb_pass_supported(MP, R) && !fma && (MP >= 128 || tcb)) return false;
-  const char* e = std::getenv("NTT_PLAN_ENGINE");
-  if (e && std::strcmp(e, "pass") == 0) return false;
-  if (e && std::strcmp(e, "group") == 0) return true;
+  if (route == NTT_ROUTE_PASS || route == NTT_ROUTE_GENERIC) return false;
+  if (route == NTT_ROUTE_GROUPED) return true;
+  if (route == NTT_ROUTE_TC && ((xbf16 && tcb_pass_supported(MP, R)) || (!xbf16 && tc_pass_supported(MP, R))))
+    return false;
+  if (route != NTT_ROUTE_FMA && xbf16 && tcb_pass_supported(MP, R) && MP >= 128) return false;
   return MP <= 256 && R >= 16;
 }
 
 // Record the whole decomposition on stream `st` (captured or eager).
+// tab / tab_dev: host and device addresses of the mapped pinned tables of
+// the routed stages (written here; uploaded by a kernel at each stage).
 ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, char* ws,
-                             cudaStream_t st) {
+                             cudaStream_t st, char* tab, const char* tab_dev) {
   int* status = reinterpret_cast<int*>(ws + p->off_status);
   unsigned* tickets = reinterpret_cast<unsigned*>(ws + p->off_tickets);
   double* scal = reinterpret_cast<double*>(ws + p->off_scal);
   double* obj = reinterpret_cast<double*>(ws + p->off_obj);
-  NTT_CUDA_TRY(cudaMemsetAsync(status, 0, 64, st));
-  NTT_CUDA_TRY(cudaMemsetAsync(tickets, 0, 64, st));
   int* stop = reinterpret_cast<int*>(ws + p->off_stop);
-  NTT_CUDA_TRY(cudaMemsetAsync(stop, 0, NTT_MAX_D * sizeof(int), st));
+  // status word, tickets and stop words are consecutive in the layout
+  NTT_CUDA_TRY(launch_zero(status, p->off_stop + NTT_MAX_D * sizeof(int) - p->off_status, st));
   const int d = p->d;
-  int64_t launches = 0;
+  int64_t launches = 1;
   // External event nodes: a plain record on a capturing stream would only
   // mark a capture dependency and put no timing node into the graph.
   auto rec = [&](int i) -> cudaError_t {
@@ -375,8 +387,10 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
       g.scratch = nullptr;
       g.obj = obj + S.obj_off;
       g.xnorm2 = xnorm2;
-      launches += 1;   // the engine's own Gram launch
-      return group_run(rt.gp, &g, ws, p->h_tables + rt.host_off, iters, p->eps, st, t0);
+      group_fill_tables(rt.gp, &g, ws, tab + rt.host_off);
+      NTT_CUDA_TRY(launch_copy_words(ws + rt.gp.off_tables, tab_dev + rt.host_off, rt.gp.table_bytes, st));
+      launches += 3;   // table upload, ticket reset and the engine's own Gram launch
+      return group_launch(rt.gp, ws, ws + rt.gp.off_tables, iters, p->eps, st, t0);
     };
     if (p->xdt == NTT_BF16) {
       __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
@@ -403,9 +417,22 @@ ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, ch
   return NTT_OK;
 }
 
-bool eager_mode() {
-  const char* e = std::getenv("NTT_EAGER");
-  return e && e[0] == '1';
+// Mapped pinned host memory: *host for the host, *dev for kernels.
+ntt_status alloc_mapped(size_t bytes, char** host, char** dev) {
+  void* h = nullptr;
+  void* d = nullptr;
+  if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return NTT_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(h);
+    return NTT_ERR_CUDA;
+  }
+  *host = reinterpret_cast<char*>(h);
+  *dev = reinterpret_cast<char*>(d);
+  return NTT_OK;
 }
 
 }  // namespace
@@ -447,6 +474,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (desc->x_dtype != NTT_F32 && desc->x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
   if (desc->refine_iters < 0) return NTT_ERR_INVALID_ARG;
   if (!(desc->tol >= 0.0) || desc->tol > 1e300) return NTT_ERR_INVALID_ARG;
+  if (desc->route < NTT_ROUTE_AUTO || desc->route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
+  if (desc->flags & ~NTT_PLAN_EAGER) return NTT_ERR_INVALID_ARG;
   if (desc->tol > 0.0 && desc->check_every < 1) return NTT_ERR_INVALID_ARG;
   const int64_t* dims = desc->dims;
   const int64_t* ranks = desc->ranks;
@@ -472,6 +501,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->seed = desc->seed;
   p->tol = desc->tol;
   p->check = desc->tol > 0.0 ? desc->check_every : 0;
+  p->route = desc->route;
+  p->eager = (desc->flags & NTT_PLAN_EAGER) != 0;
   const int sms = device_sms();
   size_t max_part = 1, max_red = 1, maxH[2] = {1, 1}, max_xb = 1;
   for (int s = 0; s < d - 1; ++s) {
@@ -485,6 +516,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
       delete p;
       return e;
     }
+    S.f32.route = p->route;
+    S.bf16.route = p->route;
     S.iters_total = p->iters + p->refine;
     S.obj_off = p->obj_total;
     p->obj_total += S.iters_total;
@@ -506,7 +539,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
       ntt_plan_s::Route& rt = xb ? S.gbf16 : S.gf32;
       if (xb && p->xdt != NTT_BF16) continue;
       if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
-      if (!plan_route_group(S.m, S.n, S.r, xb != 0)) continue;
+      if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route)) continue;
       // a main loop with a stopping test runs on the single-problem passes
       const bool main_loop = xb != 0 || p->xdt != NTT_BF16;
       if (main_loop && p->tol > 0.0) continue;
@@ -593,11 +626,11 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
     p->ev.assign(4 * d + 2, nullptr);
     for (auto& e : p->ev) NTT_CUDA_TRY(cudaEventCreate(&e));
   }
-  if (p->h_bytes && !p->h_tables) NTT_CUDA_TRY(cudaMallocHost(&p->h_tables, p->h_bytes));
-  if (eager_mode()) {
-    // the engine's pinned tables are rewritten: the previous run must have read them
+  if (p->eager) {
+    // the eager tables are rewritten: the previous run must have read them
     if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
-    NTT_TRY(enqueue_decompose(p, A, cores, ws, st));
+    if (p->h_bytes && !p->h_eager) NTT_TRY(alloc_mapped(p->h_bytes, &p->h_eager, &p->h_eager_dev));
+    NTT_TRY(enqueue_decompose(p, A, cores, ws, st, p->h_eager, p->h_eager_dev));
   } else {
     ntt_plan_s::Graph* G = nullptr;
     for (auto& g : p->graphs) {
@@ -608,14 +641,19 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
     if (!G) {
       G = &p->graphs[p->graph_victim];
       p->graph_victim ^= 1;
+      // the entry's tables are rewritten by the capture: its last launch must be done
+      if (G->launched) NTT_CUDA_TRY(cudaEventSynchronize(G->done));
+      G->launched = false;
       if (G->exec) {
         cudaGraphExecDestroy(G->exec);
         G->exec = nullptr;
       }
+      if (!G->done) NTT_CUDA_TRY(cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming));
+      if (p->h_bytes && !G->h_tab) NTT_TRY(alloc_mapped(p->h_bytes, &G->h_tab, &G->h_tab_dev));
       if (!p->cap) NTT_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
       cudaGraph_t g = nullptr;
       NTT_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-      ntt_status e = enqueue_decompose(p, A, cores, ws, p->cap);
+      ntt_status e = enqueue_decompose(p, A, cores, ws, p->cap, G->h_tab, G->h_tab_dev);
       cudaError_t ce = cudaStreamEndCapture(p->cap, &g);
       if (e != NTT_OK) {
         if (g) cudaGraphDestroy(g);
@@ -637,6 +675,8 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
       G->cores.assign(cores, cores + d);
     }
     NTT_CUDA_TRY(cudaGraphLaunch(G->exec, st));
+    NTT_CUDA_TRY(cudaEventRecord(G->done, st));
+    G->launched = true;
   }
   p->last_stream = st;
   p->last_ws = workspace;
@@ -669,20 +709,30 @@ ntt_status ntt_decompose_host(ntt_plan p, const float* A_host, float* const* cor
   NTT_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->slot_free[slot], 0));   // never recorded: no wait
   NTT_CUDA_TRY(cudaMemcpyAsync(A_dev, A_host, abytes, cudaMemcpyHostToDevice, p->copy_st));
   NTT_CUDA_TRY(cudaEventRecord(p->slot_ready[slot], p->copy_st));
-  NTT_CUDA_TRY(cudaStreamWaitEvent(st, p->slot_ready[slot], 0));
-  NTT_TRY(ntt_decompose(p, A_dev, cdev.data(), workspace, stream));
-  if (err_host) {
-    double* err_dev = reinterpret_cast<double*>(ws + p->off_err);
-    NTT_TRY(ntt_rel_error(d, p->dims.data(), p->ranks.data(), cdev.data(), A_dev, err_dev,
-                          ws + p->off_chain, stream));
-    NTT_CUDA_TRY(cudaMemcpyAsync(err_host, err_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // From here on the slot's free event is recorded on every return path: the
+  // next copy into this slot must wait for whatever of this call was enqueued.
+  auto body = [&]() -> ntt_status {
+    NTT_CUDA_TRY(cudaStreamWaitEvent(st, p->slot_ready[slot], 0));
+    NTT_TRY(ntt_decompose(p, A_dev, cdev.data(), workspace, stream));
+    if (err_host) {
+      double* err_dev = reinterpret_cast<double*>(ws + p->off_err);
+      NTT_TRY(ntt_rel_error(d, p->dims.data(), p->ranks.data(), cdev.data(), A_dev, err_dev,
+                            ws + p->off_chain, stream));
+      NTT_CUDA_TRY(cudaMemcpyAsync(err_host, err_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    for (int k = 0; k < d; ++k) {
+      const size_t cb = (size_t)p->ranks[k] * p->dims[k] * p->ranks[k + 1] * 4;
+      NTT_CUDA_TRY(cudaMemcpyAsync(cores_host[k], cdev[k], cb, cudaMemcpyDeviceToHost, st));
+    }
+    return NTT_OK;
+  };
+  const ntt_status res = body();
+  // slot read by the graph and Eq. (3); recorded even when the call failed
+  if (cudaEventRecord(p->slot_free[slot], st) != cudaSuccess) {
+    cudaGetLastError();
+    if (res == NTT_OK) return NTT_ERR_CUDA;
   }
-  for (int k = 0; k < d; ++k) {
-    const size_t cb = (size_t)p->ranks[k] * p->dims[k] * p->ranks[k + 1] * 4;
-    NTT_CUDA_TRY(cudaMemcpyAsync(cores_host[k], cdev[k], cb, cudaMemcpyDeviceToHost, st));
-  }
-  NTT_CUDA_TRY(cudaEventRecord(p->slot_free[slot], st));   // slot read by the graph and Eq. (3)
-  return NTT_OK;
+  return res;
 }
 
 ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
@@ -763,7 +813,15 @@ ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype,
 ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
                        float* H, int iters, float eps_mu, double* obj_dev, void* ws,
                        void* stream) {
+  return nmf_mu_step_route(m, n, r, X, x_dtype, W, H, iters, eps_mu, obj_dev, ws, stream,
+                           NTT_ROUTE_AUTO, nullptr);
+}
+
+ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
+                             float* H, int iters, float eps_mu, double* obj_dev, void* ws,
+                             void* stream, int route, int* engine_out) {
   if (!X || !W || !H || !ws || iters < 0 || !(eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
+  if (route < NTT_ROUTE_AUTO || route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
   if (x_dtype != NTT_F32 && x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
   if (r > m || r > n) return NTT_ERR_RANK_INFEASIBLE;
@@ -773,8 +831,8 @@ ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_d
   MuWs L = mu_ws_layout(s, &total);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
-  NTT_CUDA_TRY(cudaMemsetAsync(w + L.status, 0, 64, st));
-  NTT_CUDA_TRY(cudaMemsetAsync(w + L.tickets, 0, 64, st));
+  // status word and tickets are consecutive in the layout
+  NTT_CUDA_TRY(launch_zero(w + L.status, L.tickets + 64 - L.status, st));
   unsigned* tickets = reinterpret_cast<unsigned*>(w + L.tickets);
   double* scal = reinterpret_cast<double*>(w + L.scal);
   if (obj_dev)
@@ -792,7 +850,8 @@ ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_d
   dev.xnorm2 = scal;
   dev.status = reinterpret_cast<int*>(w + L.status);
   NTT_CUDA_TRY(launch_gram(s, dev, st));
-  return run_mu_iters(s, dev, eps_mu, iters, 0, st);
+  s.route = route;
+  return run_mu_iters(s, dev, eps_mu, iters, 0, st, engine_out);
 }
 
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out) {
@@ -800,6 +859,15 @@ ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out) {
   int v = 0;
   NTT_CUDA_TRY(cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost));
   *out = (ntt_status)v;
+  return NTT_OK;
+}
+
+ntt_status ntt_wait_probe(void* ws, int64_t limit_ns, void* stream) {
+  if (!ws || limit_ns < 0 || (reinterpret_cast<uintptr_t>(ws) % 256)) return NTT_ERR_INVALID_ARG;
+  // the status word is the first word of an nmf_mu_step workspace; the probe
+  // copies the 256 bytes that start there
+  NTT_CUDA_TRY(launch_wait_probe(ws, reinterpret_cast<int*>(ws), (long long)limit_ns,
+                                 reinterpret_cast<cudaStream_t>(stream)));
   return NTT_OK;
 }
 
@@ -859,7 +927,7 @@ ntt_status ntt_rel_error(int d, const int64_t* dims, const int64_t* ranks,
   const float *L, *R;
   NTT_TRY(build_chain(d, dims, ranks, cores, c, w, &L, &R, st));
   unsigned* ticket = reinterpret_cast<unsigned*>(w + c.ticket);
-  NTT_CUDA_TRY(cudaMemsetAsync(ticket, 0, 64, st));
+  NTT_CUDA_TRY(launch_zero(ticket, 64, st));
   return resid_into(A, 0, L, R, c.rows, c.cols, (int)ranks[c.s], 1, 1.0,
                     reinterpret_cast<double*>(w + c.acc), err_dev,
                     reinterpret_cast<double*>(w + c.part64), ticket, st);

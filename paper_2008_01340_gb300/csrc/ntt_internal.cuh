@@ -97,14 +97,24 @@ __device__ __forceinline__ long long global_ns() {
   return t;
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of an mbarrier, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completion counted on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -283,6 +293,7 @@ struct MuShape {
   int tc = 0;        // tensor-core (tcgen05) pass instead of the FMA pass
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
   int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
+  int route = NTT_ROUTE_AUTO;   // ntt_route restricting the pass choice
   size_t smem = 0;   // dynamic shared memory of the pass kernel
   int part_stride() const { return (MP + R) * R; }
 };
@@ -338,6 +349,18 @@ cudaError_t launch_mu_pass_narrow(const MuShape& s, const MuDev& d, float eps, c
                                   const CUtensorMap& mh, cudaStream_t st);
 
 cudaError_t launch_uniform(uint64_t key, int64_t count, float* out, cudaStream_t st);
+// Zero `bytes` (a multiple of 4) at a 4-byte aligned device address by a
+// kernel, so a captured graph holds no memset node.
+cudaError_t launch_zero(void* dst, size_t bytes, cudaStream_t st);
+// Copy `bytes` (a multiple of 4) from mapped pinned host memory (a device
+// pointer of it) to device memory by a kernel, so a captured graph holds no
+// memcpy node that could queue behind a large transfer on a copy engine.
+cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t st);
+// Failure-detection probe: one CTA starts a real bulk copy of `src` (256
+// bytes, 16-byte aligned), waits at most limit_ns for an mbarrier that nothing
+// arrives at, then drains its copy (bounded by kWaitLimitNs) and sets *status
+// to NTT_ERR_TIMEOUT -- the path every kernel takes when a wait gives up.
+cudaError_t launch_wait_probe(const void* src, int* status, long long limit_ns, cudaStream_t st);
 cudaError_t launch_cast_bf16(const float* in, __nv_bfloat16* out, int64_t count, cudaStream_t st);
 
 // Sum-of-squares / residual / reconstruction over an M x N matrix X (FP32 or

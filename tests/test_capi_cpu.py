@@ -83,6 +83,18 @@ def test_plan_validation(lib):
         assert e.value.code == 1
     ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, tol=1e-3, check_every=5).destroy()
     ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, tol=0.0, check_every=0).destroy()
+    # kernel routes and flags are plan fields validated on the host
+    for route in ntt.ROUTES:
+        ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, route=route, eager=True).destroy()
+    with pytest.raises(ValueError):
+        ntt.ntt_plan_create((8, 8), (1, 2, 1), 10, route="fastest")
+    for route, flags in ((6, 0), (-1, 0), (0, 2)):
+        d_arr, r_arr = ntt._i64arr((8, 8)), ntt._i64arr((1, 2, 1))
+        desc = ntt._PlanDesc(d=2, dims=ctypes.cast(d_arr, ctypes.POINTER(ctypes.c_int64)),
+                             ranks=ctypes.cast(r_arr, ctypes.POINTER(ctypes.c_int64)), iters=10,
+                             eps_mu=1e-12, route=route, flags=flags)
+        h = ctypes.c_void_p()
+        assert lib.ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)) == 1
 
 
 def test_workspace_sizes(lib):
@@ -108,6 +120,10 @@ def test_null_arguments_rejected_without_launch(lib):
     assert lib.nmf_mu_step(8, 8, 2, None, 0, None, None, 1, ctypes.c_float(1e-12), None, None, None) == 1
     assert lib.ntt_plan_workspace_size(None, None) == 1
     assert lib.ntt_uniform_init(1, 0, 0, 2, 10, vp(16), None) == 1   # bad matrix id
+    assert lib.ntt_wait_probe(None, 1000, None) == 1
+    assert lib.ntt_wait_probe(vp(256), -5, None) == 1
+    assert lib.nmf_mu_step_route(8, 8, 2, vp(256), 0, vp(256), vp(256), 1, ctypes.c_float(1e-12), None,
+                                 vp(256), None, 9, None) == 1                              # bad route
 
 
 def test_batch_validation(lib):

@@ -115,8 +115,8 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
-def _decompose(ntt, A, ranks, iters, refine, seed):
-    plan = ntt.ntt_plan_create(A.shape, ranks, iters, 1e-12, "bf16", refine, seed)
+def _decompose(ntt, A, ranks, iters, refine, seed, route="auto"):
+    plan = ntt.ntt_plan_create(A.shape, ranks, iters, 1e-12, "bf16", refine, seed, route=route)
     ws = ntt.empty_workspace(plan.workspace_size())
     cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
     ntt.ntt_decompose(plan, torch.from_numpy(np.ascontiguousarray(A).ravel()).cuda(), cores, ws)
@@ -133,18 +133,17 @@ def c3_small():
 
 
 @pytest.mark.parametrize("kernel", ["default", "fma"])
-def test_c3_recipe_16x6_per_iterate_matches_oracle_precision_form(ntt, c3_small, monkeypatch, kernel):
+def test_c3_recipe_16x6_per_iterate_matches_oracle_precision_form(ntt, c3_small, kernel):
     A, ranks, seed = c3_small
-    if kernel == "fma":
-        monkeypatch.setenv("NTT_PASS", "fma")
-    cg = _decompose(ntt, A, ranks, 10, 2, seed)
+    cg = _decompose(ntt, A, ranks, 10, 2, seed, route="fma" if kernel == "fma" else "auto")
     co, _ = oracle.ntt_decompose(A, ranks, 10, seed=seed, record=False, x_precision="bf16", refine=2)
     errs = [_rel(g, o) for g, o in zip(cg, co)]
     print(f"16^6 precision form, {kernel} kernels: per-core errors " + " ".join(f"{e:.2e}" for e in errs))
-    # core k's unfolding carries the FP32 rounding differences of stages 1..k-1,
-    # which each stage's MU iterations amplify: the bound grows geometrically
+    # core k's unfolding carries the FP32 rounding differences of stages 1..k-1:
+    # the per-iterate bound of one NMF (1e-4) scaled by the number of stages
+    # whose rounding the core has seen, as in the FP32 nTT parity tests
     for k, e in enumerate(errs):
-        assert e <= 1e-4 * 2 ** k, f"core {k}: {e:.2e}"
+        assert e <= 1e-4 * (k + 1), f"core {k}: {e:.2e}"
 
 
 def test_c3_recipe_16x6_final_error_matches_oracle_precision_form(ntt, c3_small):

@@ -85,12 +85,12 @@ SHAPES = [
 ]
 
 
-def _run_gpu_mu(ntt, X, W0, H0, iters, obj=True):
+def _run_gpu_mu(ntt, X, W0, H0, iters, obj=True, route="auto", engine=None):
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     Wd = torch.from_numpy(W0.astype(np.float32)).cuda()
     Hd = torch.from_numpy(H0.astype(np.float32)).cuda()
     od = torch.zeros(max(iters, 1), dtype=torch.float64, device="cuda") if obj else None
-    ws = ntt.nmf_mu_step(Xd, Wd, Hd, iters, 1e-12, od)
+    ws = ntt.nmf_mu_step(Xd, Wd, Hd, iters, 1e-12, od, route=route, engine=engine)
     torch.cuda.synchronize()
     assert ntt.ntt_status_of_workspace(ws) == "NTT_OK"
     return Wd.cpu().numpy(), Hd.cpu().numpy(), (od.cpu().numpy() if obj else None)
@@ -177,9 +177,10 @@ def test_mu_bf16_x(ntt, m, n, r):
 
 # ------------------------------------------------------------------ whole nTT
 
-def _decompose(ntt, A, ranks, iters, seed, x_dtype="f32", refine=0, tol=0.0, check_every=10):
+def _decompose(ntt, A, ranks, iters, seed, x_dtype="f32", refine=0, tol=0.0, check_every=10, route="auto",
+               eager=False):
     dims = A.shape
-    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, seed, tol, check_every)
+    plan = ntt.ntt_plan_create(dims, ranks, iters, 1e-12, x_dtype, refine, seed, tol, check_every, route, eager)
     ws = ntt.empty_workspace(plan.workspace_size())
     cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -286,15 +287,26 @@ def test_ntt_stopping_test_matches_oracle(ntt, x_dtype, refine):
     assert [st["iters"] for st in stats0["stages"]] == [iters + refine] * 2
 
 
-def test_ntt_host_variant_equals_device(ntt):
+HOST_CASES = [
+    # (dims, ranks, x_dtype, refine): small ranks (single-problem passes only);
+    # a first stage routed to the grouped engine (16 rows, rank 16); the
+    # precision form with a BF16 tensor-core stage and grouped stages
+    ((8, 9, 10, 7), (1, 4, 5, 3, 1), "f32", 0),
+    ((16, 16, 16, 16), (1, 16, 16, 16, 1), "f32", 0),
+    ((16, 8, 16, 16), (1, 16, 16, 16, 1), "bf16", 2),
+]
+
+
+@pytest.mark.parametrize("dims,ranks,x_dtype,refine", HOST_CASES)
+def test_ntt_host_variant_equals_device(ntt, dims, ranks, x_dtype, refine):
     """Host-buffer calls issued back to back (A1, A2, A1, no sync between them:
     the input copies alternate between two slots and overlap the previous
-    call's compute) each give exactly the device-buffer result of their input."""
-    dims, ranks = (8, 9, 10, 7), (1, 4, 5, 3, 1)
+    call's compute; each slot has its own cached graph and table upload) each
+    give exactly the device-buffer result of their input."""
     A1, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=8)
     A2, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=9)
-    ref = [_decompose(ntt, A, ranks, 30, 5)[0] for A in (A1, A2)]
-    plan = ntt.ntt_plan_create(dims, ranks, 30, 1e-12, "f32", 0, 5)
+    ref = [_decompose(ntt, A, ranks, 30, 5, x_dtype=x_dtype, refine=refine)[0] for A in (A1, A2)]
+    plan = ntt.ntt_plan_create(dims, ranks, 30, 1e-12, x_dtype, refine, 5)
     ws = ntt.empty_workspace(plan.workspace_size_host())
     Ah = [torch.from_numpy(A).pin_memory() for A in (A1, A2)]
     outs = []
@@ -306,6 +318,39 @@ def test_ntt_host_variant_equals_device(ntt):
     for which, ch in outs:
         for a, b in zip(ref[which], ch):
             assert np.array_equal(a, b.numpy())
+
+
+@pytest.mark.parametrize("dims,ranks,x_dtype,refine", HOST_CASES[1:])
+def test_ntt_alternating_workspaces_and_recapture(ntt, dims, ranks, x_dtype, refine):
+    """Device-buffer calls of one plan on three (A, workspace) pairs issued back
+    to back without a sync (the third capture replaces a cached graph whose
+    launch may still be queued), then the first pair again: every call gives
+    bitwise the result of a fresh plan on its input."""
+    As = [synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=s)[0] for s in (21, 22, 23)]
+    ref = [_decompose(ntt, A, ranks, 20, 6, x_dtype=x_dtype, refine=refine)[0] for A in As]
+    plan = ntt.ntt_plan_create(dims, ranks, 20, 1e-12, x_dtype, refine, 6)
+    wss = [ntt.empty_workspace(plan.workspace_size()) for _ in range(3)]
+    Ads = [torch.from_numpy(A).cuda() for A in As]
+    outs = []
+    for which in (0, 1, 2, 0, 1):
+        cores = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.core_shapes()]
+        ntt.ntt_decompose(plan, Ads[which], cores, wss[which])
+        outs.append((which, cores))
+    torch.cuda.synchronize()
+    for which, cores in outs:
+        for a, b in zip(ref[which], cores):
+            assert np.array_equal(a, b.cpu().numpy())
+
+
+def test_ntt_eager_equals_graph(ntt):
+    """A plan with NTT_PLAN_EAGER (every launch enqueued per call) gives bitwise
+    the cached-graph result, on a plan with a grouped-engine stage."""
+    dims, ranks = (16, 16, 16, 16), (1, 16, 16, 16, 1)
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=24)
+    a = _decompose(ntt, A, ranks, 15, 3)[0]
+    b = _decompose(ntt, A, ranks, 15, 3, eager=True)[0]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
 
 
 def test_ntt_repeat_is_bitwise_identical(ntt):
@@ -419,15 +464,15 @@ def test_c2_full_size_decompose_properties(ntt, c2_full):
 
 @pytest.mark.parametrize("m,n,r", [(32, 70000, 8), (16, 20000, 16), (24, 9000, 8), (32, 8192, 12),
                                    (32, 9000 * 128, 8)])
-def test_tensor_core_and_fma_passes_agree(ntt, m, n, r, monkeypatch):
-    """The tcgen05 pass (m <= 32, r <= 16, selected by NTT_PASS=tc) and the
-    default FMA pass both match the oracle's iterates within the FP32 tolerance."""
+def test_tensor_core_and_fma_passes_agree(ntt, m, n, r):
+    """The 3xTF32 tcgen05 pass (m <= 32, r <= 16, route "tc") and the default
+    FMA pass both match the oracle's iterates within the FP32 tolerance."""
     X = _x_matrix("lowrank", m, n, 77 + m)
     W0 = synth.uniform_matrix((m, r), 78)
     H0 = synth.uniform_matrix((r, n), 79)
-    monkeypatch.setenv("NTT_PASS", "tc")
-    Wt, Ht, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
-    monkeypatch.delenv("NTT_PASS")
+    eng = []
+    Wt, Ht, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="tc", engine=eng)
+    assert eng == ["tc_tf32"]
     Wf, Hf, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
     Wo, Ho, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
     for Wg, Hg in ((Wt, Ht), (Wf, Hf)):
@@ -439,19 +484,20 @@ def test_tensor_core_and_fma_passes_agree(ntt, m, n, r, monkeypatch):
 # 32-column box, fewer boxes than warps, and many boxes per warp
 @pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (20, 36004, 5), (16, 8196, 8), (9, 100, 2),
                                    (32, 64, 8), (32, 2_000_000, 8), (1, 4096, 1)])
-def test_narrow_and_wide_passes_agree(ntt, m, n, r, monkeypatch):
+def test_narrow_and_wide_passes_agree(ntt, m, n, r):
     """The warp-streamed pass (FP32 X, <= 32 rows, rank <= 8: the default there)
-    and the generic pass (NTT_PASS=wide) both match the oracle's iterates within
-    the FP32 tolerance, and the narrow pass repeats bitwise."""
+    and the generic pass (route "generic") both match the oracle's iterates
+    within the FP32 tolerance, and the narrow pass repeats bitwise."""
     X = _x_matrix("lowrank", m, n, 91 + m)
     W0 = synth.uniform_matrix((m, r), 92)
     H0 = synth.uniform_matrix((r, n), 93)
-    Wn, Hn, on = _run_gpu_mu(ntt, X, W0, H0, 10)
+    eng = []
+    Wn, Hn, on = _run_gpu_mu(ntt, X, W0, H0, 10, engine=eng)
     Wn2, Hn2, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
     assert np.array_equal(Wn, Wn2) and np.array_equal(Hn, Hn2)
-    monkeypatch.setenv("NTT_PASS", "wide")
-    Ww, Hw, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
-    monkeypatch.delenv("NTT_PASS")
+    Ww, Hw, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="generic", engine=eng)
+    if n % 4 == 0:   # TMA-aligned rows: the narrow pass takes the default route
+        assert eng == ["fma_narrow", "fma_pass"]
     Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
     for Wg, Hg in ((Wn, Hn), (Ww, Hw)):
         assert _fro_rel(Wg, Wo) <= REL_ITERATE
@@ -470,20 +516,29 @@ def test_narrow_pass_reported_for_first_stage(ntt):
 
 
 @pytest.mark.parametrize("x_dtype,refine", [("f32", 0), ("bf16", 3)])
-def test_plan_engine_routes_agree(ntt, monkeypatch, x_dtype, refine):
+def test_plan_engine_routes_agree(ntt, x_dtype, refine):
     """Stages with <= 256 rows and rank >= 16 run on the grouped engine by default;
-    forcing the single-problem pass everywhere gives the same iterates within
-    rounding (10 MU iterations per stage, per-core relative 1e-4 x stage index)."""
+    every route (single-problem passes only, grouped wherever it applies, FMA
+    only, generic pass only, tensor cores wherever they apply) gives the same
+    iterates within rounding (10 MU iterations per stage, per-core relative
+    1e-4 x stage index), and each route reports the engines it allows."""
     dims, ranks = (16, 16, 16, 16, 16), (1, 8, 16, 16, 8, 1)
     A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=12)
     out = {}
-    for engine in ("pass", "group"):
-        monkeypatch.setenv("NTT_PLAN_ENGINE", engine)
-        cores, stats, *_ = _decompose(ntt, A, ranks, 10, 7, x_dtype=x_dtype, refine=refine)
+    for route in ("auto", "pass", "grouped", "fma", "generic", "tc"):
+        cores, stats, *_ = _decompose(ntt, A, ranks, 10, 7, x_dtype=x_dtype, refine=refine, route=route)
         assert stats["status"] == "NTT_OK"
-        out[engine] = cores
-    for k, (a, b) in enumerate(zip(out["group"], out["pass"])):
-        assert _fro_rel(a, b) <= 1e-4 * (k + 1), f"core {k}: {_fro_rel(a, b):.2e}"
+        engines = [st["engine"] for st in stats["stages"]]
+        if route in ("pass", "generic"):
+            assert "grouped" not in engines
+        if route == "generic":
+            assert set(engines) == {"fma_pass"}
+        if route == "fma":
+            assert not {"tc_bf16", "tc_tf32"} & set(engines)
+        out[route] = cores
+    for route in out:
+        for k, (a, b) in enumerate(zip(out[route], out["auto"])):
+            assert _fro_rel(a, b) <= 1e-4 * (k + 1), f"{route} core {k}: {_fro_rel(a, b):.2e}"
 
 
 def test_mu_bf16_tensor_core_pass_repeats_bitwise(ntt):
@@ -534,18 +589,19 @@ def test_mu_bf16_tensor_core_pass_long_accumulation(ntt):
 
 
 @pytest.mark.parametrize("m,n,r", [(16, 8192, 16), (32, 20008, 32), (12, 4096, 12), (24, 40960, 20)])
-def test_mu_bf16_stacked_tensor_core_form(ntt, monkeypatch, m, n, r):
-    """The stacked form of the BF16 tensor-core pass (16/32 rows; opt-in with
-    NTT_PASS=tcb) against the oracle on the BF16-rounded X, 10 iterations."""
-    monkeypatch.setenv("NTT_PASS", "tcb")
+def test_mu_bf16_stacked_tensor_core_form(ntt, m, n, r):
+    """The stacked form of the BF16 tensor-core pass (16/32 rows; route "tc")
+    against the oracle on the BF16-rounded X, 10 iterations."""
     X = _x_matrix("lowrank", m, n, 31)
     Xb = torch.from_numpy(X).to(torch.bfloat16)
     W0 = synth.uniform_matrix((m, r), 32)
     H0 = synth.uniform_matrix((r, n), 33)
     Wd = torch.from_numpy(W0).cuda()
     Hd = torch.from_numpy(H0).cuda()
-    ntt.nmf_mu_step(Xb.cuda(), Wd, Hd, 10)
+    eng = []
+    ntt.nmf_mu_step(Xb.cuda(), Wd, Hd, 10, route="tc", engine=eng)
     torch.cuda.synchronize()
+    assert eng == ["tc_bf16"]
     Wo, Ho, _ = oracle.nmf_mu(Xb.to(torch.float64).numpy(), W0, H0, 10)
     assert _fro_rel(Wd.cpu().numpy(), Wo) <= REL_ITERATE
     assert _fro_rel(Hd.cpu().numpy(), Ho) <= REL_ITERATE
