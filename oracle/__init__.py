@@ -2,7 +2,12 @@
 
 from .ntt_oracle import *  # noqa: F401,F403
 from .ntt_oracle import (  # noqa: F401
+    BCD_DELTA,
     EPS_MU,
+    bcd_nmf,
+    select_rank,
+    singular_values,
+    spectral_norm_sym,
     compression_ratio,
     handoff_normalize,
     init_columns_H,

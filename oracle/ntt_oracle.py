@@ -22,6 +22,14 @@ of the paper it restates:
 * precision form (not in the paper, whose experiments are FP32: each unfolding
   rounded to bfloat16, the MU iterations on it, then refinement iterations on
   the unrounded unfolding)                          -> bf16_round, ntt_decompose(x_precision=)
+* Algorithm 2's rank rule: r_l = the smallest k with
+  sqrt(sigma_{k+1}^2 + ... + sigma_N^2) / sqrt(sigma_1^2 + ... + sigma_N^2) <= eps,
+  sigma_i the singular values of X_l, N = min(m, n)
+                                                   -> singular_values, select_rank,
+                                                      ntt_decompose(ranks=None, eps_rank=)
+* Algorithm 3 (distBCDnmf): block coordinate descent with prox-linear
+  (projected gradient) block updates, extrapolation and the restart test,
+  read through the method it cites (Xu & Yin 2013)  -> bcd_nmf, ntt_decompose(solver="bcd")
 
 Readings where the paper is silent or garbled (the list is repeated in the
 design notes):
@@ -31,7 +39,23 @@ design notes):
   column is left as it is;
 * the unfolding X_l is (r_{l-1} n_l) x prod_{j>l} n_j (Algorithm 2's comment on
   S is inconsistent; this is the shape its reshape produces);
-* best restart = lowest final objective, ties to the lowest restart index.
+* best restart = lowest final objective, ties to the lowest restart index;
+* rank rule: k >= 1 (a rank-0 factor is no NMF); an all-zero X gets rank 1;
+  an optional cap min(k, rank_cap) is this library's (the built kernels go to
+  rank 32), not the paper's;
+* Algorithm 3 (its listing is garbled in places) as APG-BCD: the W step is
+  max(0, W_m - (W_m HH^T - XH^T) / ||HH^T||_2) (the printed line drops the
+  gradient), the H step max(0, H_m - (W^TW H_m - W^TX) / ||W^TW||_2) (the
+  printed square root is read as the same spectral norm), the initial
+  objective is 1/2 ||X||_F^2 (printed without the square); an iteration whose
+  objective is >= the last accepted one is rejected and the next one starts
+  from the last accepted iterate without extrapolation (the "correction");
+  otherwise t <- (1 + sqrt(1 + 4 t^2)) / 2, w = (t_old - 1) / t and each block
+  is extrapolated by min(w, delta sqrt(L_prev / L)) with L its Lipschitz
+  constant of this iteration and L_prev that of the previous accepted one.
+  The listing's in-loop W /= ||W||_1 is not applied inside the loop (it would
+  rescale W between the two block steps of one iteration without rescaling
+  H); the column-L1 normalisation happens once per stage in the hand-off.
 
 Parity pins for every function live in tests/test_oracle_pins.py.  No function
 here is "parity unpinned".
@@ -175,7 +199,114 @@ def handoff_normalize(W, H):
 
 
 # --------------------------------------------------------------------------
-# Algorithm 2 with fixed ranks.
+# Algorithm 2's rank rule.
+# --------------------------------------------------------------------------
+
+def singular_values(X):
+    """The min(m, n) singular values of X in non-increasing order (FP64 SVD,
+    the distSVD step of Algorithm 2 on one node)."""
+    return np.linalg.svd(np.asarray(X, dtype=np.float64), compute_uv=False)
+
+
+def select_rank(sigma, eps_rank, rank_cap=None):
+    """Algorithm 2: the smallest k (1 <= k <= N) whose tail ratio
+    sqrt(sum_{i>k} sigma_i^2) / sqrt(sum_i sigma_i^2) is <= eps_rank; N =
+    len(sigma).  All-zero sigma gives 1.  rank_cap (optional) caps the result."""
+    sig2 = np.asarray(sigma, dtype=np.float64) ** 2
+    N = len(sig2)
+    total = float(np.sum(sig2))
+    k_sel = N
+    if total <= 0.0:
+        k_sel = 1
+    else:
+        for k in range(1, N + 1):
+            tail = float(np.sum(sig2[k:]))
+            if math.sqrt(tail) / math.sqrt(total) <= eps_rank:
+                k_sel = k
+                break
+    if rank_cap is not None:
+        k_sel = min(k_sel, int(rank_cap))
+    return max(1, k_sel)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 3: BCD NMF with extrapolation and restarts.
+# --------------------------------------------------------------------------
+BCD_DELTA = 0.9999
+
+
+def spectral_norm_sym(M):
+    """||M||_2 of a symmetric positive semi-definite matrix (its largest eigenvalue)."""
+    M = np.asarray(M, dtype=np.float64)
+    if M.size == 0:
+        return 0.0
+    return float(np.max(np.linalg.eigvalsh(M)))
+
+
+def bcd_nmf(X, W0, H0, iters, delta=BCD_DELTA, record=True):
+    """Algorithm 3 on one node (see the readings in the module docstring).
+
+    Initial factors W0, H0 are scaled to Frobenius norm sqrt(||X||_F) each
+    (Algorithm 3's normalisation).  Iteration l: W step from the extrapolated
+    W_m with the Gram terms of the current H, H step from the extrapolated H_m
+    with the new W, objective f = 1/2 ||X - W H||^2; f >= the last accepted
+    objective rejects the iteration (the factors return to the last accepted
+    ones and the next steps start there without extrapolation), otherwise the
+    iterate is accepted and both blocks are extrapolated.
+
+    Returns (W, H, trace, accepted): the last accepted factors, trace[l] = the
+    last accepted objective after iteration l+1, accepted[l] = whether
+    iteration l+1 was accepted.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    nx = float(np.linalg.norm(X))
+    W = np.array(W0, dtype=np.float64)
+    H = np.array(H0, dtype=np.float64)
+    nw, nh = float(np.linalg.norm(W)), float(np.linalg.norm(H))
+    if nw > 0.0:
+        W = W / nw * math.sqrt(nx)
+    if nh > 0.0:
+        H = H / nh * math.sqrt(nx)
+    W_acc, H_acc = W, H            # last accepted iterate
+    W_m, H_m = W, H                # extrapolated points the next steps start from
+    HHt, XHt = H_acc @ H_acc.T, X @ H_acc.T
+    t = 1.0
+    obj = 0.5 * nx * nx
+    Lw_prev = Lh_prev = None
+    trace, accepted = [], []
+    for _ in range(int(iters)):
+        Lw = spectral_norm_sym(HHt)
+        W_new = np.maximum(0.0, W_m - (W_m @ HHt - XHt) / Lw) if Lw > 0.0 else W_m.copy()
+        WtW = W_new.T @ W_new
+        Lh = spectral_norm_sym(WtW)
+        H_new = np.maximum(0.0, H_m - (WtW @ H_m - W_new.T @ X) / Lh) if Lh > 0.0 else H_m.copy()
+        f = objective(X, W_new, H_new)
+        if f >= obj:
+            # correction: back to the last accepted iterate, no extrapolation
+            W_m, H_m = W_acc, H_acc
+            HHt, XHt = H_acc @ H_acc.T, X @ H_acc.T
+            accepted.append(False)
+        else:
+            t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+            w = (t - 1.0) / t_new
+            lw_prev = Lw if Lw_prev is None else Lw_prev
+            lh_prev = Lh if Lh_prev is None else Lh_prev
+            w_w = min(w, delta * math.sqrt(lw_prev / Lw)) if Lw > 0.0 else 0.0
+            w_h = min(w, delta * math.sqrt(lh_prev / Lh)) if Lh > 0.0 else 0.0
+            W_m = W_new + w_w * (W_new - W_acc)
+            H_m = H_new + w_h * (H_new - H_acc)
+            W_acc, H_acc = W_new, H_new
+            HHt, XHt = H_acc @ H_acc.T, X @ H_acc.T
+            t, obj = t_new, f
+            Lw_prev, Lh_prev = Lw, Lh
+            accepted.append(True)
+        if record:
+            trace.append(obj)
+    return W_acc, H_acc, np.array(trace), np.array(accepted, dtype=bool)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2.
 # --------------------------------------------------------------------------
 
 # --------------------------------------------------------------------------
@@ -209,8 +340,8 @@ def unfold(T, m):
 
 
 def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, x_precision="f32",
-                  refine=0, tol=0.0, check_every=10):
-    """Non-negative tensor train of A with given TT ranks (Algorithm 2).
+                  refine=0, tol=0.0, check_every=10, eps_rank=None, rank_cap=None, solver="mu"):
+    """Non-negative tensor train of A (Algorithm 2).
 
     Stage l (0-based s = l-1): X = reshape(current, r_{l-1} n_l, rest); NMF of
     rank r_l by multiplicative updates from the counter-RNG init; W becomes core
@@ -221,20 +352,34 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
     picks the restart is on X.
     tol > 0: each stage's main loop stops early under stop_reached (the
     refinement iterations always run).
+    ranks=None: every r_l comes from Algorithm 2's rule on X_l (select_rank
+    with eps_rank, optional rank_cap), chosen before the stage's NMF.
+    solver="bcd": each NMF runs bcd_nmf (Algorithm 3) from the same counter-RNG
+    init instead of the multiplicative updates (FP32 form, no restarts).
     Returns (cores, traces), traces[s] = objective trace of the kept restart
-    (with record=False only the final objective of each stage).
+    (with record=False only the final objective of each stage).  The ranks
+    used are the cores' shapes.
     """
     A = np.asarray(A)
     dims = A.shape
     d = len(dims)
-    ranks = tuple(int(r) for r in ranks)
-    if len(ranks) != d + 1 or ranks[0] != 1 or ranks[-1] != 1:
-        raise ValueError("ranks must have d+1 entries with r_0 = r_d = 1")
+    if ranks is None:
+        if eps_rank is None:
+            raise ValueError("ranks=None needs eps_rank")
+        ranks = [1] * (d + 1)
+    else:
+        ranks = tuple(int(r) for r in ranks)
+        if len(ranks) != d + 1 or ranks[0] != 1 or ranks[-1] != 1:
+            raise ValueError("ranks must have d+1 entries with r_0 = r_d = 1")
+    ranks = list(ranks)
+    select = eps_rank is not None
     cur = A.astype(np.float64)
     cores, traces = [], []
     for s in range(d - 1):
         m = ranks[s] * dims[s]
         n = math.prod(dims[s + 1:])
+        if select:
+            ranks[s + 1] = select_rank(singular_values(unfold(cur, m)), eps_rank, rank_cap)
         r = ranks[s + 1]
         if r > min(m, n):
             raise ValueError(f"rank r_{s+1}={r} exceeds min(m, n)=min({m},{n})")
@@ -243,7 +388,10 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
         Xi = bf16_round(X) if x_precision == "bf16" else X
         for rs in range(restarts):
             W0, H0 = init_factors(m, n, r, seed, s, rs)
-            W, H, tr = nmf_mu(Xi, W0, H0, iters, eps, record=record, tol=tol, check_every=check_every)
+            if solver == "bcd":
+                W, H, tr, _ = bcd_nmf(Xi, W0, H0, iters, record=record)
+            else:
+                W, H, tr = nmf_mu(Xi, W0, H0, iters, eps, record=record, tol=tol, check_every=check_every)
             if refine:
                 W, H, tr2 = nmf_mu(X, W, H, refine, eps, record=record)
                 tr = np.concatenate([tr, tr2])

@@ -394,3 +394,135 @@ def test_precision_form_refinement_lowers_the_fp64_objective():
     _, t0 = oracle.ntt_decompose(A, ranks, 20, seed=9, record=False, x_precision="bf16", refine=0)
     _, t5 = oracle.ntt_decompose(A, ranks, 20, seed=9, record=False, x_precision="bf16", refine=5)
     assert t5[0][-1] <= t0[0][-1]
+
+
+# ---------------------------------------------------------------- Algorithm 2's rank rule
+
+def test_singular_values_closed_forms():
+    # [[3, 0], [4, 5]]: A^T A = [[25, 20], [20, 25]] has eigenvalues 45 and 5
+    assert np.allclose(oracle.singular_values([[3.0, 0.0], [4.0, 5.0]]), [math.sqrt(45.0), math.sqrt(5.0)],
+                       rtol=1e-14)
+    # a rectangular diagonal matrix: the absolute diagonal, sorted
+    D = np.zeros((3, 5))
+    D[0, 0], D[1, 1], D[2, 2] = 1.0, -3.0, 2.0
+    assert np.allclose(oracle.singular_values(D), [3.0, 2.0, 1.0], rtol=1e-14)
+    # U diag(s) V^T with orthonormal U, V built by QR: exactly s
+    rng = np.random.Generator(np.random.PCG64(3))
+    U, _ = np.linalg.qr(rng.standard_normal((9, 4)))
+    V, _ = np.linalg.qr(rng.standard_normal((13, 4)))
+    s = np.array([5.0, 2.5, 0.75, 0.125])
+    assert np.allclose(oracle.singular_values(U @ np.diag(s) @ V.T)[:4], s, rtol=1e-12)
+
+
+def test_select_rank_hand_example():
+    # sigma = (4, 2, 1, 1/2): sum of squares 21.25; tail ratios after k = 1..4:
+    # sqrt(5.25/21.25) = 0.497, sqrt(1.25/21.25) = 0.2425, sqrt(0.25/21.25) = 0.1085, 0
+    sig = [4.0, 2.0, 1.0, 0.5]
+    for eps, k in ((1.0, 1), (0.5, 1), (0.49, 2), (0.3, 2), (0.2, 3), (0.11, 3), (0.1, 4), (0.0, 4)):
+        assert oracle.select_rank(sig, eps) == k, eps
+    assert oracle.select_rank(sig, 0.1, rank_cap=2) == 2
+    assert oracle.select_rank([0.0, 0.0, 0.0], 0.1) == 1
+
+
+def test_select_rank_brute_force_and_invariances():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for trial in range(40):
+        m, n = rng.integers(2, 9), rng.integers(2, 12)
+        X = rng.random((m, n)) ** 3
+        sig = oracle.singular_values(X)
+        for eps in (0.3, 0.1, 0.03, 0.01):
+            k = oracle.select_rank(sig, eps)
+            # brute force over every candidate k: tail energy from the reversed cumulative sum
+            tails = np.concatenate([np.cumsum((sig ** 2)[::-1])[::-1][1:], [0.0]])
+            ok = [kk + 1 for kk in range(len(sig)) if math.sqrt(tails[kk] / np.sum(sig ** 2)) <= eps]
+            assert k == min(ok)
+            # scaling and transposing X change no singular value ratio
+            assert oracle.select_rank(oracle.singular_values(7.5 * X.T), eps) == k
+
+
+def test_select_rank_finds_exact_low_rank():
+    rng = np.random.Generator(np.random.PCG64(7))
+    for k in (1, 2, 5):
+        X = rng.random((12, k)) @ rng.random((k, 40))
+        assert oracle.select_rank(oracle.singular_values(X), 1e-8) == k
+
+
+def test_ntt_rank_rule_first_stage_and_one_stage():
+    # a noise-free TT tensor: X_1 has rank r_1 exactly, so a tiny eps picks r_1
+    dims, ranks = (6, 5, 7), (1, 3, 2, 1)
+    A = oracle.tt_full(synth.tt_cores(dims, ranks, "uniform", seed=17))
+    cores, _ = oracle.ntt_decompose(A, None, 20, seed=1, eps_rank=1e-9)
+    assert cores[0].shape[2] == 3
+    # d = 2: one stage, the rank of the rule on A itself
+    B = synth.uniform_matrix((9, 14), 4).astype(np.float64)
+    for eps in (0.5, 0.2, 0.05):
+        k = oracle.select_rank(oracle.singular_values(B), eps)
+        cores, _ = oracle.ntt_decompose(B, None, 5, seed=1, eps_rank=eps)
+        assert cores[0].shape == (1, 9, k) and cores[1].shape == (k, 14, 1)
+
+
+# ---------------------------------------------------------------- Algorithm 3 (BCD)
+
+def test_spectral_norm_is_the_two_norm():
+    rng = np.random.Generator(np.random.PCG64(8))
+    for n in (1, 3, 8):
+        B = rng.random((n, 2 * n))
+        M = B @ B.T
+        assert abs(oracle.spectral_norm_sym(M) - np.linalg.norm(M, 2)) <= 1e-12 * np.linalg.norm(M, 2)
+
+
+def test_bcd_first_w_step_is_least_squares_for_orthogonal_h():
+    """H with disjoint row supports and equal row norms: H H^T = c I, the
+    Lipschitz step 1/c makes the first W step the unconstrained least-squares
+    solution X H^T (H H^T)^-1, which is non-negative here (numpy lstsq)."""
+    rng = np.random.Generator(np.random.PCG64(9))
+    m, r, per = 7, 3, 5
+    n = r * per
+    H0 = np.zeros((r, n))
+    for k in range(r):
+        v = rng.random(per) + 0.1
+        H0[k, k * per:(k + 1) * per] = v / np.linalg.norm(v)
+    X = rng.random((m, n))
+    W0 = rng.random((m, r))
+    W, H, tr, acc = oracle.bcd_nmf(X, W0, H0, 1)
+    assert acc[0]
+    Hm = H0 / np.linalg.norm(H0) * math.sqrt(np.linalg.norm(X))   # Algorithm 3's normalisation
+    W_ls = np.linalg.lstsq(Hm.T, X.T, rcond=None)[0].T
+    assert np.allclose(W, W_ls, rtol=1e-12, atol=1e-14)
+
+
+def test_bcd_rank_one_exact_factorisation_is_a_fixed_point():
+    rng = np.random.Generator(np.random.PCG64(10))
+    u, v = rng.random((6, 1)) + 0.1, rng.random((1, 9)) + 0.1
+    X = u @ v
+    W, H, tr, acc = oracle.bcd_nmf(X, 3.0 * u, 0.5 * v, 20)
+    assert np.allclose(W @ H, X, rtol=1e-12)
+    assert tr[-1] <= 1e-24 * np.sum(X ** 2)
+
+
+def test_bcd_objective_monotone_converges_and_rejections_restore():
+    rng = np.random.Generator(np.random.PCG64(11))
+    X = rng.random((10, 4)) @ rng.random((4, 30))
+    W0, H0 = oracle.init_factors(10, 30, 4, seed=3, stage=0)
+    W, H, tr, acc = oracle.bcd_nmf(X, W0, H0, 400)
+    assert np.all(np.diff(tr) <= 0.0)                              # accepted objectives never rise
+    assert tr[-1] <= 1e-6 * 0.5 * np.sum(X ** 2)                  # exact low-rank data: converges
+    assert np.all(W >= 0) and np.all(H >= 0)
+    assert np.allclose(oracle.objective(X, W, H), tr[-1], rtol=1e-12)
+    # a rejected iteration leaves the factors where the previous iteration left them
+    rej = [i for i in range(1, len(acc)) if not acc[i]]
+    assert rej, "the extrapolation produced no rejected iteration on this case"
+    for i in rej[:3]:
+        Wa, Ha, _, _ = oracle.bcd_nmf(X, W0, H0, i)
+        Wb, Hb, _, _ = oracle.bcd_nmf(X, W0, H0, i + 1)
+        assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+
+
+def test_ntt_bcd_solver_d2_is_one_bcd_nmf():
+    X = synth.uniform_matrix((8, 21), 12).astype(np.float64)
+    cores, tr = oracle.ntt_decompose(X, (1, 3, 1), 50, seed=6, solver="bcd")
+    W0, H0 = oracle.init_factors(8, 21, 3, seed=6, stage=0)
+    W, H, t2, _ = oracle.bcd_nmf(X, W0, H0, 50)
+    Wn, Hn = oracle.handoff_normalize(W, H)
+    assert np.allclose(cores[0].reshape(8, 3), Wn, rtol=1e-14) and np.allclose(cores[1].reshape(3, 21), Hn)
+    assert np.array_equal(tr[0], t2)
