@@ -10,8 +10,8 @@
  * the Lee-Seung multiplicative updates the paper times in Section IV:
  *     H <- max(0, H o (W^T X) / (W^T W H + eps))
  *     W <- max(0, W o (X H^T) / (W H H^T + eps))
- * TT ranks are given (the paper's SVD rank rule of Algorithm 2 is not built:
- * NULL ranks return NTT_ERR_UNSUPPORTED).
+ * TT ranks are given, or chosen stage by stage by Algorithm 2's rule on the
+ * singular values of each unfolding (ranks == NULL, eps_rank > 0).
  *
  * Conventions for every entry point:
  *  - All arrays are dense, row-major (C order).  Device pointers must point to
@@ -77,11 +77,12 @@ typedef enum {
                                cached CUDA graph (debugging; each call then first waits for
                                the previous call of the plan to finish) */
 
-/* Plan description (Algorithm 2's inputs with fixed ranks). */
+/* Plan description (Algorithm 2's inputs). */
 typedef struct {
   int d;                 /* tensor order, 2 <= d <= NTT_MAX_D */
   const int64_t* dims;   /* d mode sizes n_1..n_d (host) */
-  const int64_t* ranks;  /* d+1 TT ranks r_0..r_d with r_0 = r_d = 1 (host) */
+  const int64_t* ranks;  /* d+1 TT ranks r_0..r_d with r_0 = r_d = 1 (host), or NULL:
+                            Algorithm 2's rank rule with eps_rank (see below) */
   int iters;             /* multiplicative-update iterations per stage (>= 1) */
   float eps_mu;          /* epsilon added to both MU denominators (e.g. 1e-12) */
   ntt_dtype x_dtype;     /* NTT_F32, or NTT_BF16: each unfolding is cast to BF16 and
@@ -97,6 +98,14 @@ typedef struct {
   int check_every;       /* K of that test; >= 1 when tol > 0 */
   int route;             /* ntt_route of every stage (0 = NTT_ROUTE_AUTO) */
   unsigned flags;        /* NTT_PLAN_* bits (0: cached CUDA graph) */
+  double eps_rank;       /* ranks == NULL: Algorithm 2's threshold.  Before stage l's NMF,
+                            r_l = the smallest k >= 1 with
+                              sqrt(s_{k+1}^2 + ... + s_N^2) / sqrt(s_1^2 + ... + s_N^2) <= eps_rank,
+                            s_i the singular values of X_l, N = min(m, n); > 0 */
+  int rank_cap;          /* ranks == NULL: upper bound of every chosen rank (0: NTT_MAX_RANK).
+                            The rule's rank is also capped at NTT_MAX_RANK and at
+                            NTT_MAX_ROWS / n_{l+1}, so that the next unfolding fits the
+                            built height (ntt_plan_get_ranks reports these bounds). */
 } ntt_plan_desc;
 
 /* Per-stage statistics, filled by ntt_plan_get_stats after the last call. */
@@ -134,8 +143,15 @@ const char* ntt_version(void);
 /* Validate `desc` and build a plan (host only, no device work).  Checks the
  * ranks against Algorithm 2's feasibility bound r_k <= min(r_{k-1} n_k,
  * prod_{j>k} n_j), r_k <= NTT_MAX_RANK and r_{k-1} n_k <= NTT_MAX_ROWS.
+ * With ranks == NULL the workspace and the core buffers are sized for the
+ * largest ranks the rule may choose (ntt_plan_get_ranks before any call).
  * On success *out owns a plan to be released with ntt_plan_destroy. */
 ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out);
+
+/* The plan's d+1 TT ranks: the given ones; with the rank rule, the ranks the
+ * last ntt_decompose chose, or before any call the largest the rule may
+ * choose (core k then needs r_k n_{k+1} r_{k+1} floats of those bounds). */
+ntt_status ntt_plan_get_ranks(ntt_plan plan, int64_t* ranks);
 
 /* Device workspace bytes needed by ntt_decompose with this plan. */
 ntt_status ntt_plan_workspace_size(ntt_plan plan, size_t* bytes);
@@ -152,8 +168,14 @@ ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes);
  *             overwritten.
  * Stage l uses W = core l as its m x r factor and H in the workspace (the
  * last stage writes H straight into the last core), so no reshape copies are
- * made: each reshape of Algorithm 1/2 is a C-order view.  The whole
- * decomposition is one cached CUDA graph per (A, cores, workspace) triple
+ * made: each reshape of Algorithm 1/2 is a C-order view.
+ * With the rank rule (ranks == NULL) each stage first computes the singular
+ * values of its unfolding and picks r_l on the device, then the host reads
+ * r_l (the call synchronises `stream` once per stage) and enqueues the
+ * stage's NMF; core k is written packed as r_k x n_{k+1} x r_{k+1} of the
+ * chosen ranks at the start of its buffer (sized for the bounds), and the
+ * call returns after the last stage has been enqueued (not finished).
+ * Otherwise the whole decomposition is one cached CUDA graph per (A, cores, workspace) triple
  * (two triples are kept), launched on `stream`; the graph contains kernel
  * nodes only.  Capturing a third triple first waits for the last launch of
  * the graph it replaces. */
@@ -247,6 +269,28 @@ ntt_status nmf_mu_many(int count, const int64_t* m, const int64_t* n, const int*
 
 /* Device status word left in an nmf_mu_step workspace (sync first). */
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out);
+
+/* ------------------------------------------------------------------------
+ * Algorithm 2's rank rule on its own.  X: device m x n FP32 (C order),
+ * min(m, n) <= NTT_MAX_ROWS.  The singular values are the square roots of the
+ * eigenvalues of the min(m, n)-sided Gram matrix (X X^T or X^T X), formed from
+ * FP32 products summed in runs of 256 and accumulated in FP64, then reduced to
+ * tridiagonal form and solved by bisection in FP64.
+ * ------------------------------------------------------------------------ */
+/* Workspace bytes of ntt_singular_values / ntt_select_rank. */
+ntt_status ntt_rank_workspace_size(int64_t m, int64_t n, size_t* bytes);
+
+/* sigma_dev: device, min(m, n) doubles, receives the singular values of X in
+ * non-increasing order.  ws: ntt_rank_workspace_size bytes, 256-byte aligned. */
+ntt_status ntt_singular_values(int64_t m, int64_t n, const float* X, double* sigma_dev, void* ws,
+                               void* stream);
+
+/* rank_dev: device int, receives the smallest k >= 1 with
+ * sqrt(sum_{i>k} s_i^2) / sqrt(sum_i s_i^2) <= eps_rank (Algorithm 2), capped
+ * at rank_cap when rank_cap > 0; an all-zero X gives 1.  sigma_dev
+ * (nullable) receives the singular values as above. */
+ntt_status ntt_select_rank(int64_t m, int64_t n, const float* X, double eps_rank, int rank_cap,
+                           int* rank_dev, double* sigma_dev, void* ws, void* stream);
 
 /* Failure-detection probe of the bounded device waits (Section III's
  * distributed design has no counterpart; every kernel of this library bounds

@@ -340,7 +340,7 @@ def unfold(T, m):
 
 
 def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, x_precision="f32",
-                  refine=0, tol=0.0, check_every=10, eps_rank=None, rank_cap=None, solver="mu"):
+                  refine=0, tol=0.0, check_every=10, eps_rank=None, rank_cap=None, solver="mu", info=None):
     """Non-negative tensor train of A (Algorithm 2).
 
     Stage l (0-based s = l-1): X = reshape(current, r_{l-1} n_l, rest); NMF of
@@ -358,7 +358,8 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
     init instead of the multiplicative updates (FP32 form, no restarts).
     Returns (cores, traces), traces[s] = objective trace of the kept restart
     (with record=False only the final objective of each stage).  The ranks
-    used are the cores' shapes.
+    used are the cores' shapes.  info (optional dict) receives "sigma": the
+    singular values of every unfolding the rank rule saw.
     """
     A = np.asarray(A)
     dims = A.shape
@@ -379,7 +380,10 @@ def ntt_decompose(A, ranks, iters, eps=EPS_MU, seed=0, restarts=1, record=True, 
         m = ranks[s] * dims[s]
         n = math.prod(dims[s + 1:])
         if select:
-            ranks[s + 1] = select_rank(singular_values(unfold(cur, m)), eps_rank, rank_cap)
+            sig = singular_values(unfold(cur, m))
+            if info is not None:
+                info.setdefault("sigma", []).append(sig)
+            ranks[s + 1] = select_rank(sig, eps_rank, rank_cap)
         r = ranks[s + 1]
         if r > min(m, n):
             raise ValueError(f"rank r_{s+1}={r} exceeds min(m, n)=min({m},{n})")

@@ -53,7 +53,8 @@ EXPORTS = (
     "ntt_status_string", "ntt_version", "ntt_plan_create", "ntt_plan_workspace_size",
     "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
-    "nmf_mu_step_route", "ntt_wait_probe",
+    "nmf_mu_step_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
+    "ntt_singular_values", "ntt_select_rank",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
@@ -83,6 +84,8 @@ class _PlanDesc(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("route", ctypes.c_int),
         ("flags", ctypes.c_uint),
+        ("eps_rank", ctypes.c_double),
+        ("rank_cap", ctypes.c_int),
     ]
 
 
@@ -163,6 +166,10 @@ def lib():
     L.nmf_mu_step_noalloc.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp]
     L.ntt_status_of_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ntt_wait_probe.argtypes = [vp, i64, vp]
+    L.ntt_plan_get_ranks.argtypes = [vp, p64]
+    L.ntt_rank_workspace_size.argtypes = [i64, i64, psz]
+    L.ntt_singular_values.argtypes = [i64, i64, vp, vp, vp, vp]
+    L.ntt_select_rank.argtypes = [i64, i64, vp, ctypes.c_double, i32, vp, vp, vp, vp]
     L.ntt_uniform_init.argtypes = [ctypes.c_uint64, i32, i32, i32, i64, vp, vp]
     L.ntt_reconstruct_workspace_size.argtypes = [i32, p64, p64, psz]
     L.ntt_reconstruct.argtypes = [i32, p64, p64, ctypes.POINTER(vp), vp, vp, vp]
@@ -229,6 +236,7 @@ class Plan:
     iters: int
     x_dtype: str
     refine_iters: int
+    max_ranks: tuple = None
 
     def workspace_size(self):
         n = ctypes.c_size_t(0)
@@ -241,8 +249,23 @@ class Plan:
                "ntt_plan_workspace_size_host")
         return n.value
 
+    def current_ranks(self):
+        """The plan's ranks (include/ntt.h ntt_plan_get_ranks): the given ones, or
+        with the rank rule the last call's choice (the bounds before any call)."""
+        out = (ctypes.c_int64 * (len(self.dims) + 1))()
+        _check(lib().ntt_plan_get_ranks(self.handle, out), "ntt_plan_get_ranks")
+        return tuple(int(v) for v in out)
+
     def core_shapes(self):
-        return [(self.ranks[k], self.dims[k], self.ranks[k + 1]) for k in range(len(self.dims))]
+        """Shapes of the core buffers to allocate (with the rank rule: the bounds)."""
+        ranks = self.ranks if self.ranks is not None else self.max_ranks
+        return [(ranks[k], self.dims[k], ranks[k + 1]) for k in range(len(self.dims))]
+
+    def core_views(self, cores):
+        """The cores at the plan's current ranks, as views of buffers of core_shapes()."""
+        ranks = self.current_ranks()
+        return [c.reshape(-1)[:ranks[k] * self.dims[k] * ranks[k + 1]].view(ranks[k], self.dims[k], ranks[k + 1])
+                for k, c in enumerate(cores)]
 
     def destroy(self):
         if self.handle:
@@ -257,8 +280,9 @@ class Plan:
 
 
 def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, tol=0.0,
-                    check_every=10, route="auto", eager=False):
-    """route: one of ROUTES (ntt_route); eager: enqueue every call instead of a cached graph."""
+                    check_every=10, route="auto", eager=False, eps_rank=0.0, rank_cap=0):
+    """route: one of ROUTES (ntt_route); eager: enqueue every call instead of a cached graph;
+    ranks=None: Algorithm 2's rank rule with eps_rank (> 0) and optional rank_cap."""
     dims = tuple(int(n) for n in dims)
     ranks = tuple(int(r) for r in ranks) if ranks is not None else None
     d_arr = _i64arr(dims)
@@ -276,9 +300,13 @@ def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iter
     desc.check_every = int(check_every)
     desc.route = _route(route)
     desc.flags = NTT_PLAN_EAGER if eager else 0
+    desc.eps_rank = float(eps_rank)
+    desc.rank_cap = int(rank_cap)
     h = ctypes.c_void_p()
     _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
-    return Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
+    plan = Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
+    plan.max_ranks = plan.current_ranks()
+    return plan
 
 
 def _ptr_array(ptrs):
@@ -436,6 +464,40 @@ def ntt_wait_probe(workspace, limit_ns, stream=None):
     word reads NTT_ERR_TIMEOUT once the stream has run it (include/ntt.h)."""
     _check(lib().ntt_wait_probe(_dev_ptr(workspace, None, "ws"), int(limit_ns), _stream_ptr(stream)),
            "ntt_wait_probe")
+
+
+def ntt_rank_workspace_size(m, n):
+    b = ctypes.c_size_t(0)
+    _check(lib().ntt_rank_workspace_size(int(m), int(n), ctypes.byref(b)), "ntt_rank_workspace_size")
+    return b.value
+
+
+def ntt_singular_values(X, sigma=None, workspace=None, stream=None):
+    """Singular values of a CUDA float32 matrix X (non-increasing, float64 CUDA tensor)."""
+    import torch
+    m, n = X.shape
+    if sigma is None:
+        sigma = torch.empty(min(m, n), dtype=torch.float64, device=X.device)
+    if workspace is None:
+        workspace = empty_workspace(ntt_rank_workspace_size(m, n), X.device)
+    _check(lib().ntt_singular_values(m, n, _dev_ptr(X, torch.float32, "X"), _dev_ptr(sigma, torch.float64, "sigma"),
+                                     _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)), "ntt_singular_values")
+    return sigma
+
+
+def ntt_select_rank(X, eps_rank, rank_cap=0, rank=None, sigma=None, workspace=None, stream=None):
+    """Algorithm 2's rank of a CUDA float32 matrix X into `rank` (int32 CUDA tensor, 1 entry)."""
+    import torch
+    m, n = X.shape
+    if rank is None:
+        rank = torch.zeros(1, dtype=torch.int32, device=X.device)
+    if workspace is None:
+        workspace = empty_workspace(ntt_rank_workspace_size(m, n), X.device)
+    sp = _dev_ptr(sigma, torch.float64, "sigma") if sigma is not None else None
+    _check(lib().ntt_select_rank(m, n, _dev_ptr(X, torch.float32, "X"), float(eps_rank), int(rank_cap),
+                                 _dev_ptr(rank, torch.int32, "rank"), sp, _dev_ptr(workspace, None, "ws"),
+                                 _stream_ptr(stream)), "ntt_select_rank")
+    return rank
 
 
 def ntt_uniform_init(seed, stage, restart, matrix, out, stream=None):
@@ -631,15 +693,17 @@ def ntt_compression_ratio(dims, ranks):
 
 
 def decompose(A, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, stream=None, tol=0.0,
-              check_every=10, route="auto"):
-    """Convenience wrapper: returns (cores, stats) for a CUDA float32 tensor A."""
+              check_every=10, route="auto", eps_rank=0.0, rank_cap=0):
+    """Convenience wrapper: returns (cores, stats) for a CUDA float32 tensor A
+    (ranks=None: Algorithm 2's rank rule with eps_rank)."""
     import torch
     plan = ntt_plan_create(tuple(A.shape), ranks, iters, eps_mu, x_dtype, refine_iters, seed, tol, check_every,
-                           route)
+                           route, eps_rank=eps_rank, rank_cap=rank_cap)
     ws = empty_workspace(plan.workspace_size(), A.device)
     cores = [torch.empty(s, dtype=torch.float32, device=A.device) for s in plan.core_shapes()]
     ntt_decompose(plan, A.contiguous(), cores, ws, stream)
     stats = ntt_plan_get_stats(plan)
+    cores = [c.clone() for c in plan.core_views(cores)]
     plan.destroy()
     return cores, stats
 

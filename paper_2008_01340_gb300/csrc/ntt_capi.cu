@@ -222,6 +222,12 @@ struct ntt_plan_s {
   int check = 0;
   int route = NTT_ROUTE_AUTO;    // ntt_route of every stage
   bool eager = false;            // NTT_PLAN_EAGER: enqueue every call, no graph
+  // Algorithm 2's rank rule: ranks chosen stage by stage at run time
+  bool auto_rank = false;
+  double eps_rank = 0.0;
+  std::vector<int64_t> ranks_max;   // the largest ranks the rule may pick (workspace sizing)
+  size_t off_rank = 0, rank_bytes = 0;
+  size_t grp_bytes = 0;             // grouped-engine scratch reserved in the layout
   size_t off_stop = 0;           // one stop word per stage
 
   // A stage's MU loop runs either on the single-problem pass (TMA, phase
@@ -321,100 +327,176 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route) {
 }
 
 // Record the whole decomposition on stream `st` (captured or eager).
-// tab / tab_dev: host and device addresses of the mapped pinned tables of
-// the routed stages (written here; uploaded by a kernel at each stage).
-ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, char* ws,
-                             cudaStream_t st, char* tab, const char* tab_dev) {
+// Shapes of stage s from the plan's current ranks (not its routes).
+ntt_status make_stage(ntt_plan p, int s, int sms, ntt_plan_s::Stage* out) {
+  ntt_plan_s::Stage S;
+  const int d = p->d;
+  S.m = p->ranks[s] * p->dims[s];
+  S.n = prod(p->dims.data(), s + 1, d);
+  S.r = (int)p->ranks[s + 1];
+  ntt_status e = mu_choose_shape(S.m, S.n, S.r, 0, sms, &S.f32);
+  if (e == NTT_OK && p->xdt == NTT_BF16) e = mu_choose_shape(S.m, S.n, S.r, 1, sms, &S.bf16);
+  if (e != NTT_OK) return e;
+  S.f32.route = p->route;
+  S.bf16.route = p->route;
+  S.iters_total = p->iters + p->refine;
+  S.obj_off = (size_t)s * S.iters_total;
+  const double xs = p->xdt == NTT_BF16 ? 2.0 : 4.0;
+  S.alg_bytes = (double)S.m * S.n * xs + 8.0 * S.r * S.n;
+  *out = S;
+  return NTT_OK;
+}
+
+// Grouped-engine routes of a stage, planned at scratch offset `base`; host
+// table offsets from *h_off on.  Returns the largest scratch end offset.
+size_t plan_stage_routes(ntt_plan p, ntt_plan_s::Stage& S, int sms, size_t base, size_t* h_off) {
+  size_t end = 0;
+  for (int xb = 0; xb < 2; ++xb) {
+    ntt_plan_s::Route& rt = xb ? S.gbf16 : S.gf32;
+    rt.on = false;
+    if (xb && p->xdt != NTT_BF16) continue;
+    if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
+    if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route)) continue;
+    // a main loop with a stopping test runs on the single-problem passes
+    const bool main_loop = xb != 0 || p->xdt != NTT_BF16;
+    if (main_loop && p->tol > 0.0) continue;
+    GroupShape sh;
+    sh.n = S.n;
+    sh.m = (int)S.m;
+    sh.re = S.r;
+    sh.blk = S.r;
+    sh.xbf16 = xb;
+    if (group_plan({sh}, sms, base, false, true, &rt.gp) != NTT_OK) continue;
+    rt.on = true;
+    end = std::max(end, rt.gp.bytes);
+    rt.host_off = *h_off;
+    *h_off += (rt.gp.table_bytes + 255) / 256 * 256;
+  }
+  return end;
+}
+
+struct EnqueueCtx {
+  bool capturing = false;
+  int64_t launches = 0;
+};
+
+// Timing event i of the plan on `st` (external event nodes when capturing: a
+// plain record on a capturing stream would only mark a capture dependency and
+// put no timing node into the graph; a plain record otherwise).
+cudaError_t plan_record(ntt_plan p, int i, cudaStream_t st, const EnqueueCtx& c) {
+  if (p->ev.empty()) return cudaSuccess;
+  return c.capturing ? cudaEventRecordWithFlags(p->ev[i], st, cudaEventRecordExternal)
+                     : cudaEventRecord(p->ev[i], st);
+}
+
+ntt_status enqueue_begin(ntt_plan p, char* ws, cudaStream_t st, EnqueueCtx* c) {
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  NTT_CUDA_TRY(cudaStreamIsCapturing(st, &cap_status));
+  c->capturing = cap_status == cudaStreamCaptureStatusActive;
+  // status word, tickets and stop words are consecutive in the layout
+  NTT_CUDA_TRY(launch_zero(ws + p->off_status, p->off_stop + NTT_MAX_D * sizeof(int) - p->off_status, st));
+  c->launches = 1;
+  NTT_CUDA_TRY(plan_record(p, 4 * p->d, st, *c));
+  return NTT_OK;
+}
+
+// Stage s of Algorithm 2 (init, ||X||^2, Gram, the MU loops, direct objective, hand-off).
+ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores, char* ws, cudaStream_t st,
+                         char* tab, const char* tab_dev, EnqueueCtx* c) {
   int* status = reinterpret_cast<int*>(ws + p->off_status);
   unsigned* tickets = reinterpret_cast<unsigned*>(ws + p->off_tickets);
   double* scal = reinterpret_cast<double*>(ws + p->off_scal);
   double* obj = reinterpret_cast<double*>(ws + p->off_obj);
   int* stop = reinterpret_cast<int*>(ws + p->off_stop);
-  // status word, tickets and stop words are consecutive in the layout
-  NTT_CUDA_TRY(launch_zero(status, p->off_stop + NTT_MAX_D * sizeof(int) - p->off_status, st));
   const int d = p->d;
-  int64_t launches = 1;
-  // External event nodes: a plain record on a capturing stream would only
-  // mark a capture dependency and put no timing node into the graph.
-  auto rec = [&](int i) -> cudaError_t {
-    return p->ev.empty() ? cudaSuccess
-                         : cudaEventRecordWithFlags(p->ev[i], st, cudaEventRecordExternal);
-  };
-  NTT_CUDA_TRY(rec(4 * d));
-  for (int s = 0; s < d - 1; ++s) {
-    const auto& S = p->st[s];
-    NTT_CUDA_TRY(rec(4 * s));
-    const float* X = (s == 0) ? A : reinterpret_cast<const float*>(ws + p->off_H[(s - 1) % 2]);
-    float* W = cores[s];
-    float* H = (s == d - 2) ? cores[d - 1] : reinterpret_cast<float*>(ws + p->off_H[s % 2]);
-    NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 0), S.m * S.r, W, st));
-    NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 1), (int64_t)S.r * S.n, H, st));
-    double* xnorm2 = scal + s;
-    NTT_TRY(resid_into(X, 0, nullptr, nullptr, S.m, S.n, 0, 0, 1.0, xnorm2, nullptr,
-                       reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
-    MuDev dev;
-    dev.W = W;
-    dev.H = H;
-    dev.G = reinterpret_cast<float*>(ws + p->off_G);
-    dev.part = reinterpret_cast<float*>(ws + p->off_part);
-    dev.red = reinterpret_cast<float*>(ws + p->off_red);
-    dev.ticket = tickets;
-    dev.obj = obj + S.obj_off;
-    dev.xnorm2 = xnorm2;
-    dev.status = status;
-    NTT_CUDA_TRY(launch_gram(S.f32, dev, st));
-    launches += 4;
-    auto mu = [&](const ntt_plan_s::Route& rt, const MuShape& shp, const void* Xv, int iters,
-                  int t0) -> ntt_status {
-      if (iters <= 0) return NTT_OK;
-      const bool main_loop = t0 == 0;
-      if (!rt.on) {
-        dev.X = Xv;
-        dev.stop = main_loop && p->tol > 0.0 ? stop + s : nullptr;
-        dev.tol = p->tol;
-        dev.check = p->check;
-        dev.loop_t0 = t0;
-        int eng = NTT_ENGINE_FMA_PASS;
-        const ntt_status e = run_mu_iters(shp, dev, p->eps, iters, t0, st, &eng);
-        if (main_loop) p->st[s].engine = eng;
-        return e;
-      }
-      if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;
-      GroupPtrs g;
-      g.X = Xv;
-      g.H = H;
-      g.W = W;
-      g.scratch = nullptr;
-      g.obj = obj + S.obj_off;
-      g.xnorm2 = xnorm2;
-      group_fill_tables(rt.gp, &g, ws, tab + rt.host_off);
-      NTT_CUDA_TRY(launch_copy_words(ws + rt.gp.off_tables, tab_dev + rt.host_off, rt.gp.table_bytes, st));
-      launches += 3;   // table upload, ticket reset and the engine's own Gram launch
-      return group_launch(rt.gp, ws, ws + rt.gp.off_tables, iters, p->eps, st, t0);
-    };
-    if (p->xdt == NTT_BF16) {
-      __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
-      NTT_CUDA_TRY(launch_cast_bf16(X, xb, S.m * S.n, st));
-      launches += 1;
-      NTT_CUDA_TRY(rec(4 * s + 2));
-      NTT_TRY(mu(S.gbf16, S.bf16, xb, p->iters, 0));
-      NTT_TRY(mu(S.gf32, S.f32, X, p->refine, p->iters));
-    } else {
-      NTT_CUDA_TRY(rec(4 * s + 2));
-      NTT_TRY(mu(S.gf32, S.f32, X, p->iters, 0));
+  int64_t& launches = c->launches;
+  auto rec = [&](int i) { return plan_record(p, i, st, *c); };
+  const auto& S = p->st[s];
+  NTT_CUDA_TRY(rec(4 * s));
+  const float* X = (s == 0) ? A : reinterpret_cast<const float*>(ws + p->off_H[(s - 1) % 2]);
+  float* W = cores[s];
+  float* H = (s == d - 2) ? cores[d - 1] : reinterpret_cast<float*>(ws + p->off_H[s % 2]);
+  NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 0), S.m * S.r, W, st));
+  NTT_CUDA_TRY(launch_uniform(stream_key(p->seed, s, 0, 1), (int64_t)S.r * S.n, H, st));
+  double* xnorm2 = scal + s;
+  NTT_TRY(resid_into(X, 0, nullptr, nullptr, S.m, S.n, 0, 0, 1.0, xnorm2, nullptr,
+                     reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
+  MuDev dev;
+  dev.W = W;
+  dev.H = H;
+  dev.G = reinterpret_cast<float*>(ws + p->off_G);
+  dev.part = reinterpret_cast<float*>(ws + p->off_part);
+  dev.red = reinterpret_cast<float*>(ws + p->off_red);
+  dev.ticket = tickets;
+  dev.obj = obj + S.obj_off;
+  dev.xnorm2 = xnorm2;
+  dev.status = status;
+  NTT_CUDA_TRY(launch_gram(S.f32, dev, st));
+  launches += 4;
+  auto mu = [&](const ntt_plan_s::Route& rt, const MuShape& shp, const void* Xv, int iters,
+                int t0) -> ntt_status {
+    if (iters <= 0) return NTT_OK;
+    const bool main_loop = t0 == 0;
+    if (!rt.on) {
+      dev.X = Xv;
+      dev.stop = main_loop && p->tol > 0.0 ? stop + s : nullptr;
+      dev.tol = p->tol;
+      dev.check = p->check;
+      dev.loop_t0 = t0;
+      int eng = NTT_ENGINE_FMA_PASS;
+      const ntt_status e = run_mu_iters(shp, dev, p->eps, iters, t0, st, &eng);
+      if (main_loop) p->st[s].engine = eng;
+      return e;
     }
-    NTT_CUDA_TRY(rec(4 * s + 3));
-    launches += 2LL * S.iters_total;
-    // stage-end objective, direct FP64 pass: 1/2 ||X - W H||^2
-    NTT_TRY(resid_into(X, 0, W, H, S.m, S.n, S.r, 1, 0.5, scal + NTT_MAX_D + s, nullptr,
-                       reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
-    NTT_CUDA_TRY(launch_handoff(W, H, S.m, S.n, S.r, reinterpret_cast<float*>(ws + p->off_hs), st));
-    launches += 3;
-    NTT_CUDA_TRY(rec(4 * s + 1));
+    if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;
+    GroupPtrs g;
+    g.X = Xv;
+    g.H = H;
+    g.W = W;
+    g.scratch = nullptr;
+    g.obj = obj + S.obj_off;
+    g.xnorm2 = xnorm2;
+    group_fill_tables(rt.gp, &g, ws, tab + rt.host_off);
+    NTT_CUDA_TRY(launch_copy_words(ws + rt.gp.off_tables, tab_dev + rt.host_off, rt.gp.table_bytes, st));
+    launches += 3;   // table upload, ticket reset and the engine's own Gram launch
+    return group_launch(rt.gp, ws, ws + rt.gp.off_tables, iters, p->eps, st, t0);
+  };
+  if (p->xdt == NTT_BF16) {
+    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
+    NTT_CUDA_TRY(launch_cast_bf16(X, xb, S.m * S.n, st));
+    launches += 1;
+    NTT_CUDA_TRY(rec(4 * s + 2));
+    NTT_TRY(mu(S.gbf16, S.bf16, xb, p->iters, 0));
+    NTT_TRY(mu(S.gf32, S.f32, X, p->refine, p->iters));
+  } else {
+    NTT_CUDA_TRY(rec(4 * s + 2));
+    NTT_TRY(mu(S.gf32, S.f32, X, p->iters, 0));
   }
-  NTT_CUDA_TRY(rec(4 * d + 1));
-  p->launches = launches;
+  NTT_CUDA_TRY(rec(4 * s + 3));
+  launches += 2LL * S.iters_total;
+  // stage-end objective, direct FP64 pass: 1/2 ||X - W H||^2
+  NTT_TRY(resid_into(X, 0, W, H, S.m, S.n, S.r, 1, 0.5, scal + NTT_MAX_D + s, nullptr,
+                     reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
+  NTT_CUDA_TRY(launch_handoff(W, H, S.m, S.n, S.r, reinterpret_cast<float*>(ws + p->off_hs), st));
+  launches += 3;
+  NTT_CUDA_TRY(rec(4 * s + 1));
   return NTT_OK;
+}
+
+ntt_status enqueue_end(ntt_plan p, cudaStream_t st, EnqueueCtx* c) {
+  NTT_CUDA_TRY(plan_record(p, 4 * p->d + 1, st, *c));
+  p->launches = c->launches;
+  return NTT_OK;
+}
+
+// tab / tab_dev: host and device addresses of the mapped pinned tables of
+// the routed stages (written here; uploaded by a kernel at each stage).
+ntt_status enqueue_decompose(ntt_plan p, const float* A, float* const* cores, char* ws,
+                             cudaStream_t st, char* tab, const char* tab_dev) {
+  EnqueueCtx c;
+  NTT_TRY(enqueue_begin(p, ws, st, &c));
+  for (int s = 0; s < p->d - 1; ++s) NTT_TRY(enqueue_stage(p, s, A, cores, ws, st, tab, tab_dev, &c));
+  return enqueue_end(p, st, &c);
 }
 
 // Mapped pinned host memory: *host for the host, *dev for kernels.
@@ -433,6 +515,46 @@ ntt_status alloc_mapped(size_t bytes, char** host, char** dev) {
   *host = reinterpret_cast<char*>(h);
   *dev = reinterpret_cast<char*>(d);
   return NTT_OK;
+}
+
+// Algorithm 2 with the rank rule: per stage, the rank of X_l on the device,
+// read by the host (one stream synchronisation), then the stage's NMF
+// enqueued with that rank.  Launches are enqueued directly (no graph).
+ntt_status decompose_auto_rank(ntt_plan p, const float* A, float* const* cores, char* ws, cudaStream_t st) {
+  if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  const int d = p->d, sms = device_sms();
+  if (p->h_bytes && !p->h_eager) NTT_TRY(alloc_mapped(p->h_bytes, &p->h_eager, &p->h_eager_dev));
+  p->ranks = p->ranks_max;
+  p->ranks[0] = 1;
+  EnqueueCtx c;
+  NTT_TRY(enqueue_begin(p, ws, st, &c));
+  int* rank_dev = reinterpret_cast<int*>(ws + p->off_scal + 3 * NTT_MAX_D * sizeof(double));
+  for (int s = 0; s < d - 1; ++s) {
+    const int64_t m = p->ranks[s] * p->dims[s];
+    const int64_t n = prod(p->dims.data(), s + 1, d);
+    const float* X = (s == 0) ? A : reinterpret_cast<const float*>(ws + p->off_H[(s - 1) % 2]);
+    const RankWs w = rank_ws_layout(m, n, sms);
+    if (w.bytes > p->rank_bytes) return NTT_ERR_OOM;
+    NTT_CUDA_TRY(launch_rank_select(X, m, n, p->eps_rank, (int)p->ranks_max[s + 1], w, ws + p->off_rank, nullptr,
+                                    rank_dev + s, st));
+    int k = 0;
+    NTT_CUDA_TRY(cudaMemcpyAsync(&k, rank_dev + s, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NTT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (k < 1 || k > p->ranks_max[s + 1]) return NTT_ERR_CUDA;
+    p->ranks[s + 1] = k;
+    c.launches += 4;
+    NTT_TRY(make_stage(p, s, sms, &p->st[s]));
+    size_t h = 0;
+    if (p->off_grp) {
+      const size_t end = plan_stage_routes(p, p->st[s], sms, p->off_grp, &h);
+      if (end > p->off_grp + p->grp_bytes || h > p->h_bytes) {
+        p->st[s].gf32.on = false;
+        p->st[s].gbf16.on = false;
+      }
+    }
+    NTT_TRY(enqueue_stage(p, s, A, cores, ws, st, p->h_eager, p->h_eager_dev, &c));
+  }
+  return enqueue_end(p, st, &c);
 }
 
 }  // namespace
@@ -469,7 +591,9 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   *out = nullptr;
   const int d = desc->d;
   if (d < 2 || d > NTT_MAX_D || !desc->dims) return NTT_ERR_INVALID_ARG;
-  if (!desc->ranks) return NTT_ERR_UNSUPPORTED;  // SVD rank selection is not built
+  const bool auto_rank = desc->ranks == nullptr;
+  if (auto_rank && !(desc->eps_rank > 0.0 && desc->eps_rank <= 1e300)) return NTT_ERR_INVALID_ARG;
+  if (desc->rank_cap < 0) return NTT_ERR_INVALID_ARG;
   if (desc->iters < 1 || !(desc->eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
   if (desc->x_dtype != NTT_F32 && desc->x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
   if (desc->refine_iters < 0) return NTT_ERR_INVALID_ARG;
@@ -478,22 +602,43 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (desc->flags & ~NTT_PLAN_EAGER) return NTT_ERR_INVALID_ARG;
   if (desc->tol > 0.0 && desc->check_every < 1) return NTT_ERR_INVALID_ARG;
   const int64_t* dims = desc->dims;
-  const int64_t* ranks = desc->ranks;
-  if (ranks[0] != 1 || ranks[d] != 1) return NTT_ERR_INVALID_ARG;
   for (int i = 0; i < d; ++i)
     if (dims[i] < 1) return NTT_ERR_INVALID_ARG;
-  for (int k = 1; k < d; ++k) {
-    const int64_t m = ranks[k - 1] * dims[k - 1];
-    const int64_t n = prod(dims, k, d);
-    if (ranks[k] < 1) return NTT_ERR_INVALID_ARG;
-    if (ranks[k] > m || ranks[k] > n) return NTT_ERR_RANK_INFEASIBLE;
-    if (ranks[k] > NTT_MAX_RANK || m > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+  std::vector<int64_t> rk(d + 1, 1);
+  if (auto_rank) {
+    // Largest rank the rule may pick at each stage: min(m, n) (Algorithm 2's
+    // N), the built maximum, the caller's cap, and a height of the next
+    // unfolding r_l n_{l+1} <= NTT_MAX_ROWS.
+    const int64_t cap = desc->rank_cap > 0 ? std::min<int64_t>(desc->rank_cap, NTT_MAX_RANK) : NTT_MAX_RANK;
+    if (dims[0] > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+    for (int k = 1; k < d; ++k) {
+      const int64_t m = rk[k - 1] * dims[k - 1];
+      const int64_t n = prod(dims, k, d);
+      int64_t r = std::min(std::min(m, n), cap);
+      if (k < d - 1) r = std::min<int64_t>(r, NTT_MAX_ROWS / dims[k]);
+      if (r < 1) return NTT_ERR_UNSUPPORTED;
+      rk[k] = r;
+    }
+  } else {
+    const int64_t* ranks = desc->ranks;
+    if (ranks[0] != 1 || ranks[d] != 1) return NTT_ERR_INVALID_ARG;
+    for (int k = 1; k < d; ++k) {
+      const int64_t m = ranks[k - 1] * dims[k - 1];
+      const int64_t n = prod(dims, k, d);
+      if (ranks[k] < 1) return NTT_ERR_INVALID_ARG;
+      if (ranks[k] > m || ranks[k] > n) return NTT_ERR_RANK_INFEASIBLE;
+      if (ranks[k] > NTT_MAX_RANK || m > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+    }
+    rk.assign(ranks, ranks + d + 1);
   }
   ntt_plan p = new (std::nothrow) ntt_plan_s();
   if (!p) return NTT_ERR_OOM;
   p->d = d;
   p->dims.assign(dims, dims + d);
-  p->ranks.assign(ranks, ranks + d + 1);
+  p->ranks = rk;
+  p->auto_rank = auto_rank;
+  p->eps_rank = desc->eps_rank;
+  p->ranks_max = rk;
   p->iters = desc->iters;
   p->eps = desc->eps_mu;
   p->xdt = desc->x_dtype;
@@ -502,27 +647,17 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->tol = desc->tol;
   p->check = desc->tol > 0.0 ? desc->check_every : 0;
   p->route = desc->route;
-  p->eager = (desc->flags & NTT_PLAN_EAGER) != 0;
+  p->eager = auto_rank || (desc->flags & NTT_PLAN_EAGER) != 0;
   const int sms = device_sms();
   size_t max_part = 1, max_red = 1, maxH[2] = {1, 1}, max_xb = 1;
   for (int s = 0; s < d - 1; ++s) {
     ntt_plan_s::Stage S;
-    S.m = ranks[s] * dims[s];
-    S.n = prod(dims, s + 1, d);
-    S.r = (int)ranks[s + 1];
-    ntt_status e = mu_choose_shape(S.m, S.n, S.r, 0, sms, &S.f32);
-    if (e == NTT_OK && p->xdt == NTT_BF16) e = mu_choose_shape(S.m, S.n, S.r, 1, sms, &S.bf16);
+    const ntt_status e = make_stage(p, s, sms, &S);
     if (e != NTT_OK) {
       delete p;
       return e;
     }
-    S.f32.route = p->route;
-    S.bf16.route = p->route;
-    S.iters_total = p->iters + p->refine;
-    S.obj_off = p->obj_total;
     p->obj_total += S.iters_total;
-    const double xs = p->xdt == NTT_BF16 ? 2.0 : 4.0;
-    S.alg_bytes = (double)S.m * S.n * xs + 8.0 * S.r * S.n;
     size_t pf = mu_partial_floats(S.f32);
     if (p->xdt == NTT_BF16 && mu_partial_floats(S.bf16) > pf) pf = mu_partial_floats(S.bf16);
     if (pf > max_part) max_part = pf;
@@ -532,30 +667,34 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
     p->st.push_back(S);
   }
   // grouped-engine routes: plan each at offset 0 for its size; one scratch
-  // region shared by the routed stages follows the device layout
-  size_t grp = 0;
-  for (auto& S : p->st) {
-    for (int xb = 0; xb < 2; ++xb) {
-      ntt_plan_s::Route& rt = xb ? S.gbf16 : S.gf32;
-      if (xb && p->xdt != NTT_BF16) continue;
-      if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
-      if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route)) continue;
-      // a main loop with a stopping test runs on the single-problem passes
-      const bool main_loop = xb != 0 || p->xdt != NTT_BF16;
-      if (main_loop && p->tol > 0.0) continue;
-      GroupShape sh;
-      sh.n = S.n;
-      sh.m = (int)S.m;
-      sh.re = S.r;
-      sh.blk = S.r;
-      sh.xbf16 = xb;
-      if (group_plan({sh}, sms, 0, false, true, &rt.gp) != NTT_OK) continue;
-      rt.on = true;
-      grp = std::max(grp, rt.gp.bytes);
-      rt.host_off = p->h_bytes;
-      p->h_bytes += (rt.gp.table_bytes + 255) / 256 * 256;
+  // region shared by the routed stages follows the device layout.  With the
+  // rank rule, every rank up to the stage's maximum is sized for.
+  size_t grp = 0, hb = 0;
+  for (int s = 0; s < d - 1; ++s) {
+    if (!auto_rank) {
+      grp = std::max(grp, plan_stage_routes(p, p->st[s], sms, 0, &hb));
+      continue;
     }
+    size_t hmax = 0;
+    for (int64_t r = 1; r <= p->ranks_max[s + 1]; ++r) {
+      ntt_plan_s::Stage S;
+      p->ranks[s + 1] = r;
+      if (make_stage(p, s, sms, &S) != NTT_OK) continue;
+      size_t h = 0;
+      grp = std::max(grp, plan_stage_routes(p, S, sms, 0, &h));
+      hmax = std::max(hmax, h);
+    }
+    p->ranks[s + 1] = p->ranks_max[s + 1];
+    hb = std::max(hb, hmax);
   }
+  p->h_bytes = hb;
+  size_t rank_bytes = 0;
+  if (auto_rank)
+    for (int s = 0; s < d - 1; ++s) {
+      const int64_t n = prod(dims, s + 1, d);
+      for (int64_t r = 1; r <= p->ranks_max[s]; ++r)
+        rank_bytes = std::max(rank_bytes, rank_ws_layout(r * dims[s], n, sms).bytes);
+    }
   Arena ar;
   p->off_status = ar.take(64);
   p->off_tickets = ar.take(64);
@@ -570,29 +709,56 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->off_H[0] = ar.take(maxH[0] * 4);
   p->off_H[1] = ar.take(maxH[1] * 4);
   if (p->xdt == NTT_BF16) p->off_xb = ar.take(max_xb * 2);
+  if (auto_rank) {
+    p->off_rank = ar.take(rank_bytes);
+    p->rank_bytes = rank_bytes;
+  }
   if (grp) p->off_grp = ar.take(grp);
+  p->grp_bytes = grp;
   p->ws_bytes = ar.off;
   p->off_A[0] = ar.take((size_t)prod(dims, 0, d) * 4);
   p->off_A[1] = ar.take((size_t)prod(dims, 0, d) * 4);
   for (int k = 0; k < d; ++k)
-    p->core_off.push_back(ar.take((size_t)ranks[k] * dims[k] * ranks[k + 1] * 4));
+    p->core_off.push_back(ar.take((size_t)rk[k] * dims[k] * rk[k + 1] * 4));
   p->off_err = ar.take(8 * sizeof(double));
-  p->off_chain = ar.take(chain_layout(d, dims, ranks).total);
+  p->off_chain = ar.take(chain_layout(d, dims, rk.data()).total);
   p->ws_bytes_host = ar.off;
-  if (p->off_grp)
-    for (auto& S : p->st)
-      for (ntt_plan_s::Route* rt : {&S.gf32, &S.gbf16}) {
-        if (!rt->on) continue;
-        GroupShape sh;
-        sh.n = S.n;
-        sh.m = (int)S.m;
-        sh.re = S.r;
-        sh.blk = S.r;
-        sh.xbf16 = rt == &S.gbf16 ? 1 : 0;
-        if (group_plan({sh}, sms, p->off_grp, false, true, &rt->gp) != NTT_OK) rt->on = false;
-      }
+  if (!auto_rank && p->off_grp) {
+    size_t h = 0;
+    for (auto& S : p->st) plan_stage_routes(p, S, sms, p->off_grp, &h);
+  }
   *out = p;
   return NTT_OK;
+}
+
+ntt_status ntt_plan_get_ranks(ntt_plan plan, int64_t* ranks) {
+  if (!plan || !ranks) return NTT_ERR_INVALID_ARG;
+  for (int k = 0; k <= plan->d; ++k) ranks[k] = plan->ranks[k];
+  return NTT_OK;
+}
+
+ntt_status ntt_rank_workspace_size(int64_t m, int64_t n, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1) return NTT_ERR_INVALID_ARG;
+  if (std::min(m, n) > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+  *bytes = rank_ws_layout(m, n, device_sms()).bytes;
+  return NTT_OK;
+}
+
+ntt_status ntt_select_rank(int64_t m, int64_t n, const float* X, double eps_rank, int rank_cap, int* rank_dev,
+                           double* sigma_dev, void* ws, void* stream) {
+  if (!X || !ws || m < 1 || n < 1 || rank_cap < 0) return NTT_ERR_INVALID_ARG;
+  if (rank_dev && !(eps_rank >= 0.0)) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  if (std::min(m, n) > NTT_MAX_ROWS) return NTT_ERR_UNSUPPORTED;
+  const RankWs w = rank_ws_layout(m, n, device_sms());
+  NTT_CUDA_TRY(launch_rank_select(X, m, n, eps_rank, rank_cap, w, reinterpret_cast<char*>(ws), sigma_dev, rank_dev,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return NTT_OK;
+}
+
+ntt_status ntt_singular_values(int64_t m, int64_t n, const float* X, double* sigma_dev, void* ws, void* stream) {
+  if (!sigma_dev) return NTT_ERR_INVALID_ARG;
+  return ntt_select_rank(m, n, X, 0.0, 0, nullptr, sigma_dev, ws, stream);
 }
 
 ntt_status ntt_plan_workspace_size(ntt_plan plan, size_t* bytes) {
@@ -626,7 +792,9 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
     p->ev.assign(4 * d + 2, nullptr);
     for (auto& e : p->ev) NTT_CUDA_TRY(cudaEventCreate(&e));
   }
-  if (p->eager) {
+  if (p->auto_rank) {
+    NTT_TRY(decompose_auto_rank(p, A, cores, ws, st));
+  } else if (p->eager) {
     // the eager tables are rewritten: the previous run must have read them
     if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
     if (p->h_bytes && !p->h_eager) NTT_TRY(alloc_mapped(p->h_bytes, &p->h_eager, &p->h_eager_dev));

@@ -396,6 +396,20 @@ cudaError_t launch_small_mm(const float* A, const float* B, float* C, int64_t M,
 cudaError_t launch_handoff(float* W, float* H, int64_t m, int64_t n, int r, float* s_scratch,
                            cudaStream_t st);
 
+// Algorithm 2's rank rule on the device (ntt_rank.cu): Gram of the unfolding
+// on its smaller side (N = min(m, n) <= NTT_MAX_ROWS), FP64 eigenvalues by
+// tridiagonalisation and bisection, singular values and the tail rule.
+struct RankWs {
+  int M = 0, nb = 0, S = 0;
+  int64_t chunk = 0;
+  size_t off_part = 0, off_G = 0, off_d = 0, off_e = 0, off_sigma = 0, off_rank = 0, bytes = 0;
+};
+RankWs rank_ws_layout(int64_t m, int64_t n, int num_sms);
+// sigma_out (nullable: workspace) receives the N singular values, non-increasing;
+// rank_out (nullable) the rule's rank for eps_rank, capped by rank_cap (> 0).
+cudaError_t launch_rank_select(const float* X, int64_t m, int64_t n, double eps_rank, int rank_cap,
+                               const RankWs& w, char* ws, double* sigma_out, int* rank_out, cudaStream_t st);
+
 // Number of SMs of the current device (cached; 152 when no device).
 int device_sms();
 

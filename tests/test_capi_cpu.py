@@ -72,10 +72,25 @@ def test_plan_validation(lib):
     # iters < 1
     with pytest.raises(ntt.NTTError):
         ntt.ntt_plan_create((8, 8), (1, 2, 1), 0)
-    # no ranks: SVD rank selection is not built
+    # no ranks: Algorithm 2's rank rule needs eps_rank > 0
     with pytest.raises(ntt.NTTError) as e:
         ntt.ntt_plan_create((8, 8), None, 10)
+    assert e.value.code == 1
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan_create((8, 8), None, 10, eps_rank=0.1, rank_cap=-1)
+    assert e.value.code == 1
+    # rank-rule plans are sized for the largest ranks the rule may choose:
+    # min(m, n), the built maximum 32, the cap, and next height r_l n_{l+1} <= 512
+    p = ntt.ntt_plan_create((8, 8, 8, 8), None, 10, eps_rank=0.1)
+    assert p.current_ranks() == (1, 8, 32, 8, 1) and p.core_shapes()[1] == (8, 8, 32)
+    p = ntt.ntt_plan_create((8, 8, 8, 8), None, 10, eps_rank=0.1, rank_cap=5)
+    assert p.current_ranks() == (1, 5, 5, 5, 1)
+    p = ntt.ntt_plan_create((4, 200, 3), None, 10, eps_rank=0.1)
+    assert p.current_ranks() == (1, 2, 3, 1)     # 4 * 200 and 2 * 200 <= 512 needs r_1 <= 2
+    with pytest.raises(ntt.NTTError) as e:        # first unfolding taller than 512
+        ntt.ntt_plan_create((600, 4), None, 10, eps_rank=0.1)
     assert e.value.code == 6
+    assert p.workspace_size() > 0
     # stopping test: tol >= 0 (not NaN), check_every >= 1 when tol > 0
     for tol, k in ((-1e-3, 10), (float("nan"), 10), (1e-3, 0)):
         with pytest.raises(ntt.NTTError) as e:
