@@ -72,6 +72,10 @@ typedef enum {
                               forms that are slower than the FMA kernels on GB300 */
 } ntt_route;
 
+/* ntt_plan_desc.solver: the NMF of every stage */
+#define NTT_SOLVER_MU 0     /* Lee-Seung multiplicative updates (the default) */
+#define NTT_SOLVER_BCD 1    /* Algorithm 3, block coordinate descent (FP32 X, no stopping test) */
+
 /* ntt_plan_desc.flags */
 #define NTT_PLAN_EAGER 1u   /* enqueue every launch on each call instead of replaying a
                                cached CUDA graph (debugging; each call then first waits for
@@ -106,6 +110,7 @@ typedef struct {
                             The rule's rank is also capped at NTT_MAX_RANK and at
                             NTT_MAX_ROWS / n_{l+1}, so that the next unfolding fits the
                             built height (ntt_plan_get_ranks reports these bounds). */
+  int solver;            /* NTT_SOLVER_MU or NTT_SOLVER_BCD; `iters` counts its iterations */
 } ntt_plan_desc;
 
 /* Per-stage statistics, filled by ntt_plan_get_stats after the last call. */
@@ -133,6 +138,7 @@ typedef struct {
 #define NTT_ENGINE_TC_BF16 2          /* BF16-X tensor-core pass (tcgen05 kind::f16) */
 #define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (only with NTT_ROUTE_TC) */
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
+#define NTT_ENGINE_BCD_PASS 5         /* the fused pass in its BCD (Algorithm 3) mode */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);
@@ -218,6 +224,31 @@ ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype,
 ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
                        float* W, float* H, int iters, float eps_mu, double* obj_dev,
                        void* ws, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Algorithm 3 (distBCDnmf) on one GPU: block coordinate descent with
+ * prox-linear block steps, extrapolation and the correction test, as the
+ * APG-BCD method the paper cites defines them:
+ *   W_new = max(0, W_m - (W_m H H^T - X H^T) / ||H H^T||_2)
+ *   H_new = max(0, H_m - (W^T W H_m - W^T X) / ||W^T W||_2)      (W = W_new)
+ * An iteration whose objective 1/2||X - W H||^2 is not below the last
+ * accepted one is rejected: the next steps start from the last accepted
+ * iterate without extrapolation.  Otherwise t <- (1 + sqrt(1 + 4t^2))/2,
+ * w = (t_old - 1)/t and each block is extrapolated from its accepted iterate,
+ * X_m = X_new + min(w, 0.9999 sqrt(L_prev / L)) (X_new - X_acc).  The
+ * initial W and H are first scaled to Frobenius norm sqrt(||X||_F) each.
+ * Each iteration reads X once (the H step and X H^T, H H^T of the new H
+ * from the same tile); FP32 X, m <= NTT_MAX_ROWS, r <= NTT_MAX_RANK.
+ * ------------------------------------------------------------------------ */
+ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes);
+
+/* `iters` BCD iterations on the m x n FP32 X (device), W (m x r) and H
+ * (r x n) device FP32: initial factors in, the last accepted iterate out.
+ * obj_dev (nullable): `iters` doubles, obj_dev[t] = the last accepted
+ * objective after iteration t (FP64, Gram form).  ws: device,
+ * nmf_bcd_workspace_size bytes, 256-byte aligned (overwritten). */
+ntt_status nmf_bcd_step(int64_t m, int64_t n, int r, const float* X, float* W, float* H, int iters,
+                        double* obj_dev, void* ws, void* stream);
 
 /* nmf_mu_step with its kernel choice restricted by `route` (ntt_route; the
  * plan's routes other than NTT_ROUTE_GROUPED, which is a plan-level choice and

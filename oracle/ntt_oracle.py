@@ -243,7 +243,7 @@ def spectral_norm_sym(M):
     return float(np.max(np.linalg.eigvalsh(M)))
 
 
-def bcd_nmf(X, W0, H0, iters, delta=BCD_DELTA, record=True):
+def bcd_nmf(X, W0, H0, iters, delta=BCD_DELTA, record=True, info=None):
     """Algorithm 3 on one node (see the readings in the module docstring).
 
     Initial factors W0, H0 are scaled to Frobenius norm sqrt(||X||_F) each
@@ -256,7 +256,8 @@ def bcd_nmf(X, W0, H0, iters, delta=BCD_DELTA, record=True):
 
     Returns (W, H, trace, accepted): the last accepted factors, trace[l] = the
     last accepted objective after iteration l+1, accepted[l] = whether
-    iteration l+1 was accepted.
+    iteration l+1 was accepted.  info (optional dict) receives "f": the
+    objective of every iteration's new iterate, accepted or not.
     """
     X = np.asarray(X, dtype=np.float64)
     nx = float(np.linalg.norm(X))
@@ -281,6 +282,8 @@ def bcd_nmf(X, W0, H0, iters, delta=BCD_DELTA, record=True):
         Lh = spectral_norm_sym(WtW)
         H_new = np.maximum(0.0, H_m - (WtW @ H_m - W_new.T @ X) / Lh) if Lh > 0.0 else H_m.copy()
         f = objective(X, W_new, H_new)
+        if info is not None:
+            info.setdefault("f", []).append(f)
         if f >= obj:
             # correction: back to the last accepted iterate, no extrapolation
             W_m, H_m = W_acc, H_acc

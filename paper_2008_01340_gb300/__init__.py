@@ -54,7 +54,7 @@ EXPORTS = (
     "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
     "nmf_mu_step_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
-    "ntt_singular_values", "ntt_select_rank",
+    "ntt_singular_values", "ntt_select_rank", "nmf_bcd_workspace_size", "nmf_bcd_step",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
@@ -86,6 +86,7 @@ class _PlanDesc(ctypes.Structure):
         ("flags", ctypes.c_uint),
         ("eps_rank", ctypes.c_double),
         ("rank_cap", ctypes.c_int),
+        ("solver", ctypes.c_int),
     ]
 
 
@@ -131,7 +132,8 @@ class _Stats(ctypes.Structure):
     ]
 
 
-ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow"}
+ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow", 5: "bcd_pass"}
+SOLVERS = {"mu": 0, "bcd": 1}
 
 
 _lib_handle = None
@@ -167,6 +169,8 @@ def lib():
     L.ntt_status_of_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ntt_wait_probe.argtypes = [vp, i64, vp]
     L.ntt_plan_get_ranks.argtypes = [vp, p64]
+    L.nmf_bcd_workspace_size.argtypes = [i64, i64, i32, psz]
+    L.nmf_bcd_step.argtypes = [i64, i64, i32, vp, vp, vp, i32, vp, vp, vp]
     L.ntt_rank_workspace_size.argtypes = [i64, i64, psz]
     L.ntt_singular_values.argtypes = [i64, i64, vp, vp, vp, vp]
     L.ntt_select_rank.argtypes = [i64, i64, vp, ctypes.c_double, i32, vp, vp, vp, vp]
@@ -280,9 +284,10 @@ class Plan:
 
 
 def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iters=0, seed=0, tol=0.0,
-                    check_every=10, route="auto", eager=False, eps_rank=0.0, rank_cap=0):
+                    check_every=10, route="auto", eager=False, eps_rank=0.0, rank_cap=0, solver="mu"):
     """route: one of ROUTES (ntt_route); eager: enqueue every call instead of a cached graph;
-    ranks=None: Algorithm 2's rank rule with eps_rank (> 0) and optional rank_cap."""
+    ranks=None: Algorithm 2's rank rule with eps_rank (> 0) and optional rank_cap;
+    solver: "mu" (multiplicative updates) or "bcd" (Algorithm 3)."""
     dims = tuple(int(n) for n in dims)
     ranks = tuple(int(r) for r in ranks) if ranks is not None else None
     d_arr = _i64arr(dims)
@@ -302,6 +307,9 @@ def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iter
     desc.flags = NTT_PLAN_EAGER if eager else 0
     desc.eps_rank = float(eps_rank)
     desc.rank_cap = int(rank_cap)
+    if solver not in SOLVERS:
+        raise ValueError(f"solver must be one of {sorted(SOLVERS)}")
+    desc.solver = SOLVERS[solver]
     h = ctypes.c_void_p()
     _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
     plan = Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
@@ -408,6 +416,30 @@ def nmf_mu_step_noalloc(X, W, H, iters, eps_mu=1e-12, obj=None, stream=None):
                                      _dev_ptr(W, torch.float32, "W"),
                                      _dev_ptr(H, torch.float32, "H"), int(iters), float(eps_mu),
                                      optr, _stream_ptr(stream)), "nmf_mu_step_noalloc")
+
+
+def nmf_bcd_workspace_size(m, n, r):
+    b = ctypes.c_size_t(0)
+    _check(lib().nmf_bcd_workspace_size(int(m), int(n), int(r), ctypes.byref(b)), "nmf_bcd_workspace_size")
+    return b.value
+
+
+def nmf_bcd_step(X, W, H, iters, obj=None, workspace=None, stream=None):
+    """`iters` BCD iterations (Algorithm 3) on float32 CUDA X, W (m x r), H (r x n):
+    initial factors in, the last accepted iterate out; obj: optional float64 CUDA
+    tensor of `iters` entries receiving the accepted objective after each iteration."""
+    import torch
+    m, n = X.shape
+    r = W.shape[1]
+    if W.shape[0] != m or H.shape != (r, n):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = empty_workspace(nmf_bcd_workspace_size(m, n, r), X.device)
+    optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
+    _check(lib().nmf_bcd_step(m, n, r, _dev_ptr(X, torch.float32, "X"), _dev_ptr(W, torch.float32, "W"),
+                              _dev_ptr(H, torch.float32, "H"), int(iters), optr, _dev_ptr(workspace, None, "ws"),
+                              _stream_ptr(stream)), "nmf_bcd_step")
+    return workspace
 
 
 def _many_args(Xs, Ws, Hs):

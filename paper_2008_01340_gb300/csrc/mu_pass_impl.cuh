@@ -23,6 +23,15 @@
 //   phase B  thread = (row group g of RB stacked rows, 8-rank block, column
 //            group q): the stacked rows are [X_tile ; H_new ; 0] so P and Q
 //            come out of one register-blocked outer-product loop.
+//
+// BCD mode (Algorithm 3, the prox-linear block step): the same pass with the
+// H step of block coordinate descent in place of the multiplicative update,
+//   H_m   = H + w_h (H - H_prev)                     (extrapolation)
+//   H_new = max(0, H_m - (G_W H_m - W^T X) / L_h)    (projected gradient, L_h = ||G_W||_2)
+// H and H_prev are the last two accepted iterates and H_new goes to the third
+// buffer; the buffer roles rotate on the device (BcdState::rot), so a captured
+// graph replays every iteration unchanged.  The init launch (bcd_init) only
+// accumulates P = X H^T and Q = H H^T of the current H.
 #pragma once
 
 #include "ntt_internal.cuh"
@@ -39,11 +48,12 @@ __host__ __device__ constexpr int pick_nrg(int ms, int kbb, int nt) {
   return g;
 }
 
-template <int MP_, int R_, bool BF16_>
+template <int MP_, int R_, bool BF16_, bool BCD_ = false>
 struct PassCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
   static constexpr bool BF16 = BF16_;
+  static constexpr bool BCD = BCD_;                // BCD step: a second H tile (H_prev) per stage
   static constexpr int XB = BF16 ? 2 : 4;          // bytes per X element
   static constexpr int NT = kPassThreads;
   static constexpr int T = cmax(16, cmin(cmin(256, 8192 / MP), 4096 / R));
@@ -65,7 +75,8 @@ struct PassCfg {
   static constexpr int NXB = MP / BR;              // X boxes per tile
   static constexpr int XS_BYTES = MP * T * XB;
   static constexpr int HS_BYTES = R * T * 4;
-  static constexpr int STAGE_BYTES = (XS_BYTES + HS_BYTES + 1023) / 1024 * 1024;
+  static constexpr int NHT = BCD ? 2 : 1;          // H tiles per stage
+  static constexpr int STAGE_BYTES = (XS_BYTES + NHT * HS_BYTES + 1023) / 1024 * 1024;
   static constexpr int HN_ROWS = MSP - MP;
   static constexpr int HN_BYTES = HN_ROWS * T * 4;
   static constexpr int Y_BYTES = SA * R * T * 4;
@@ -78,7 +89,7 @@ struct PassCfg {
   static constexpr int STAGES = cmin(4, (SMEM_CAP - FIXED) / STAGE_BYTES);
   static constexpr int SMEM = STAGES * STAGE_BYTES + FIXED;
   static constexpr int RED_BYTES = MSP * R * CG * 4;
-  static constexpr uint32_t TX_BYTES = XS_BYTES + HS_BYTES;
+  static constexpr uint32_t TX_BYTES = XS_BYTES + NHT * HS_BYTES;
 
   static_assert(R % 8 == 0 && R <= 32, "rank bucket");
   static_assert(CH * KBA * SA == NT && SA * RPS == MP, "phase A mapping");
@@ -129,15 +140,23 @@ struct PassParams {
   int ntiles;
   int use_tma;
   float eps;
+  // BCD mode
+  float* Hb[3];              // the three H buffers (cooperative loader / stores)
+  const BcdState* bcd;       // rotation, w_h, L_h
+  int bcd_init;              // accumulate P, Q of the accepted H only
 };
 
+
+// tmH: the H tile loaded (updated in place in MU mode); tmHp: H_prev (BCD);
+// tmHs: the target of the H_new store.  Hld / Hp / Hst: the same buffers for
+// the cooperative path.  BCD step parameters come from the state.
 template <class C>
-__global__ void __launch_bounds__(kPassThreads, 1)
-mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmH,
-               const PassParams p) {
+__device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUtensorMap& tmH,
+                                             const CUtensorMap& tmHp, const CUtensorMap& tmHs,
+                                             const float* Hld, const float* Hp, float* Hst, float w_h,
+                                             float Lh, const PassParams& p) {
   using XT = typename XLoad<C::BF16>::T;
   constexpr int T = C::T, R = C::R, MP = C::MP, NT = C::NT;
-  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   constexpr int HNF = C::HN_BUF / 4;   // floats per H_new buffer
 
   extern __shared__ uint8_t smem_raw[];
@@ -161,6 +180,7 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     if (tma) {
       prefetch_tensormap(&tmX);
       prefetch_tensormap(&tmH);
+      if constexpr (C::BCD) prefetch_tensormap(&tmHp);
       for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
       fence_mbar_init();
     }
@@ -183,6 +203,7 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     for (int b = 0; b < C::NXB; ++b)
       tma_load_2d(dst + b * C::BR * T * C::XB, &tmX, tile * T, b * C::BR, bar);
     tma_load_2d(dst + C::XS_BYTES, &tmH, tile * T, 0, bar);
+    if constexpr (C::BCD) tma_load_2d(dst + C::XS_BYTES + C::HS_BYTES, &tmHp, tile * T, 0, bar);
   };
 
   int issued = 0;  // tiles issued by thread 0 (TMA mode)
@@ -233,7 +254,8 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       for (int idx = tid; idx < R * T; idx += NT) {
         const int k = idx / T, c = idx % T;
         const int64_t col = col0 + c;
-        Hw[idx] = (k < r && col < n) ? p.H[(int64_t)k * n + col] : 0.0f;
+        Hw[idx] = (k < r && col < n) ? Hld[(int64_t)k * n + col] : 0.0f;
+        if constexpr (C::BCD) Hw[R * T + idx] = (k < r && col < n) ? Hp[(int64_t)k * n + col] : 0.0f;
       }
       __syncthreads();
     }
@@ -272,7 +294,48 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     if (s_err) break;
 
     // ---------------- H update for column c, ranks kg*KPT ..
-    {
+    if constexpr (C::BCD) {
+      // H_m = H + w_h (H - H_prev); H_new = max(0, H_m - (G H_m - Y) / L_h)
+      const int c = tid % T;
+      const int kg = tid / T;
+      if (kg * C::KPT < R) {
+        float hm[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const float a = Hs[j * T + c], b = Hs[R * T + j * T + c];
+          hm[j] = fmaf(w_h, a - b, a);
+        }
+        const int64_t col = col0 + c;
+#pragma unroll
+        for (int kk = 0; kk < C::KPT; ++kk) {
+          const int k = kg * C::KPT + kk;
+          float hn;
+          if (p.bcd_init) {
+            hn = Hs[k * T + c];
+          } else {
+            float y = 0.0f;
+#pragma unroll
+            for (int s2 = 0; s2 < C::SA; ++s2) y += Ysm[(s2 * R + k) * T + c];
+            float gh = 0.0f;
+#pragma unroll
+            for (int j = 0; j < R; j += 4) {
+              const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + j);
+              gh = fmaf(g.x, hm[j], gh);
+              gh = fmaf(g.y, hm[j + 1], gh);
+              gh = fmaf(g.z, hm[j + 2], gh);
+              gh = fmaf(g.w, hm[j + 3], gh);
+            }
+            float hk = 0.0f;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+              if (j == k) hk = hm[j];
+            hn = Lh > 0.0f ? fmaxf(0.0f, hk - __fdiv_rn(gh - y, Lh)) : hk;
+          }
+          Hn[k * T + c] = hn;
+          if (!tma && !p.bcd_init && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
+        }
+      }
+    } else {
       const int c = tid % T;
       const int kg = tid / T;
       if (kg * C::KPT < R) {
@@ -303,7 +366,7 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             const float den = ((k & 1) ? gh[k / 2].y : gh[k / 2].x) + p.eps;
             const float hn = fmaxf(0.0f, __fdividef(h[k] * y, den));
             Hn[k * T + c] = hn;
-            if (!tma && k < r && col < n) p.H[(int64_t)k * n + col] = hn;
+            if (!tma && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
           }
         } else {
 #pragma unroll
@@ -327,15 +390,15 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
               if (j == k) hk = h[j];
             const float hn = fmaxf(0.0f, __fdividef(hk * y, gh + p.eps));
             Hn[k * T + c] = hn;
-            if (!tma && k < r && col < n) p.H[(int64_t)k * n + col] = hn;
+            if (!tma && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
           }
         }
       }
     }
     if (tma) fence_proxy_async_smem();   // H_new visible to the TMA store
     __syncthreads();
-    if (tma && tid == 0) {
-      tma_store_2d(&tmH, smem_u32(Hn), (int)col0, 0);
+    if (tma && tid == 0 && !(C::BCD && p.bcd_init)) {
+      tma_store_2d(&tmHs, smem_u32(Hn), (int)col0, 0);
       bulk_commit();
     }
 
@@ -424,6 +487,59 @@ mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 }
 
 template <class C>
+__global__ void __launch_bounds__(kPassThreads, 1)
+mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmH,
+               const PassParams p) {
+  if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
+  mu_pass_body<C>(tmX, tmH, tmH, tmH, p.H, p.H, p.H, 0.0f, 0.0f, p);
+}
+
+// BCD step: the buffer roles come from the state the previous combine wrote.
+template <class C>
+__global__ void __launch_bounds__(kPassThreads, 1)
+mu_pass_bcd_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ HMaps3 hm,
+                   const PassParams p) {
+  const int rot = __ldcg(&p.bcd->rot);
+  const int ia = rot, ip = (rot + 2) % 3, in = (rot + 1) % 3;
+  const float w_h = p.bcd_init ? 0.0f : __ldcg(&p.bcd->w_h);
+  const float Lh = __ldcg(&p.bcd->Lh);
+  mu_pass_body<C>(tmX, hm.h[ia], hm.h[ip], hm.h[in], p.Hb[ia], p.Hb[ip], p.Hb[in], w_h, Lh, p);
+}
+
+// One BCD pass launch of bucket C.  Hb: the three H buffers (device), maps of
+// the same (TMA mode); init: P, Q of the accepted H only.
+template <class C>
+cudaError_t launch_pass_bcd_cfg(const MuShape& s, const MuDev& d, const CUtensorMap& mx, const HMaps3& mh,
+                                float* const* Hb, const BcdState* st_dev, int init, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(mu_pass_bcd_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  PassParams p;
+  p.X = d.X;
+  p.H = Hb[0];
+  p.W = d.W;
+  p.G = d.G;
+  p.part = d.part;
+  p.status = d.status;
+  p.stop = nullptr;
+  p.n = s.n;
+  p.m = (int)s.m;
+  p.r = s.r;
+  p.ntiles = (int)((s.n + C::T - 1) / C::T);
+  p.use_tma = s.tma;
+  p.eps = 0.0f;
+  for (int i = 0; i < 3; ++i) p.Hb[i] = Hb[i];
+  p.bcd = st_dev;
+  p.bcd_init = init;
+  mu_pass_bcd_kernel<C><<<s.grid, kPassThreads, C::SMEM, st>>>(mx, mh, p);
+  return cudaGetLastError();
+}
+
+template <class C>
 cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                             const CUtensorMap& mh, cudaStream_t st) {
   static bool attr_set = false;  // per-device attribute; set once per process
@@ -447,6 +563,9 @@ cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const C
   p.ntiles = (int)((s.n + C::T - 1) / C::T);
   p.use_tma = s.tma;
   p.eps = eps;
+  p.Hb[0] = p.Hb[1] = p.Hb[2] = d.H;
+  p.bcd = nullptr;
+  p.bcd_init = 0;
   mu_pass_kernel<C><<<s.grid, kPassThreads, C::SMEM, st>>>(mx, mh, p);
   return cudaGetLastError();
 }

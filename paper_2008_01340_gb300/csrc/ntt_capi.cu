@@ -228,6 +228,8 @@ struct ntt_plan_s {
   std::vector<int64_t> ranks_max;   // the largest ranks the rule may pick (workspace sizing)
   size_t off_rank = 0, rank_bytes = 0;
   size_t grp_bytes = 0;             // grouped-engine scratch reserved in the layout
+  int solver = NTT_SOLVER_MU;       // NMF of every stage
+  size_t off_bcd = 0;               // BCD scratch (solver == NTT_SOLVER_BCD)
   size_t off_stop = 0;           // one stop word per stage
 
   // A stage's MU loop runs either on the single-problem pass (TMA, phase
@@ -354,6 +356,7 @@ size_t plan_stage_routes(ntt_plan p, ntt_plan_s::Stage& S, int sms, size_t base,
   for (int xb = 0; xb < 2; ++xb) {
     ntt_plan_s::Route& rt = xb ? S.gbf16 : S.gf32;
     rt.on = false;
+    if (p->solver != NTT_SOLVER_MU) continue;   // the grouped engine runs multiplicative updates only
     if (xb && p->xdt != NTT_BF16) continue;
     if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
     if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route)) continue;
@@ -431,6 +434,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
   dev.obj = obj + S.obj_off;
   dev.xnorm2 = xnorm2;
   dev.status = status;
+  dev.part64 = reinterpret_cast<double*>(ws + p->off_part64);
   NTT_CUDA_TRY(launch_gram(S.f32, dev, st));
   launches += 4;
   auto mu = [&](const ntt_plan_s::Route& rt, const MuShape& shp, const void* Xv, int iters,
@@ -461,7 +465,13 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
     launches += 3;   // table upload, ticket reset and the engine's own Gram launch
     return group_launch(rt.gp, ws, ws + rt.gp.off_tables, iters, p->eps, st, t0);
   };
-  if (p->xdt == NTT_BF16) {
+  if (p->solver == NTT_SOLVER_BCD) {
+    NTT_CUDA_TRY(rec(4 * s + 2));
+    dev.X = X;
+    p->st[s].engine = NTT_ENGINE_BCD_PASS;
+    NTT_TRY(run_bcd_iters(S.f32, dev, bcd_ws_layout(S.f32), ws + p->off_bcd, p->iters, 0, st));
+    launches += 6;   // three norms, scaling, Gram, H copy; the init pass and combine below
+  } else if (p->xdt == NTT_BF16) {
     __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ws + p->off_xb);
     NTT_CUDA_TRY(launch_cast_bf16(X, xb, S.m * S.n, st));
     launches += 1;
@@ -473,7 +483,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
     NTT_TRY(mu(S.gf32, S.f32, X, p->iters, 0));
   }
   NTT_CUDA_TRY(rec(4 * s + 3));
-  launches += 2LL * S.iters_total;
+  launches += 2LL * S.iters_total + (p->solver == NTT_SOLVER_BCD ? 2 : 0);
   // stage-end objective, direct FP64 pass: 1/2 ||X - W H||^2
   NTT_TRY(resid_into(X, 0, W, H, S.m, S.n, S.r, 1, 0.5, scal + NTT_MAX_D + s, nullptr,
                      reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
@@ -601,6 +611,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (desc->route < NTT_ROUTE_AUTO || desc->route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
   if (desc->flags & ~NTT_PLAN_EAGER) return NTT_ERR_INVALID_ARG;
   if (desc->tol > 0.0 && desc->check_every < 1) return NTT_ERR_INVALID_ARG;
+  if (desc->solver != NTT_SOLVER_MU && desc->solver != NTT_SOLVER_BCD) return NTT_ERR_INVALID_ARG;
+  if (desc->solver == NTT_SOLVER_BCD && (desc->x_dtype != NTT_F32 || desc->tol > 0.0)) return NTT_ERR_UNSUPPORTED;
   const int64_t* dims = desc->dims;
   for (int i = 0; i < d; ++i)
     if (dims[i] < 1) return NTT_ERR_INVALID_ARG;
@@ -647,6 +659,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->tol = desc->tol;
   p->check = desc->tol > 0.0 ? desc->check_every : 0;
   p->route = desc->route;
+  p->solver = desc->solver;
   p->eager = auto_rank || (desc->flags & NTT_PLAN_EAGER) != 0;
   const int sms = device_sms();
   size_t max_part = 1, max_red = 1, maxH[2] = {1, 1}, max_xb = 1;
@@ -688,6 +701,20 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
     hb = std::max(hb, hmax);
   }
   p->h_bytes = hb;
+  size_t bcd_bytes = 0;
+  if (p->solver == NTT_SOLVER_BCD)
+    for (int s = 0; s < d - 1; ++s) {
+      if (!auto_rank) {
+        bcd_bytes = std::max(bcd_bytes, bcd_ws_layout(p->st[s].f32).bytes);
+        continue;
+      }
+      for (int64_t r = 1; r <= p->ranks_max[s + 1]; ++r)
+        for (int64_t rp = 1; rp <= p->ranks_max[s]; ++rp) {
+          MuShape sh;
+          if (mu_choose_shape(rp * dims[s], prod(dims, s + 1, d), (int)r, 0, sms, &sh) == NTT_OK)
+            bcd_bytes = std::max(bcd_bytes, bcd_ws_layout(sh).bytes);
+        }
+    }
   size_t rank_bytes = 0;
   if (auto_rank)
     for (int s = 0; s < d - 1; ++s) {
@@ -715,6 +742,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   }
   if (grp) p->off_grp = ar.take(grp);
   p->grp_bytes = grp;
+  if (bcd_bytes) p->off_bcd = ar.take(bcd_bytes);
   p->ws_bytes = ar.off;
   p->off_A[0] = ar.take((size_t)prod(dims, 0, d) * 4);
   p->off_A[1] = ar.take((size_t)prod(dims, 0, d) * 4);
@@ -1020,6 +1048,42 @@ ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dty
   NTT_CUDA_TRY(launch_gram(s, dev, st));
   s.route = route;
   return run_mu_iters(s, dev, eps_mu, iters, 0, st, engine_out);
+}
+
+ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes) {
+  if (!bytes) return NTT_ERR_INVALID_ARG;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n, r, 0, device_sms(), &s));
+  size_t mu = 0;
+  mu_ws_layout(s, &mu);
+  *bytes = mu + bcd_ws_layout(s).bytes;
+  return NTT_OK;
+}
+
+ntt_status nmf_bcd_step(int64_t m, int64_t n, int r, const float* X, float* W, float* H, int iters,
+                        double* obj_dev, void* ws, void* stream) {
+  if (!X || !W || !H || !ws || iters < 0) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  if (r > m || r > n) return NTT_ERR_RANK_INFEASIBLE;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n, r, 0, device_sms(), &s));
+  size_t total = 0;
+  MuWs L = mu_ws_layout(s, &total);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  NTT_CUDA_TRY(launch_zero(w + L.status, L.tickets + 64 - L.status, st));
+  MuDev dev;
+  dev.X = X;
+  dev.W = W;
+  dev.H = H;
+  dev.G = reinterpret_cast<float*>(w + L.G);
+  dev.part = reinterpret_cast<float*>(w + L.part);
+  dev.red = reinterpret_cast<float*>(w + L.red);
+  dev.ticket = reinterpret_cast<unsigned*>(w + L.tickets);
+  dev.obj = obj_dev;
+  dev.status = reinterpret_cast<int*>(w + L.status);
+  dev.part64 = reinterpret_cast<double*>(w + L.part64);
+  return run_bcd_iters(s, dev, bcd_ws_layout(s), w + total, iters, 0, st);
 }
 
 ntt_status ntt_status_of_workspace(const void* ws, ntt_status* out) {

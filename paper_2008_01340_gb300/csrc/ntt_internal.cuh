@@ -298,6 +298,31 @@ struct MuShape {
   int part_stride() const { return (MP + R) * R; }
 };
 
+// Device state of a BCD solve (Algorithm 3), written by its combine kernel.
+struct BcdState {
+  int rot;          // accepted H in buffer rot, previous accepted in (rot + 2) % 3, new in (rot + 1) % 3
+  int init;         // 1 once the init combine has run
+  float w_h;        // extrapolation weight of the next H step (0 after a rejection)
+  float Lh;         // ||W^T W||_2 of the next H step
+  double obj;       // last accepted objective 1/2 ||X - W H||^2 (FP64, Gram form)
+  double t;         // extrapolation sequence t_k
+  double Lw, Lw_prev, Lh_prev;   // Lipschitz constants: current W step, last accepted iteration
+  int accepted;     // iterations accepted so far
+  int last_ok;      // whether the last iteration was accepted
+};
+
+struct HMaps3 {
+  CUtensorMap h[3];          // the three H buffers of a BCD solve
+};
+
+constexpr double kBcdDelta = 0.9999;   // delta of Algorithm 3's extrapolation weights
+
+// Scratch of a BCD solve (after the nmf_mu_step scratch): state, W_new,
+// accepted [P ; Q], the two extra H buffers, norms.
+struct BcdWs {
+  size_t state = 0, Wn = 0, pacc = 0, H1 = 0, H2 = 0, norms = 0, bytes = 0;
+};
+
 // Device pointers of one NMF.
 struct MuDev {
   const void* X = nullptr;
@@ -309,6 +334,7 @@ struct MuDev {
   unsigned* ticket = nullptr;    // last-block counter of the combine kernel
   double* obj = nullptr;         // objective trace or nullptr
   const double* xnorm2 = nullptr;
+  double* part64 = nullptr;      // FP64 partials of the residual kernel (2 * kMaxResidBlocks)
   int* status = nullptr;
   int blk = 0;                   // > 0: independent restarts of rank blk side by side
   // optional stopping test of the loop (the plan's main MU loop of a stage):
@@ -418,6 +444,12 @@ constexpr int kMaxResidBlocks = 4096;
 // the first objective entry).
 ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int iters, int t0,
                         cudaStream_t st, int* engine = nullptr);
+// Algorithm 3 (BCD): the scratch layout for a shape, and the enqueue of the
+// normalisation, the init pass/combine and `iters` (pass, combine) pairs with
+// the final H moved into dev.H.  dev.W / dev.H: initial factors in, accepted out.
+BcdWs bcd_ws_layout(const MuShape& s);
+ntt_status run_bcd_iters(const MuShape& shp, const MuDev& dev, const BcdWs& L, char* bws, int iters, int t0,
+                         cudaStream_t st);
 // Enqueue one residual / norm pass (see ResidArgs); part64 holds 2 * kMaxResidBlocks doubles.
 ntt_status resid_into(const void* X, int xbf16, const float* L, const float* Rm, int64_t M,
                       int64_t N, int r, int mode, double scale, double* acc, double* rel,

@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(kTriThreads) eig_rule_kernel(const double* d_i
   __syncthreads();
   for (int i = tid; i < M; i += kTriThreads) sigma[i] = sqrt(fmax(0.0, lam[M - 1 - i]));
   if (rank_out && tid == 0) {
+    // the total is the trace (= the sum of the eigenvalues), exactly 0 for X = 0
     double total = 0.0;
-    for (int i = 0; i < M; ++i) total += fmax(0.0, lam[i]);
+    for (int i = 0; i < M; ++i) total += d[i];
     int k_sel = M;
     if (!(total > 0.0)) {
       k_sel = 1;
