@@ -178,3 +178,29 @@ def test_bcd_ntt_16x6_final_error(ntt):
     print(f"16^6 BCD: gpu {eg:.6f} oracle {eo:.6f}; MU gpu {emu:.6f}")
     assert abs(eg - eo) <= 1e-3
     assert eg < emu
+
+
+def test_bcd_rejected_iteration_matches_oracle(ntt):
+    """A case whose 23rd iteration is rejected (the extrapolated step raises
+    the objective), with every decision of the first 26 clear by > 4e-2: the
+    device rejects the same iteration (its accepted-objective trace repeats the
+    previous value exactly) and the iterates after it still match."""
+    rng = np.random.Generator(np.random.PCG64(6))
+    m, n, r = 24, 3000, 4
+    X = (rng.random((m, r)) @ rng.random((r, n))).astype(np.float32)
+    X += (0.001 * rng.random((m, n))).astype(np.float32)
+    W0 = synth.uniform_matrix((m, r), 8)
+    H0 = synth.uniform_matrix((r, n), 9)
+    iters = 26
+    assert _decisions_clear(X, W0, H0, iters, margin=1e-3)
+    Wo, Ho, tr, acc = oracle.bcd_nmf(X.astype(np.float64), W0, H0, iters)
+    assert not acc[22] and acc[:22].all()
+    Wd = torch.from_numpy(W0.copy()).cuda()
+    Hd = torch.from_numpy(H0.copy()).cuda()
+    obj = torch.zeros(iters, dtype=torch.float64, device="cuda")
+    ntt.nmf_bcd_step(torch.from_numpy(X).cuda(), Wd, Hd, iters, obj)
+    torch.cuda.synchronize()
+    o = obj.cpu().numpy()
+    assert o[22] == o[21] and np.all(np.diff(o)[:21] < 0)
+    assert _rel(Wd.cpu().numpy(), Wo) <= REL_ITERATE
+    assert _rel(Hd.cpu().numpy(), Ho) <= REL_ITERATE
