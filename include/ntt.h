@@ -139,6 +139,7 @@ typedef struct {
 #define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (only with NTT_ROUTE_TC) */
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 #define NTT_ENGINE_BCD_PASS 5         /* the fused pass in its BCD (Algorithm 3) mode */
+#define NTT_ENGINE_TC_SPLIT 6         /* FP32 X split in two BF16 matrices on the tensor-core pass */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);
@@ -250,10 +251,18 @@ ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes);
 ntt_status nmf_bcd_step(int64_t m, int64_t n, int r, const float* X, float* W, float* H, int iters,
                         double* obj_dev, void* ws, void* stream);
 
+/* Workspace bytes of nmf_mu_step_route: with NTT_ROUTE_TC on an FP32 X of
+ * 128 or 256 rows at rank 9..32 (n a multiple of 8) it adds 4 m n bytes for
+ * the split tensor-core form's two BF16 terms of X; otherwise as
+ * nmf_mu_workspace_size. */
+ntt_status nmf_mu_workspace_size_route(int64_t m, int64_t n, int r, ntt_dtype x_dtype, int route,
+                                      size_t* bytes);
+
 /* nmf_mu_step with its kernel choice restricted by `route` (ntt_route; the
  * plan's routes other than NTT_ROUTE_GROUPED, which is a plan-level choice and
  * acts here as NTT_ROUTE_AUTO).  *engine_out (nullable) receives the
- * NTT_ENGINE_* of the pass that ran.  Other arguments as for nmf_mu_step. */
+ * NTT_ENGINE_* of the pass that ran.  ws: nmf_mu_workspace_size_route bytes.
+ * Other arguments as for nmf_mu_step. */
 ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype,
                              float* W, float* H, int iters, float eps_mu, double* obj_dev,
                              void* ws, void* stream, int route, int* engine_out);

@@ -53,7 +53,7 @@ EXPORTS = (
     "ntt_status_string", "ntt_version", "ntt_plan_create", "ntt_plan_workspace_size",
     "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
-    "nmf_mu_step_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
+    "nmf_mu_step_route", "nmf_mu_workspace_size_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
     "ntt_singular_values", "ntt_select_rank", "nmf_bcd_workspace_size", "nmf_bcd_step",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
@@ -132,7 +132,8 @@ class _Stats(ctypes.Structure):
     ]
 
 
-ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow", 5: "bcd_pass"}
+ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow", 5: "bcd_pass",
+           6: "tc_split"}
 SOLVERS = {"mu": 0, "bcd": 1}
 
 
@@ -163,6 +164,7 @@ def lib():
     L.ntt_plan_destroy.argtypes = [vp]
     L.nmf_mu_workspace_size.argtypes = [i64, i64, i32, i32, psz]
     L.nmf_mu_step.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.nmf_mu_workspace_size_route.argtypes = [i64, i64, i32, i32, i32, psz]
     L.nmf_mu_step_route.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp, vp, i32,
                                     ctypes.POINTER(ctypes.c_int)]
     L.nmf_mu_step_noalloc.argtypes = [i64, i64, i32, vp, i32, vp, vp, i32, ctypes.c_float, vp, vp]
@@ -364,11 +366,10 @@ def ntt_plan_get_stats(plan):
     return out
 
 
-def nmf_mu_workspace_size(m, n, r, x_dtype="f32"):
+def nmf_mu_workspace_size(m, n, r, x_dtype="f32", route="auto"):
     b = ctypes.c_size_t(0)
-    _check(lib().nmf_mu_workspace_size(int(m), int(n), int(r),
-                                       NTT_BF16 if x_dtype == "bf16" else NTT_F32, ctypes.byref(b)),
-           "nmf_mu_workspace_size")
+    _check(lib().nmf_mu_workspace_size_route(int(m), int(n), int(r), NTT_BF16 if x_dtype == "bf16" else NTT_F32,
+                                             _route(route), ctypes.byref(b)), "nmf_mu_workspace_size_route")
     return b.value
 
 
@@ -386,7 +387,7 @@ def nmf_mu_step(X, W, H, iters, eps_mu=1e-12, obj=None, workspace=None, stream=N
         raise ValueError("shape mismatch")
     xd = "bf16" if X.dtype == torch.bfloat16 else "f32"
     if workspace is None:
-        workspace = empty_workspace(nmf_mu_workspace_size(m, n, r, xd), X.device)
+        workspace = empty_workspace(nmf_mu_workspace_size(m, n, r, xd, route), X.device)
     optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
     eng = ctypes.c_int(-1)
     _check(lib().nmf_mu_step_route(m, n, r, _dev_ptr(X, None, "X"),

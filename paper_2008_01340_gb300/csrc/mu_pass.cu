@@ -112,13 +112,35 @@ static bool tcb_enabled(int MP, int route) {
 
 static bool tc_enabled(int route) { return route == NTT_ROUTE_TC; }
 
+// FP32 X with 128 or 256 rows at rank bucket 16 or 32 (n a multiple of 8)
+// runs on the split tensor-core form (X in two BF16 matrices) where the
+// caller provides its scratch.
+bool tcs_route_ok(int64_t m, int64_t n, int r, int route) {
+  if (route == NTT_ROUTE_FMA || route == NTT_ROUTE_GENERIC || route == NTT_ROUTE_GROUPED) return false;
+  int MP = 16;
+  while (MP < m) MP *= 2;
+  const int R = r <= 8 ? 8 : (r <= 16 ? 16 : 32);
+  return n % 8 == 0 && tcs_pass_supported(MP, R);
+}
+
 static bool narrow_enabled(int route) { return route != NTT_ROUTE_GENERIC; }
 
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tc = 0;
   s->tcb = 0;
+  s->tcs = 0;
   s->narrow = 0;
+  if (!s->bf16 && s->tma && s->split_ok && tcs_route_ok(s->m, s->n, s->r, s->route)) {
+    s->tcs = 1;
+    s->T = 64;
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+    return;
+  }
   if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP, s->route)) {
     s->tcb = 1;
     s->T = 128;
@@ -208,6 +230,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st) {
+  if (s.tcs) return launch_mu_pass_tcs(s, d, eps, st);
   if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
   if (s.tc) return launch_mu_pass_tc(s, d, eps, mx, mh, st);
   if (s.narrow) return launch_mu_pass_narrow(s, d, eps, mx, mh, st);

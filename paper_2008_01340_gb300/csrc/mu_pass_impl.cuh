@@ -302,8 +302,10 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
         float hm[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
+          // no extrapolation (first step, after a rejection): H_prev is not read,
+          // so a buffer that holds no iterate yet cannot leak into H_m
           const float a = Hs[j * T + c], b = Hs[R * T + j * T + c];
-          hm[j] = fmaf(w_h, a - b, a);
+          hm[j] = w_h != 0.0f ? fmaf(w_h, a - b, a) : a;
         }
         const int64_t col = col0 + c;
 #pragma unroll

@@ -15,7 +15,7 @@
 //   phase B  D_B += [X_tile ; Hstack] Hstack^T                    (K = columns)
 //            P = sum over the three column groups of the X rows,
 //            Q = sum over the nine (row term, column term) blocks
-// D_B accumulates in TMEM over runs of kFlushB tiles (2048 columns); after
+// D_B accumulates in TMEM over runs of 2048 columns; after
 // each run its term sums are added, in FP32, into the CTA's (MP + R) x R
 // partial block in HBM, which the common combine kernel reduces.  Measured:
 // long TMEM runs carry a small accumulation bias -- 12 iterations on
@@ -32,6 +32,15 @@
 // earlier, has then completed too), and overlaps the epilogue and phase B.
 // Every wait is bounded; on expiry the kernel sets the status word, drains
 // its MMAs and copies, frees its TMEM and returns.
+//
+// Split form (FP32 X, 128/256 rows): the unfolding is first split once per
+// stage into two BF16 matrices X1 = bf16(X), X2 = bf16(X - X1) (16
+// significand bits of X; the same HBM bytes per iteration as FP32 X).  A tile
+// then covers 64 columns: its first 64-column atom holds X1 and the second X2,
+// so phase A (M = 128 over both atoms) leaves X1^T W in TMEM lanes c and
+// X2^T W in lanes 64 + c, summed in the epilogue, and phase B (K = 128 over
+// both atoms, the H_new terms written into both atoms of the stack) sums
+// (X1 + X2) H_new^T; Q = H_new H_new^T runs over the first atom only.
 #include "ntt_internal.cuh"
 
 namespace ntt {
@@ -39,7 +48,6 @@ namespace ntt {
 namespace {
 
 constexpr int kTbThreads = 256;
-constexpr int kFlushB = 16;   // tiles per TMEM accumulation run of D_B
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -74,11 +82,14 @@ __device__ __forceinline__ void split3(float a, __nv_bfloat16* t) {
   t[2] = __float2bfloat16_rn(r2);
 }
 
-template <int MP_, int R_>
+template <int MP_, int R_, bool SPLIT_ = false>
 struct TbCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
-  static constexpr int T = 128;
+  static constexpr bool SPLIT = SPLIT_;            // X = X1 + X2 in two BF16 matrices
+  static constexpr int T = 128;                    // tile width in shared memory (MMA M of phase A)
+  static constexpr int TC = SPLIT ? 64 : T;        // columns of X per tile
+  static constexpr int FLUSH = 2048 / TC;          // tiles per TMEM accumulation run of D_B
   static constexpr int N3 = 3 * R;                 // MMA N: three terms of R ranks
   static constexpr int KH = R / 2;                 // ranks per thread in the epilogue
   // Stacked form (MP <= 32): a stage holds 128 rows, X in rows 0..MP-1 and the
@@ -100,13 +111,18 @@ struct TbCfg {
   static constexpr int OFF_W = OFF_HN + HNS;
   static constexpr int OFF_G = OFF_W + WOP;
   static constexpr int OFF_QS = OFF_G + R * R * 4;   // 3R x R scratch of the Q term rows
-  static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4;
+  // split form: X2 parts of Y (64 x R); they share the Q term scratch when it is
+  // large enough (the flush that uses it and the epilogue never overlap)
+  static constexpr bool YS_IN_QS = 3 * R * R >= 64 * R;
+  static constexpr int OFF_YS = YS_IN_QS ? OFF_QS : OFF_QS + 3 * R * R * 4;
+  static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4 + (SPLIT && !YS_IN_QS ? 64 * R * 4 : 0);
   static constexpr int USED = OFF_BAR + 64;
   static constexpr int SMEM = USED + 1024;         // + alignment of the 1024-byte atoms
   static constexpr uint32_t TMEM_COLS = STACK ? 256 : 512;   // D_A (N3) + D_B ((NMB + 1) N3)
   static constexpr uint32_t IDA = idesc_bf16(128, N3, true, false);
   static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
   static_assert((MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
+  static_assert(!SPLIT || !STACK, "the split form needs a separate H_new stack");
   static_assert(!STACK || MP + 3 * R <= 128, "stacked rows fit one M block");
   static_assert(N3 * (NMB + 2) <= (int)TMEM_COLS, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -115,6 +131,7 @@ struct TbCfg {
 
 struct TbParams {
   const __nv_bfloat16* X;   // m x n BF16, row stride n (n % 8 == 0, 16-byte aligned)
+  const __nv_bfloat16* X2;  // split form: the second term X - X1 (same layout)
   float* H;                 // r x n FP32, updated in place
   const float* W;           // m x r
   const float* G;           // R x R
@@ -183,13 +200,15 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   // n; tiles past the CTA's range issue nothing but still commit a group
   auto issue = [&](int stage, int tile, bool valid) {
     uint8_t* dst = smem + C::OFF_X + stage * C::XST;
-    const int64_t col0 = (int64_t)tile * T;
+    const int64_t col0 = (int64_t)tile * C::TC;
     for (int e = tid; valid && e < m * (T / 8); e += kTbThreads) {
       const int row = e / (T / 8), ch = e % (T / 8);
-      const int64_t col = col0 + 8 * ch;
+      // split form: chunks 0..7 from X1, 8..15 from X2 (the same 64 columns)
+      const int term = C::SPLIT ? ch / 8 : 0;
+      const int64_t col = col0 + 8 * (C::SPLIT ? ch % 8 : ch);
       const int64_t left = n - col;
       const int bytes = left >= 8 ? 16 : (left > 0 ? (int)left * 2 : 0);
-      const __nv_bfloat16* src = p.X + (int64_t)row * n + (bytes ? col : 0);
+      const __nv_bfloat16* src = (term ? p.X2 : p.X) + (int64_t)row * n + (bytes ? col : 0);
       const uint32_t off = swz(row, 8 * ch, C::SR);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + off)), "l"(src),
                    "r"(bytes)
@@ -202,8 +221,11 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   const uint64_t dW = smem_desc(sbase + C::OFF_W, 16, 1024, kLayoutSw128);
   const uint64_t dH = smem_desc(sbase + C::OFF_HN, 16, 1024, kLayoutSw128);
 
-  // epilogue role: column c (TMEM lane), ranks kh0 .. kh0 + KH - 1
+  // epilogue role: TMEM lane c, ranks kh0 .. kh0 + KH - 1; the tile column is
+  // c (split form: c % 64, lanes 64.. holding the X2 part of the same column)
   const int c = (warp % 4) * 32 + lane;
+  const int cc = C::SPLIT ? c % 64 : c;
+  const bool owner = !C::SPLIT || c < 64;   // threads that update H
   const int kh0 = (warp / 4) * KH;
   const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
 
@@ -211,6 +233,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   float* out = p.part + (size_t)blockIdx.x * ((MP + R) * R);
   for (int e = tid; e < (MP + R) * R; e += kTbThreads) out[e] = 0.0f;
   float* qs = reinterpret_cast<float*>(smem + C::OFF_QS);
+  float* ys = reinterpret_cast<float*>(smem + C::OFF_YS);   // split form: X2 parts of Y
   // Add the finished TMEM run of D_B: P rows (X blocks) straight into `out`
   // (each entry owned by one thread), Q through the term sums in `qs`.
   auto flush = [&]() {
@@ -254,7 +277,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   for (; j < count; ++j) {
     const int s = j % C::STAGES;
     const int tile = (int)blockIdx.x + j * (int)gridDim.x;
-    const int64_t col = (int64_t)tile * T + c;
+    const int64_t col = (int64_t)tile * C::TC + cc;
     asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
     fence_proxy_async_smem();
     __syncthreads();
@@ -271,13 +294,13 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     // old H of this column, all ranks (overlaps the MMAs)
     float h[R];
 #pragma unroll
-    for (int l = 0; l < R; ++l) h[l] = (l < r && col < n) ? p.H[(int64_t)l * n + col] : 0.0f;
+    for (int l = 0; l < R; ++l) h[l] = (owner && l < r && col < n) ? p.H[(int64_t)l * n + col] : 0.0f;
     if (!mbar_wait_bounded(barA, (uint32_t)(j & 1))) s_err = 1;
     tc_fence_after();
     __syncthreads();
     if (s_err) break;
-    // phase B of tile j-1 is complete: end the TMEM run every kFlushB tiles
-    if (j > 0 && j % kFlushB == 0) flush();
+    // phase B of tile j-1 is complete: end the TMEM run every FLUSH tiles
+    if (j > 0 && j % C::FLUSH == 0) flush();
     // tile j + STAGES - 1 into the stage of tile j - 1, whose readers (phases A
     // and B of tile j - 1) are done
     issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x, j + C::STAGES - 1 < count);
@@ -297,6 +320,16 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
       }
     }
     tc_fence_before();
+    if constexpr (C::SPLIT) {
+      // Y = X1^T W (lane c) + X2^T W (lane 64 + c)
+      if (!owner)
+#pragma unroll
+        for (int q = 0; q < KH; ++q) ys[(c - 64) * R + kh0 + q] = y[q];
+      __syncthreads();
+      if (owner)
+#pragma unroll
+        for (int q = 0; q < KH; ++q) y[q] += ys[c * R + kh0 + q];
+    }
     float hn[KH];
 #pragma unroll
     for (int q = 0; q < KH; ++q) {
@@ -318,14 +351,19 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     }
 #pragma unroll
     for (int q = 0; q < KH; ++q) {
+      if (!owner) break;
       const int k = kh0 + q;
       if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[q];
       __nv_bfloat16 t3[3];
       split3(hn[q], t3);
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
+      for (int t = 0; t < 3; ++t) {
         *reinterpret_cast<__nv_bfloat16*>(smem + (C::STACK ? C::OFF_X + s * C::XST : C::OFF_HN) +
                                           swz(C::HROW0 + t * R + k, c, C::HSR)) = t3[t];
+        // split form: the same terms under the X2 atom of the tile
+        if constexpr (C::SPLIT)
+          *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_HN + swz(C::HROW0 + t * R + k, c + 64, C::HSR)) = t3[t];
+      }
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -336,7 +374,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
 #pragma unroll
       for (int kk = 0; kk < T / 16; ++kk) {
         const uint32_t xo = (uint32_t)((kk >> 2) * C::SR * 128 + (kk & 3) * 32);
-        const uint32_t acc = (j % kFlushB != 0 || kk > 0) ? 1u : 0u;
+        const uint32_t acc = (j % C::FLUSH != 0 || kk > 0) ? 1u : 0u;
         if constexpr (C::STACK) {
           // one block: A = the stage's 128 rows [X ; H_new terms ; 0], B = its H_new rows
           const uint32_t base = sbase + C::OFF_X + s * C::XST + xo;
@@ -348,7 +386,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
           for (int mb = 0; mb < C::NMB; ++mb)
             mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
                      dH + (uint64_t)(ho >> 4), C::IDB, acc);
-          mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
+          // Q once per column: the split form's second atom repeats the H terms
+          if (!C::SPLIT || kk < 4) mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
         }
       }
       mma_commit(barB);
@@ -400,8 +439,9 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;
-  p.ntiles = (int)((s.n + C::T - 1) / C::T);
+  p.ntiles = (int)((s.n + C::TC - 1) / C::TC);
   p.eps = eps;
+  p.X2 = reinterpret_cast<const __nv_bfloat16*>(d.X2);
   mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(p);
   return cudaGetLastError();
 }
@@ -410,6 +450,16 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
 
 bool tcb_pass_supported(int MP, int R) {
   return (MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32);
+}
+
+bool tcs_pass_supported(int MP, int R) { return (MP == 128 || MP == 256) && (R == 16 || R == 32); }
+
+cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  if (s.MP == 128 && s.R == 16) return launch_tcb_cfg<TbCfg<128, 16, true>>(s, d, eps, st);
+  if (s.MP == 128 && s.R == 32) return launch_tcb_cfg<TbCfg<128, 32, true>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 16) return launch_tcb_cfg<TbCfg<256, 16, true>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 32) return launch_tcb_cfg<TbCfg<256, 32, true>>(s, d, eps, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {

@@ -1,6 +1,8 @@
 // Auxiliary kernels of the nTT path:
 //   uniform_kernel   counter-based U[0,1) initialisation of W and H (INIT)
 //   cast_bf16_kernel FP32 -> BF16 (round to nearest even) staging of X
+//   split_bf16x2_kernel FP32 X -> bf16(X) and bf16(X - bf16(X)) (the split form
+//                    of the tensor-core pass)
 //   resid_kernel     ||X||^2, ||X - L R||^2 (FP64) or L R written out:
 //                    objective at stage end, Eq. (3) and Eq. (2) via the
 //                    split-chain product
@@ -46,6 +48,16 @@ __global__ void wait_probe_kernel(const void* src, int* status, long long limit_
   const bool ok = mbar_wait_bounded(never, 0, limit_ns);
   const bool drained = mbar_wait_bounded(copy, 0);   // the copy completes by itself
   if (!ok || !drained) atomicExch(status, kStatusTimeout);
+}
+
+__global__ void split_bf16x2_kernel(const float* in, __nv_bfloat16* x1, __nv_bfloat16* x2, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const float v = in[i];
+    const __nv_bfloat16 a = __float2bfloat16_rn(v);
+    x1[i] = a;
+    x2[i] = __float2bfloat16_rn(v - __bfloat162float(a));
+  }
 }
 
 __global__ void cast_bf16_kernel(const float* in, __nv_bfloat16* out, int64_t count) {
@@ -325,6 +337,13 @@ cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStre
 cudaError_t launch_wait_probe(const void* src, int* status, long long limit_ns, cudaStream_t st) {
   if (reinterpret_cast<uintptr_t>(src) & 15) return cudaErrorInvalidValue;
   wait_probe_kernel<<<1, 32, 0, st>>>(src, status, limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16* X2, int64_t count,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  split_bf16x2_kernel<<<grid_for(count, kAuxThreads * 4), kAuxThreads, 0, st>>>(X, X1, X2, count);
   return cudaGetLastError();
 }
 

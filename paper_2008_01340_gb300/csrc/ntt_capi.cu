@@ -33,15 +33,24 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
   std::memset(&mx, 0, sizeof(mx));
   std::memset(&mh, 0, sizeof(mh));
   MuShape s = shp;
+  s.split_ok = dev.xs != nullptr && !s.bf16;
   mu_finalize_shape(&s, dev.X, dev.H, device_sms());
   if (engine)
-    *engine = s.tcb ? NTT_ENGINE_TC_BF16
-                    : (s.tc ? NTT_ENGINE_TC_TF32 : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS));
-  if (s.tma) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
+    *engine = s.tcs ? NTT_ENGINE_TC_SPLIT
+                    : (s.tcb ? NTT_ENGINE_TC_BF16
+                             : (s.tc ? NTT_ENGINE_TC_TF32 : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS)));
+  MuDev d = dev;
+  if (s.tcs) {
+    // X = X1 + X2 (bf16(X) and bf16(X - bf16(X))), once for the whole loop
+    const int64_t mn = s.m * s.n;
+    NTT_CUDA_TRY_NS(launch_split_bf16x2(reinterpret_cast<const float*>(dev.X), dev.xs, dev.xs + mn, mn, st));
+    d.X = dev.xs;
+    d.X2 = dev.xs + mn;
+  }
+  if (s.tma && !s.tcs) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
   for (int t = 0; t < iters; ++t) {
-    NTT_CUDA_TRY_NS(launch_mu_pass(s, dev, eps, mx, mh, st));
-    MuDev d2 = dev;
-    NTT_CUDA_TRY_NS(launch_mu_combine(s, d2, eps, t0 + t, st));
+    NTT_CUDA_TRY_NS(launch_mu_pass(s, d, eps, mx, mh, st));
+    NTT_CUDA_TRY_NS(launch_mu_combine(s, d, eps, t0 + t, st));
   }
   return NTT_OK;
 }
@@ -109,7 +118,7 @@ int64_t prod(const int64_t* v, int a, int b) {  // prod v[a..b)
 
 // Scratch of one multiplicative-update NMF (shared by nmf_mu_step and stages).
 struct MuWs {
-  size_t status, tickets, scal, G, red, part, part64;
+  size_t status, tickets, scal, G, red, part, part64, xs;
 };
 
 size_t mu_partial_floats(const MuShape& s) { return (size_t)s.grid_cap * s.part_stride(); }
@@ -230,6 +239,7 @@ struct ntt_plan_s {
   size_t grp_bytes = 0;             // grouped-engine scratch reserved in the layout
   int solver = NTT_SOLVER_MU;       // NMF of every stage
   size_t off_bcd = 0;               // BCD scratch (solver == NTT_SOLVER_BCD)
+  size_t off_xs = 0;                // the two BF16 terms of a split-form stage's X
   size_t off_stop = 0;           // one stop word per stage
 
   // A stage's MU loop runs either on the single-problem pass (TMA, phase
@@ -324,6 +334,8 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route) {
   if (route == NTT_ROUTE_GROUPED) return true;
   if (route == NTT_ROUTE_TC && ((xbf16 && tcb_pass_supported(MP, R)) || (!xbf16 && tc_pass_supported(MP, R))))
     return false;
+  // FP32 stages of 128/256 rows at rank 16/32: the split tensor-core form
+  if (!xbf16 && tcs_route_ok(m, n, r, route)) return false;
   if (route != NTT_ROUTE_FMA && xbf16 && tcb_pass_supported(MP, R) && MP >= 128) return false;
   return MP <= 256 && R >= 16;
 }
@@ -443,6 +455,8 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
     const bool main_loop = t0 == 0;
     if (!rt.on) {
       dev.X = Xv;
+      // the split tensor-core form on FP32 unfoldings, when the layout reserved its terms
+      dev.xs = (p->off_xs && Xv == (const void*)X) ? reinterpret_cast<__nv_bfloat16*>(ws + p->off_xs) : nullptr;
       dev.stop = main_loop && p->tol > 0.0 ? stop + s : nullptr;
       dev.tol = p->tol;
       dev.check = p->check;
@@ -701,6 +715,18 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
     hb = std::max(hb, hmax);
   }
   p->h_bytes = hb;
+  // split-form terms (2 m n BF16) for FP32 stages the split tensor-core pass may take
+  size_t xs_bytes = 0;
+  if (p->solver == NTT_SOLVER_MU)
+    for (int s = 0; s < d - 1; ++s) {
+      const int64_t n = prod(dims, s + 1, d);
+      for (int64_t rp = auto_rank ? 1 : p->ranks_max[s]; rp <= p->ranks_max[s]; ++rp) {
+        const int64_t m = rp * dims[s];
+        for (int64_t r = auto_rank ? 1 : p->ranks_max[s + 1]; r <= p->ranks_max[s + 1]; ++r)
+          if (tcs_route_ok(m, n, (int)r, p->route) && !plan_route_group(m, n, (int)r, false, p->route))
+            xs_bytes = std::max(xs_bytes, (size_t)(m * n) * 4);
+      }
+    }
   size_t bcd_bytes = 0;
   if (p->solver == NTT_SOLVER_BCD)
     for (int s = 0; s < d - 1; ++s) {
@@ -743,6 +769,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   if (grp) p->off_grp = ar.take(grp);
   p->grp_bytes = grp;
   if (bcd_bytes) p->off_bcd = ar.take(bcd_bytes);
+  if (xs_bytes) p->off_xs = ar.take(xs_bytes);
   p->ws_bytes = ar.off;
   p->off_A[0] = ar.take((size_t)prod(dims, 0, d) * 4);
   p->off_A[1] = ar.take((size_t)prod(dims, 0, d) * 4);
@@ -983,7 +1010,7 @@ ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
 // ---------------------------------------------------------------------------
 // Single NMF
 // ---------------------------------------------------------------------------
-static MuWs mu_ws_layout(const MuShape& s, size_t* total) {
+static MuWs mu_ws_layout(const MuShape& s, size_t* total, bool split = false) {
   Arena ar;
   MuWs w;
   w.status = ar.take(64);
@@ -993,8 +1020,21 @@ static MuWs mu_ws_layout(const MuShape& s, size_t* total) {
   w.red = ar.take((size_t)s.part_stride() * 4);
   w.part = ar.take(mu_partial_floats(s) * 4);
   w.part64 = ar.take(2 * kMaxResidBlocks * sizeof(double));
+  w.xs = split ? ar.take((size_t)s.m * s.n * 4) : 0;
   *total = ar.off;
   return w;
+}
+
+ntt_status nmf_mu_workspace_size_route(int64_t m, int64_t n, int r, ntt_dtype x_dtype, int route,
+                                      size_t* bytes) {
+  if (!bytes) return NTT_ERR_INVALID_ARG;
+  if (x_dtype != NTT_F32 && x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
+  if (route < NTT_ROUTE_AUTO || route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
+  const bool split = route == NTT_ROUTE_TC && x_dtype == NTT_F32 && tcs_route_ok(m, n, r, route);
+  mu_ws_layout(s, bytes, split);
+  return NTT_OK;
 }
 
 ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype, size_t* bytes) {
@@ -1024,7 +1064,9 @@ ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dty
   MuShape s;
   NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
   size_t total = 0;
-  MuWs L = mu_ws_layout(s, &total);
+  // the split tensor-core form only with NTT_ROUTE_TC (its terms take 4 m n bytes of workspace)
+  const bool split = route == NTT_ROUTE_TC && x_dtype == NTT_F32 && tcs_route_ok(m, n, r, route);
+  MuWs L = mu_ws_layout(s, &total, split);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
   // status word and tickets are consecutive in the layout
@@ -1045,6 +1087,7 @@ ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dty
   dev.obj = obj_dev;
   dev.xnorm2 = scal;
   dev.status = reinterpret_cast<int*>(w + L.status);
+  dev.xs = split ? reinterpret_cast<__nv_bfloat16*>(w + L.xs) : nullptr;
   NTT_CUDA_TRY(launch_gram(s, dev, st));
   s.route = route;
   return run_mu_iters(s, dev, eps_mu, iters, 0, st, engine_out);

@@ -292,8 +292,10 @@ struct MuShape {
   int tma = 0;       // X/H tiles loaded by TMA (else cooperative loads)
   int tc = 0;        // tensor-core (tcgen05) pass instead of the FMA pass
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
+  int tcs = 0;       // FP32 X split in two BF16 matrices on the same tensor-core pass
   int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
   int route = NTT_ROUTE_AUTO;   // ntt_route restricting the pass choice
+  int split_ok = 0;  // scratch for the two BF16 terms of X exists (MuDev::xs)
   size_t smem = 0;   // dynamic shared memory of the pass kernel
   int part_stride() const { return (MP + R) * R; }
 };
@@ -326,6 +328,8 @@ struct BcdWs {
 // Device pointers of one NMF.
 struct MuDev {
   const void* X = nullptr;
+  const void* X2 = nullptr;      // split form: X - bf16(X) in BF16 (X then holds bf16(X))
+  __nv_bfloat16* xs = nullptr;   // scratch of 2 m n BF16 for the split form, or NULL
   float* W = nullptr;
   float* H = nullptr;
   float* G = nullptr;            // R x R Gram of W, zero padded
@@ -349,6 +353,8 @@ struct MuDev {
 
 // Pick template bucket, tile width and grid for an m x n x r problem.
 ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, MuShape* out);
+// Whether the split tensor-core form may run this FP32 shape under `route`.
+bool tcs_route_ok(int64_t m, int64_t n, int r, int route);
 // Whether X and H of these pointers can use TMA (alignment rules of the tensor maps).
 bool mu_tma_ok(const MuShape& s, const void* X, const float* H);
 // Decide TMA / tensor-core pass for these pointers (may change T and grid).
@@ -369,6 +375,13 @@ cudaError_t launch_gram(const MuShape& s, const MuDev& d, cudaStream_t st);
 // BF16-X tensor-core pass (tcgen05 kind::f16) for 128 or 256 rows and rank buckets 16, 32.
 bool tcb_pass_supported(int MP, int R);
 cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
+// FP32 X split in two BF16 matrices (X1 = bf16(X), X2 = bf16(X - X1)) on the
+// BF16 tensor-core pass, 64 columns per tile: 128 or 256 rows, rank buckets 16, 32.
+bool tcs_pass_supported(int MP, int R);
+cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
+// X1 = bf16(X), X2 = bf16(X - X1) elementwise (round to nearest even).
+cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16* X2, int64_t count,
+                                cudaStream_t st);
 // Warp-streamed FMA pass for 16/32-row buckets at rank bucket 8 (FP32 X, TMA-aligned).
 bool narrow_pass_supported(int MP, int R);
 cudaError_t launch_mu_pass_narrow(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,

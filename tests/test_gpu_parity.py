@@ -605,3 +605,74 @@ def test_mu_bf16_stacked_tensor_core_form(ntt, m, n, r):
     Wo, Ho, _ = oracle.nmf_mu(Xb.to(torch.float64).numpy(), W0, H0, 10)
     assert _fro_rel(Wd.cpu().numpy(), Wo) <= REL_ITERATE
     assert _fro_rel(Hd.cpu().numpy(), Ho) <= REL_ITERATE
+
+
+# ------------------------------------------------------------------ FP32 X on the tensor cores (split form)
+
+@pytest.mark.parametrize("m,n,r,kind", [(256, 40000, 16, "lowrank"), (128, 20008, 32, "uniform"),
+                                        (200, 9000, 20, "lowrank"), (256, 64, 16, "uniform"),
+                                        (130, 777 * 8, 12, "lowrank"), (256, 1 << 18, 16, "uniform")])
+def test_mu_fp32_split_tensor_core_form(ntt, m, n, r, kind):
+    """FP32 X split once into bf16(X) + bf16(X - bf16(X)) on the BF16 tensor-core
+    pass (route "tc"): iterates within the FP32 bound of the FP64 oracle on the
+    unsplit X after 10 updates, the engine reported, and a bitwise repeat."""
+    X = _x_matrix(kind, m, n, 17 + m)
+    W0 = synth.uniform_matrix((m, r), 18)
+    H0 = synth.uniform_matrix((r, n), 19)
+    eng = []
+    Wg, Hg, og = _run_gpu_mu(ntt, X, W0, H0, 10, route="tc", engine=eng)
+    assert eng == ["tc_split"]
+    Wg2, Hg2, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="tc")
+    assert np.array_equal(Wg, Wg2) and np.array_equal(Hg, Hg2)
+    Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
+    assert _fro_rel(Wg, Wo) <= REL_ITERATE, _fro_rel(Wg, Wo)
+    assert _fro_rel(Hg, Ho) <= REL_ITERATE, _fro_rel(Hg, Ho)
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    assert np.allclose(og, tr, rtol=2e-3, atol=1e-6 * float(np.sum(X.astype(np.float64) ** 2)))
+
+
+def test_mu_fp32_split_form_full_stage2_shape_sampled(ntt):
+    """The 32^6 job's stage-2 shape (256 x 1,048,576, r = 16) on the split
+    tensor-core form, one iteration: H on sampled columns, W from the oracle's
+    FP64 P = X H^T and Q = H H^T over all columns."""
+    m, n, r = 256, 1 << 20, 16
+    rng = np.random.Generator(np.random.PCG64(51))
+    X = rng.random((m, n), dtype=np.float32)
+    W0 = synth.uniform_matrix((m, r), 52)
+    H0 = synth.uniform_matrix((r, n), 53)
+    Wd = torch.from_numpy(W0).cuda()
+    Hd = torch.from_numpy(H0).cuda()
+    eng = []
+    ntt.nmf_mu_step(torch.from_numpy(X).cuda(), Wd, Hd, 1, route="tc", engine=eng)
+    torch.cuda.synchronize()
+    assert eng == ["tc_split"]
+    Hg = Hd.cpu().numpy()
+    G = W0.astype(np.float64).T @ W0.astype(np.float64)
+    P = np.zeros((m, r))
+    Q = np.zeros((r, r))
+    sample = np.sort(rng.choice(n, size=2048, replace=False))
+    chunk = 1 << 17
+    for c0 in range(0, n, chunk):
+        Xc = X[:, c0:c0 + chunk].astype(np.float64)
+        H0c = H0[:, c0:c0 + chunk].astype(np.float64)
+        H1c = np.maximum(0.0, H0c * (W0.T @ Xc) / (G @ H0c + 1e-12))
+        P += Xc @ H1c.T
+        Q += H1c @ H1c.T
+        sel = sample[(sample >= c0) & (sample < c0 + chunk)]
+        assert np.allclose(Hg[:, sel], H1c[:, sel - c0], rtol=2e-5, atol=1e-7 * H1c.max())
+    W1 = np.maximum(0.0, W0 * P / (W0 @ Q + 1e-12))
+    assert _fro_rel(Wd.cpu().numpy(), W1) <= REL_ITERATE
+
+
+def test_plan_stage2_runs_on_split_form(ntt):
+    """The 32^6 recipe at 16^6: its 128-row, rank-16 second stage runs on the
+    split tensor-core form by default and the cores match the FMA-only route."""
+    c = synth.CONFIGS["c2_32x6"]
+    dims = (16,) * 6
+    A, _ = synth.tt_tensor(dims, c["ranks"], c["core_dist"], c["noise"], c["data_seed"])
+    cores_a, stats_a, *_ = _decompose(ntt, A, c["ranks"], 10, c["init_seed"])
+    assert stats_a["stages"][1]["engine"] == "tc_split"
+    cores_f, stats_f, *_ = _decompose(ntt, A, c["ranks"], 10, c["init_seed"], route="fma")
+    assert stats_f["stages"][1]["engine"] != "tc_split"
+    for k, (a, b) in enumerate(zip(cores_a, cores_f)):
+        assert _fro_rel(a, b) <= 1e-4 * (k + 1), f"core {k}: {_fro_rel(a, b):.2e}"
