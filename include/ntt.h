@@ -246,7 +246,10 @@ ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes);
 /* `iters` BCD iterations on the m x n FP32 X (device), W (m x r) and H
  * (r x n) device FP32: initial factors in, the last accepted iterate out.
  * obj_dev (nullable): `iters` doubles, obj_dev[t] = the last accepted
- * objective after iteration t (FP64, Gram form).  ws: device,
+ * objective after iteration t.  The objective of each new iterate is the
+ * direct residual 1/2||X - W H||^2 that the pass sums over the tiles it holds
+ * (FP32 within a tile, FP64 across tiles), so the acceptance test sees no
+ * cancellation.  ws: device,
  * nmf_bcd_workspace_size bytes, 256-byte aligned (overwritten). */
 ntt_status nmf_bcd_step(int64_t m, int64_t n, int r, const float* X, float* W, float* H, int iters,
                         double* obj_dev, void* ws, void* stream);

@@ -4,7 +4,8 @@
 //
 //   W_new = max(0, W_m - (W_m Q - P) / L_w),   L_w = ||Q||_2,  P = X H^T, Q = H H^T
 //   H_new = max(0, H_m - (G H_m - W_new^T X) / L_h),  G = W_new^T W_new, L_h = ||G||_2
-//   f     = 1/2 ||X - W_new H_new||^2  (FP64, Gram form from P, Q of H_new)
+//   f     = 1/2 ||X - W_new H_new||^2  (the pass's direct residual of each tile
+//           it holds, FP64 across tiles: no extra read of X)
 //   f >= f_accepted: reject -- the next steps start from the accepted iterate
 //   otherwise accept; t' = (1 + sqrt(1 + 4 t^2)) / 2, w = (t - 1) / t',
 //   w_W = min(w, delta sqrt(L_w,prev / L_w)), w_H likewise, and
@@ -33,7 +34,7 @@ namespace ntt {
 #define NTT_DECL_BCD(MP)                                                                                   \
   cudaError_t launch_pass_bcd_f32_m##MP(int R, const MuShape& s, const MuDev& d, const CUtensorMap& mx,    \
                                          const HMaps3& mh, float* const* Hb, const BcdState* st_dev,        \
-                                         int init, cudaStream_t st);
+                                         int init, double* res_part, cudaStream_t st);
 NTT_DECL_BCD(16)
 NTT_DECL_BCD(32)
 NTT_DECL_BCD(64)
@@ -56,6 +57,7 @@ constexpr int kSquarings = 20;
 
 struct BcdCombineParams {
   const float* part;   // grid x E partials of [P ; Q] of H_new
+  const double* res_part;   // grid: ||X - W_new H_new||^2 over each pass CTA's tiles
   int nb;              // pass CTAs
   int MP, R, m, r;
   float* red;          // E: reduced [P ; Q] (FP32)
@@ -203,32 +205,20 @@ __global__ void __launch_bounds__(kAuxThreads) bcd_combine_kernel(const BcdCombi
     }
     for (int e = tid; e < E; e += blockDim.x) p.pacc[e] = red_s[e];
   } else {
-    // objective of (W_new, H_new): 1/2 (||X||^2 - 2 <W_new, P> + <G, Q>), FP64
-    double a = 0.0, b = 0.0;
-    for (int i = tid; i < m; i += blockDim.x)
-      for (int k = 0; k < r; ++k) a += (double)__ldcg(&p.Wn[i * r + k]) * (double)red_s[i * R + k];
-    for (int kl = tid; kl < r * r; kl += blockDim.x) {
-      const int k = kl / r, l = kl % r;
-      b += (double)Gs[k * R + l] * (double)red_s[(MP + k) * R + l];
-    }
+    // objective of (W_new, H_new): 1/2 ||X - W_new H_new||^2 from the pass's
+    // direct per-CTA residuals (FP32 within a tile, FP64 across), summed in a
+    // fixed order -- the value Algorithm 3's test compares; the expanded Gram
+    // form would lose about 1e-7 ||X||^2 to cancellation near convergence
+    if (tid < 32) {
+      double v = 0.0;
+      for (int b2 = tid; b2 < p.nb; b2 += 32) v += __ldcg(&p.res_part[b2]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int nw = blockDim.x / 32;
-    if ((tid & 31) == 0) {
-      dsh[tid / 32] = a;
-      dsh[nw + tid / 32] = b;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (tid == 0) dsh[0] = v;
     }
     __syncthreads();
     if (tid == 0) {
-      double As = 0.0, Bs = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        As += dsh[w];
-        Bs += dsh[nw + w];
-      }
-      const double f = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
+      const double f = 0.5 * dsh[0];
       const int acc = f < st->obj ? 1 : 0;
       s_acc = acc;
       if (acc) {
@@ -361,6 +351,7 @@ BcdWs bcd_ws_layout(const MuShape& s) {
   w.H1 = take((size_t)s.r * s.n * 4);
   w.H2 = take((size_t)s.r * s.n * 4);
   w.norms = take(4 * sizeof(double));
+  w.respart = take((size_t)kMaxPassCtas * sizeof(double));
   w.bytes = off;
   return w;
 }
@@ -386,6 +377,7 @@ ntt_status run_bcd_iters(const MuShape& shp, const MuDev& dev, const BcdWs& L, c
   BcdState* state = reinterpret_cast<BcdState*>(bws + L.state);
   float* Wn = reinterpret_cast<float*>(bws + L.Wn);
   double* norms = reinterpret_cast<double*>(bws + L.norms);
+  double* respart = reinterpret_cast<double*>(bws + L.respart);
   // Algorithm 3's normalisation of the initial factors, the state reset
   NTT_TRY_I(resid_into(dev.X, 0, nullptr, nullptr, s.m, s.n, 0, 0, 1.0, norms, nullptr, dev.part64, dev.ticket + 1, st));
   NTT_TRY_I(resid_into(dev.W, 0, nullptr, nullptr, s.m, s.r, 0, 0, 1.0, norms + 1, nullptr, dev.part64, dev.ticket + 1, st));
@@ -401,7 +393,7 @@ ntt_status run_bcd_iters(const MuShape& shp, const MuDev& dev, const BcdWs& L, c
     dp.W = init ? dev.W : Wn;
 #define NTT_CASE(MPV) \
   case MPV:           \
-    return launch_pass_bcd_f32_m##MPV(s.R, s, dp, mx, mh, Hb, state, init, st);
+    return launch_pass_bcd_f32_m##MPV(s.R, s, dp, mx, mh, Hb, state, init, respart, st);
     switch (s.MP) {
       NTT_CASE(16)
       NTT_CASE(32)
@@ -427,6 +419,7 @@ ntt_status run_bcd_iters(const MuShape& shp, const MuDev& dev, const BcdWs& L, c
   auto combine = [&](int init, int t) -> cudaError_t {
     BcdCombineParams c;
     c.part = dev.part;
+    c.res_part = respart;
     c.nb = s.grid;
     c.MP = s.MP;
     c.R = s.R;

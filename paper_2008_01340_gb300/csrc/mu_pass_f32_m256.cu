@@ -24,11 +24,11 @@ bool info_pass_f32_m256(int R, int* T, size_t* smem) {
 
 cudaError_t launch_pass_bcd_f32_m256(int R, const MuShape& s, const MuDev& d, const CUtensorMap& mx,
                                      const HMaps3& mh, float* const* Hb, const BcdState* st_dev, int init,
-                                     cudaStream_t st) {
+                                     double* res_part, cudaStream_t st) {
   switch (R) {
-    case 8: return launch_pass_bcd_cfg<PassCfg<256, 8, false, true>>(s, d, mx, mh, Hb, st_dev, init, st);
-    case 16: return launch_pass_bcd_cfg<PassCfg<256, 16, false, true>>(s, d, mx, mh, Hb, st_dev, init, st);
-    case 32: return launch_pass_bcd_cfg<PassCfg<256, 32, false, true>>(s, d, mx, mh, Hb, st_dev, init, st);
+    case 8: return launch_pass_bcd_cfg<PassCfg<256, 8, false, true>>(s, d, mx, mh, Hb, st_dev, init, res_part, st);
+    case 16: return launch_pass_bcd_cfg<PassCfg<256, 16, false, true>>(s, d, mx, mh, Hb, st_dev, init, res_part, st);
+    case 32: return launch_pass_bcd_cfg<PassCfg<256, 32, false, true>>(s, d, mx, mh, Hb, st_dev, init, res_part, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -144,6 +144,7 @@ struct PassParams {
   float* Hb[3];              // the three H buffers (cooperative loader / stores)
   const BcdState* bcd;       // rotation, w_h, L_h
   int bcd_init;              // accumulate P, Q of the accepted H only
+  double* res_part;          // BCD: per CTA, sum over its tiles of ||x_c - W h_new_c||^2
 };
 
 
@@ -230,6 +231,7 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
 #pragma unroll
       for (int e = 0; e < NACC; ++e) accB[i][k][e] = 0.0f;
 
+  double res_acc = 0.0;   // BCD: this thread's share of the direct residual
   int consumed = 0;
   int cur = 0;  // H_new buffer of this tile
   for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++consumed, cur ^= 1) {
@@ -403,6 +405,25 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
       tma_store_2d(&tmHs, smem_u32(Hn), (int)col0, 0);
       bulk_commit();
     }
+    if constexpr (C::BCD) {
+      // direct squared residual of (W, H_new) on this tile: the objective the
+      // step's acceptance test needs, without the cancellation of the Gram form
+      if (!p.bcd_init) {
+        float acc = 0.0f;
+        for (int idx = tid; idx < MP * T; idx += NT) {
+          const int i = idx / T, c = idx % T;
+          float v;
+          if constexpr (C::BF16)
+            v = __bfloat162float(Xs[i * T + c]);
+          else
+            v = Xs[i * T + c];
+#pragma unroll
+          for (int k = 0; k < R; ++k) v = fmaf(-Ws[i * R + k], Hn[k * T + c], v);
+          acc = fmaf(v, v, acc);
+        }
+        res_acc += (double)acc;
+      }
+    }
 
     // ---------------- phase B: [P ; Q] += [X_tile ; H_new] H_new^T
     {
@@ -469,6 +490,22 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
   }
   if (tma && tid == 0) bulk_wait<0>();   // H stores complete before smem is reused
   __syncthreads();
+  if constexpr (C::BCD) {
+    if (!p.bcd_init) {
+      // CTA sum of the residual shares: warp butterflies, then warps in order
+      __shared__ double s_res[NT / 32];
+      double v = res_acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) s_res[tid / 32] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += s_res[w];
+        p.res_part[blockIdx.x] = t;
+      }
+    }
+  }
 
   // ---------------- CTA reduction of phase-B accumulators over column groups
   float* red = reinterpret_cast<float*>(smem);
@@ -512,7 +549,8 @@ mu_pass_bcd_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 // the same (TMA mode); init: P, Q of the accepted H only.
 template <class C>
 cudaError_t launch_pass_bcd_cfg(const MuShape& s, const MuDev& d, const CUtensorMap& mx, const HMaps3& mh,
-                                float* const* Hb, const BcdState* st_dev, int init, cudaStream_t st) {
+                                float* const* Hb, const BcdState* st_dev, int init, double* res_part,
+                                cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(mu_pass_bcd_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -537,6 +575,7 @@ cudaError_t launch_pass_bcd_cfg(const MuShape& s, const MuDev& d, const CUtensor
   for (int i = 0; i < 3; ++i) p.Hb[i] = Hb[i];
   p.bcd = st_dev;
   p.bcd_init = init;
+  p.res_part = res_part;
   mu_pass_bcd_kernel<C><<<s.grid, kPassThreads, C::SMEM, st>>>(mx, mh, p);
   return cudaGetLastError();
 }
@@ -568,6 +607,7 @@ cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const C
   p.Hb[0] = p.Hb[1] = p.Hb[2] = d.H;
   p.bcd = nullptr;
   p.bcd_init = 0;
+  p.res_part = nullptr;
   mu_pass_kernel<C><<<s.grid, kPassThreads, C::SMEM, st>>>(mx, mh, p);
   return cudaGetLastError();
 }

@@ -322,7 +322,7 @@ constexpr double kBcdDelta = 0.9999;   // delta of Algorithm 3's extrapolation w
 // Scratch of a BCD solve (after the nmf_mu_step scratch): state, W_new,
 // accepted [P ; Q], the two extra H buffers, norms.
 struct BcdWs {
-  size_t state = 0, Wn = 0, pacc = 0, H1 = 0, H2 = 0, norms = 0, bytes = 0;
+  size_t state = 0, Wn = 0, pacc = 0, H1 = 0, H2 = 0, norms = 0, respart = 0, bytes = 0;
 };
 
 // Device pointers of one NMF.
