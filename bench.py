@@ -234,7 +234,13 @@ def run_stage1_small(args):
     from paper_2008_01340_gb300 import _build
 
     _build.build()
-    if args.case == "tcb_small":
+    route = "auto"
+    if args.case == "tcs_small":
+        # stage-2 shape of the 32^6 job at 2^21 columns (FP32 X): the split tensor-core form
+        m, n, r = 256, 1 << 21, 16
+        X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
+        route = "tc"
+    elif args.case == "tcb_small":
         # stage-2 shape of the precision form on BF16 X: the tensor-core pass
         m, n, r = 256, 1 << 21, 32
         X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).to(torch.bfloat16).cuda()
@@ -251,9 +257,10 @@ def run_stage1_small(args):
         ws = ntt.empty_workspace(ntt.nmf_mu_many_workspace_size([(m, n, r)]))
         run = lambda k: ntt.nmf_mu_many([X], [W], [H], k, workspace=ws)
     else:
-        ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r, "bf16" if X.dtype == torch.bfloat16 else "f32"))
+        ws = ntt.empty_workspace(ntt.nmf_mu_workspace_size(m, n, r, "bf16" if X.dtype == torch.bfloat16 else "f32",
+                                                           route))
         obj = torch.zeros(max(args.steps, args.warmup, 1), dtype=torch.float64, device="cuda")
-        run = lambda k: ntt.nmf_mu_step(X, W, H, k, 1e-12, obj, workspace=ws)
+        run = lambda k: ntt.nmf_mu_step(X, W, H, k, 1e-12, obj, workspace=ws, route=route)
     for _ in range(args.warmup):
         run(1)
     torch.cuda.synchronize()
@@ -456,14 +463,14 @@ def main():
                          "c5_serving: 1000 Poisson requests through the serving form")
     ap.add_argument("--engine", default="pass", choices=["pass", "group"],
                     help="stage1_small: single-problem pass or grouped engine")
-    ap.add_argument("--case", default="full", choices=["full", "stage1_small", "tcb_small", "stage3"],
+    ap.add_argument("--case", default="full", choices=["full", "stage1_small", "tcb_small", "tcs_small", "stage3"],
                     help="stage1_small: MU iterations of the stage-1 shape on 32 x 4194304 "
                          "(512 MB, larger than L2) for profiler captures")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
-    if args.case in ("stage1_small", "tcb_small", "stage3"):
+    if args.case in ("stage1_small", "tcb_small", "tcs_small", "stage3"):
         return run_stage1_small(args)
     if args.workload == "c4_batched":
         return run_batched(args)

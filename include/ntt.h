@@ -399,11 +399,37 @@ ntt_status ntt_batch_offsets(ntt_batch b, int64_t* input_off, int64_t* core_off)
 
 /* Decompose all instances.  A: device packed tensors (C order each); cores:
  * device packed cores (core k of instance i is r_k x n_{k+1} x r_{k+1});
- * workspace: device, ntt_batch_sizes bytes, 256-byte aligned.  Returns after
- * the stream has finished the work (synchronises `stream`), with the device
- * status word. */
+ * workspace: device, ntt_batch_sizes bytes, 256-byte aligned.  The whole
+ * batch -- every stage's small NMFs, grouped engine launches, residuals and
+ * selections -- is one cached CUDA graph per (A, cores, workspace) triple (two
+ * triples are kept; replacing one first waits for its last launch), launched
+ * on `stream`; the call returns without waiting.  The graph holds kernel nodes
+ * only: its tables live in the batch's mapped pinned host memory, written once
+ * at capture, and are uploaded by kernels on every launch.  The device status
+ * word is the first word of the workspace (ntt_status_of_workspace after a
+ * stream synchronisation). */
 ntt_status ntt_decompose_batched(ntt_batch b, const float* A, float* cores, void* workspace,
                                  void* stream);
+
+/* Autotuner of the batched form: for every stage with grouped (large)
+ * unfoldings, the CTA split of the grouped engine -- how many CTAs problems
+ * sharing a launch get: 1/split of one wave's tile share each, split in
+ * {1, 2, 4, 8} -- is taken from `cache_path` when that file holds an entry
+ * for the stage's signature (a hash of its problem shapes and the SM count),
+ * else timed: the batch runs eagerly on the caller's buffers once per
+ * candidate with probe_iters iterations per stage (CUDA events around each
+ * stage's grouped iterations), the fastest split is kept and appended to
+ * cache_path (nullable: no file).  Synchronises `stream`; the outputs of the
+ * probe runs are overwritten by the next ntt_decompose_batched.  Cached
+ * graphs are dropped and recaptured with the chosen splits.  The workspace
+ * size does not depend on the choice. */
+ntt_status ntt_batch_tune(ntt_batch b, const float* A, float* cores, void* workspace, void* stream,
+                          int probe_iters, const char* cache_path);
+
+/* The split of each stage (max_stages entries; 0 for stages without grouped
+ * work) and how many stages took theirs from the cache file / were timed by
+ * the last ntt_batch_tune. */
+ntt_status ntt_batch_get_tuning(ntt_batch b, int max_stages, int* split, int* from_cache, int* timed);
 
 ntt_status ntt_batch_destroy(ntt_batch b);
 

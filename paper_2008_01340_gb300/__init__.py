@@ -58,7 +58,7 @@ EXPORTS = (
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
-    "ntt_batch_destroy", "nmf_mu_many_workspace_size", "nmf_mu_many",
+    "ntt_batch_destroy", "ntt_batch_tune", "ntt_batch_get_tuning", "nmf_mu_many_workspace_size", "nmf_mu_many",
     "ntt_server_create", "ntt_server_job_footprint", "ntt_server_submit", "ntt_server_poll",
     "ntt_server_wait", "ntt_server_get_stats", "ntt_server_destroy",
 )
@@ -187,6 +187,9 @@ def lib():
     L.ntt_batch_offsets.argtypes = [vp, p64, p64]
     L.ntt_decompose_batched.argtypes = [vp, vp, vp, vp, vp]
     L.ntt_batch_destroy.argtypes = [vp]
+    L.ntt_batch_tune.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_char_p]
+    L.ntt_batch_get_tuning.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]
     L.ntt_compression_ratio.restype = ctypes.c_double
     L.ntt_compression_ratio.argtypes = [i32, p64, p64]
     for name in EXPORTS:
@@ -624,8 +627,30 @@ def ntt_batch_create(instances, iters, restarts, eps_mu=1e-12, seed=0):
     return Batch(instances, iters, restarts, eps_mu, seed)
 
 
+def ntt_batch_tune(batch, A_packed, cores_packed, workspace, probe_iters=10, cache_path=None, stream=None):
+    """Autotune the grouped engine's CTA split per stage (include/ntt.h); returns
+    dict(split=[per stage], from_cache=..., timed=...)."""
+    import torch
+    path = cache_path.encode() if cache_path else None
+    _check(lib().ntt_batch_tune(batch.handle, _dev_ptr(A_packed, torch.float32, "A"),
+                                _dev_ptr(cores_packed, torch.float32, "cores"),
+                                _dev_ptr(workspace, None, "workspace"), _stream_ptr(stream), int(probe_iters), path),
+           "ntt_batch_tune")
+    return ntt_batch_get_tuning(batch)
+
+
+def ntt_batch_get_tuning(batch):
+    nst = max(len(d) for d, _ in batch.instances) - 1
+    split = (ctypes.c_int * max(1, nst))()
+    fc, tm = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ntt_batch_get_tuning(batch.handle, nst, split, ctypes.byref(fc), ctypes.byref(tm)),
+           "ntt_batch_get_tuning")
+    return {"split": list(split)[:nst], "from_cache": fc.value, "timed": tm.value}
+
+
 def ntt_decompose_batched(batch, A_packed, cores_packed, workspace, stream=None):
-    """A_packed / cores_packed: CUDA float32 tensors laid out by batch.input_off / core_off."""
+    """A_packed / cores_packed: CUDA float32 tensors laid out by batch.input_off / core_off.
+    Asynchronous (one cached CUDA graph); the status word is ntt_status_of_workspace(workspace)."""
     import torch
     _check(lib().ntt_decompose_batched(batch.handle, _dev_ptr(A_packed, torch.float32, "A"),
                                        _dev_ptr(cores_packed, torch.float32, "cores"),

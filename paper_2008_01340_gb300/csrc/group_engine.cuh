@@ -122,9 +122,10 @@ struct GroupPtrs {
 // starts at.  fixed_split: every problem's CTA count (and so its reduction
 // order) depends on its own shape only, not on the other problems.
 // own_scratch: G, red, part and Y of every problem live in the plan's scratch;
-// otherwise GroupPtrs::scratch supplies them.
+// otherwise GroupPtrs::scratch supplies them.  split_div: problems sharing a
+// launch get CTAs of 1/split_div of one wave's tile share each (1, 2, 4, 8).
 ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, bool fixed_split,
-                      bool own_scratch, GroupPlan* out);
+                      bool own_scratch, GroupPlan* out, int split_div = 4);
 
 // Engine scratch of one problem under fixed_split (bytes, 256-byte multiple).
 size_t group_problem_scratch(const GroupShape& shape, int sms);

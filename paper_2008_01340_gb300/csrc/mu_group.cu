@@ -266,7 +266,7 @@ size_t group_problem_scratch(const GroupShape& sh, int sms) {
 }
 
 ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t base, bool fixed_split,
-                      bool own_scratch, GroupPlan* out) {
+                      bool own_scratch, GroupPlan* out, int split_div) {
   GroupPlan& pl = *out;
   pl = GroupPlan();
   pl.own_scratch = own_scratch;
@@ -325,15 +325,15 @@ ntt_status group_plan(const std::vector<GroupShape>& shapes, int sms, size_t bas
     for (const auto& e : pl.entries)
       if (e.bucket == bk && !pl.probs[e.p].S) ps.push_back(e.p);
     if (ps.empty()) continue;
-    // per-CTA tile count of a quarter of one wave's share: big problems get
-    // many CTAs, small ones one CTA each, and CTAs that finish early leave
-    // their SM to the rest (the tail is about a quarter of a wave's work)
+    // per-CTA tile count of 1/split_div of one wave's share (4 by default, a
+    // quarter): big problems get many CTAs, small ones one CTA each, and CTAs
+    // that finish early leave their SM to the rest
     const int64_t wave = (int64_t)std::max(1, sms) * std::max(1, group_ctas_per_sm(MP, R, xb != 0));
     int64_t tiles = 0;
     for (int p : ps) tiles += (pl.probs[p].n + T - 1) / T;
     // one problem alone: equal CTAs, one whole wave; several: a quarter wave's share each
     const int64_t per = ps.size() == 1 ? std::max<int64_t>(1, (tiles + wave - 1) / wave)
-                                       : std::max<int64_t>(1, (tiles + 4 * wave - 1) / (4 * wave));
+                                       : std::max<int64_t>(1, (tiles + split_div * wave - 1) / (split_div * wave));
     for (int p : ps) pl.probs[p].S = (int)(((pl.probs[p].n + T - 1) / T + per - 1) / per);
   }
   // CTA ranges of the entries inside their bucket launches

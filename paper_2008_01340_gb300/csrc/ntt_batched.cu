@@ -22,6 +22,7 @@
 //     next unfolding, for all instances of the stage at once.
 // The small-unfolding launch runs on a second stream, beside the large work.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -350,6 +351,12 @@ struct ntt_batch_s {
     size_t off_init, off_split, off_res, off_resmap, off_respart, off_sel;   // bytes, device tables
     size_t tab_bytes = 0;                          // bytes of those tables (one copy)
     size_t host_off = 0;                           // pinned host offset of this stage
+    size_t host_bytes = 0;                         // bytes of its tables + the engine's (uploaded per call)
+    std::vector<GroupShape> shapes;                // grouped problems of the stage
+    size_t gp_base = 0;                            // scratch offset of the engine plan
+    int split = 4;                                 // CTA split of the engine (autotuned)
+    uint64_t sig = 0;                              // signature of the stage's problem shapes
+    bool tuned = false;
     int sel_grid = 1;
     // small tasks and their select jobs
     size_t task_base = 0, ntasks = 0, job_base = 0, njobs = 0, small_floats = 0;
@@ -364,19 +371,51 @@ struct ntt_batch_s {
   size_t off_status, off_obj, off_tasks, off_jobs, off_small, off_x, off_stage, bytes;
   size_t n_tasks = 0, n_jobs = 0;
   int max_stages = 0;
-  // pinned host tables: small tasks, small select jobs, per-stage tables
-  char* h_pinned = nullptr;
+  // host tables (small tasks, small select jobs, per-stage tables): h_bytes per
+  // copy; every cached graph owns a mapped pinned copy written once at capture
+  // and uploaded by kernel nodes on each launch
   size_t h_bytes = 0, h_tasks_off = 0, h_jobs_off = 0;
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tables = nullptr;
-  bool tables_pending = false;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    const float* A = nullptr;
+    float* cores = nullptr;
+    void* ws = nullptr;
+    char* h = nullptr;        // host address of the tables
+    char* hdev = nullptr;     // device address of the same memory
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+  };
+  Graph graphs[2];
+  int victim = 0;
+  cudaStream_t cap = nullptr;
+  char* h_tune = nullptr;     // tables of the autotuner's eager runs
+  char* h_tune_dev = nullptr;
+  int tuned_from_cache = 0;   // stages whose split came from the cache file
+  int tuned_timed = 0;        // stages whose split was timed
+  void drop_graphs() {
+    for (auto& g : graphs) {
+      if (g.launched) cudaEventSynchronize(g.done);
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      g.launched = false;
+      g.A = nullptr;
+      g.cores = nullptr;
+      g.ws = nullptr;
+    }
+  }
   ~ntt_batch_s() {
-    if (ev_tables && tables_pending) cudaEventSynchronize(ev_tables);
+    drop_graphs();
+    for (auto& g : graphs) {
+      if (g.done) cudaEventDestroy(g.done);
+      if (g.h) cudaFreeHost(g.h);
+    }
+    if (h_tune) cudaFreeHost(h_tune);
+    if (cap) cudaStreamDestroy(cap);
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
-    if (ev_tables) cudaEventDestroy(ev_tables);
-    if (h_pinned) cudaFreeHost(h_pinned);
     cudaGetLastError();
   }
 };
@@ -394,13 +433,13 @@ float* stage_next(ntt_batch b, int i, int s, float* cores, char* ws) {
                         : reinterpret_cast<float*>(ws + b->off_x) + I.x_off[s & 1];
 }
 
-// Host tables of stage s's small tasks and their selection jobs.
-void fill_small_tables(ntt_batch b, int s, const float* A, float* cores, char* ws) {
+// Host tables of stage s's small tasks and their selection jobs (into h).
+void fill_small_tables(ntt_batch b, int s, const float* A, float* cores, char* ws, char* h) {
   const auto& S = b->stage[s];
   const int R = b->restarts;
   double* obj = reinterpret_cast<double*>(ws + b->off_obj);
-  SmallTask* tasks = reinterpret_cast<SmallTask*>(b->h_pinned + b->h_tasks_off);
-  SelectJob* jobs = reinterpret_cast<SelectJob*>(b->h_pinned + b->h_jobs_off);
+  SmallTask* tasks = reinterpret_cast<SmallTask*>(h + b->h_tasks_off);
+  SelectJob* jobs = reinterpret_cast<SelectJob*>(h + b->h_jobs_off);
   size_t t = S.task_base, jn = S.job_base, off = 0;
   for (int i = 0; i < (int)b->inst.size(); ++i) {
     auto& I = b->inst[i];
@@ -441,14 +480,16 @@ void fill_small_tables(ntt_batch b, int s, const float* A, float* cores, char* w
 }
 
 // Large unfoldings of stage s: init tables, grouped iterations, split,
-// residuals, selection -- all on stream st.
+// residuals, selection -- all on stream st.  hb / hbdev: host and device
+// addresses of the mapped pinned tables; ev (nullable): two events around the
+// grouped iterations.
 ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores, char* ws, cudaStream_t st,
-                               int sms) {
+                               int sms, char* hb, const char* hbdev, int iters, cudaEvent_t* ev) {
   auto& S = b->stage[s];
   if (S.large.empty()) return NTT_OK;
   const int R = b->restarts;
   double* obj = reinterpret_cast<double*>(ws + b->off_obj);
-  char* h = b->h_pinned + S.host_off;
+  char* h = hb + S.host_off;
   InitJob* hi = reinterpret_cast<InitJob*>(h + (S.off_init - b->off_stage));
   SplitJob* hs = reinterpret_cast<SplitJob*>(h + (S.off_split - b->off_stage));
   ResJob* hr = reinterpret_cast<ResJob*>(h + (S.off_res - b->off_stage));
@@ -525,8 +566,10 @@ ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores,
     ptrs[p].W = Wg;
     ptrs[p].scratch = nullptr;
   }
-  char* d = ws + b->off_stage;
-  if (cudaMemcpyAsync(d, h, S.tab_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return NTT_ERR_CUDA;
+  // the engine's tables follow the stage's own in the host block: one upload
+  group_fill_tables(S.gp, ptrs.data(), ws, h + (S.gp.off_tables - b->off_stage));
+  if (launch_copy_words(ws + b->off_stage, hbdev + S.host_off, S.host_bytes, st) != cudaSuccess)
+    return NTT_ERR_CUDA;
   const InitJob* di = reinterpret_cast<const InitJob*>(ws + S.off_init);
   const SplitJob* dsp = reinterpret_cast<const SplitJob*>(ws + S.off_split);
   const ResJob* dr = reinterpret_cast<const ResJob*>(ws + S.off_res);
@@ -535,7 +578,9 @@ ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores,
   const SelectJob* dsel = reinterpret_cast<const SelectJob*>(ws + S.off_sel);
   init_groups_kernel<<<dim3(sms, np), 256, 0, st>>>(di);
   if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
-  NTT_TRY_B(group_run(S.gp, ptrs.data(), ws, h + (S.gp.off_tables - b->off_stage), b->iters, b->eps, st));
+  if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return NTT_ERR_CUDA;
+  NTT_TRY_B(group_launch(S.gp, ws, ws + S.gp.off_tables, iters, b->eps, st));
+  if (ev && cudaEventRecord(ev[1], st) != cudaSuccess) return NTT_ERR_CUDA;
   split_groups_kernel<<<dim3(8, np), 256, 0, st>>>(dsp);
   resid_groups_kernel<<<S.res_blocks, 256, S.res_smem, st>>>(dr, drm, drp);
   resid_reduce_kernel<<<(S.nres + 127) / 128, 128, 0, st>>>(dr, S.nres, drp);
@@ -543,31 +588,34 @@ ntt_status enqueue_large_stage(ntt_batch b, int s, const float* A, float* cores,
   return cudaGetLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
-ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cudaStream_t st) {
-  int* status = reinterpret_cast<int*>(ws + b->off_status);
-  if (cudaMemsetAsync(status, 0, 64, st) != cudaSuccess) return NTT_ERR_CUDA;
-  if (!b->side) {
-    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_tables, cudaEventDisableTiming) != cudaSuccess)
-      return NTT_ERR_CUDA;
-    if (cudaFuncSetAttribute(small_nmf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmallSmemCap + 1024) != cudaSuccess ||
-        cudaFuncSetAttribute(resid_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             NTT_MAX_ROWS * NTT_MAX_RANK * 4) != cudaSuccess)
-      return NTT_ERR_CUDA;
-  }
-  // the pinned tables of an earlier call may still be in flight if that call failed early
-  if (b->tables_pending && cudaEventSynchronize(b->ev_tables) != cudaSuccess) return NTT_ERR_CUDA;
-  for (int s = 0; s < b->max_stages; ++s) fill_small_tables(b, s, A, cores, ws);
+ntt_status batch_setup(ntt_batch b) {
+  if (b->side) return NTT_OK;
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return NTT_ERR_CUDA;
+  if (cudaFuncSetAttribute(small_nmf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSmallSmemCap + 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(resid_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           NTT_MAX_ROWS * NTT_MAX_RANK * 4) != cudaSuccess)
+    return NTT_ERR_CUDA;
+  return NTT_OK;
+}
+
+// The whole batch on stream st (captured or eager): every stage's small tasks
+// on the side stream beside its large work, then the selections.  h / hdev:
+// the mapped pinned tables this enqueue writes and its kernels upload.
+// ev (nullable): 2 events per stage around the grouped iterations.
+ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cudaStream_t st, char* h,
+                         const char* hdev, int iters, cudaEvent_t* ev) {
+  if (launch_zero(ws + b->off_status, 64, st) != cudaSuccess) return NTT_ERR_CUDA;
+  NTT_TRY_B(batch_setup(b));
+  for (int s = 0; s < b->max_stages; ++s) fill_small_tables(b, s, A, cores, ws, h);
   SmallTask* dtasks = reinterpret_cast<SmallTask*>(ws + b->off_tasks);
   SelectJob* djobs = reinterpret_cast<SelectJob*>(ws + b->off_jobs);
-  if (b->n_tasks && cudaMemcpyAsync(dtasks, b->h_pinned + b->h_tasks_off, b->n_tasks * sizeof(SmallTask),
-                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (b->n_tasks && launch_copy_words(dtasks, hdev + b->h_tasks_off, b->n_tasks * sizeof(SmallTask), st) != cudaSuccess)
     return NTT_ERR_CUDA;
-  if (b->n_jobs && cudaMemcpyAsync(djobs, b->h_pinned + b->h_jobs_off, b->n_jobs * sizeof(SelectJob),
-                                   cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (b->n_jobs && launch_copy_words(djobs, hdev + b->h_jobs_off, b->n_jobs * sizeof(SelectJob), st) != cudaSuccess)
     return NTT_ERR_CUDA;
   const int sms = device_sms();
   for (int s = 0; s < b->max_stages; ++s) {
@@ -578,19 +626,34 @@ ntt_status enqueue_batch(ntt_batch b, const float* A, float* cores, char* ws, cu
         return NTT_ERR_CUDA;
       const int grid = (int)std::min<size_t>(S.ntasks, (size_t)sms * (S.small_smem > 110 * 1024 ? 1 : 2));
       small_nmf_kernel<<<grid, kSmallThreads, S.small_smem, b->side>>>(dtasks + S.task_base, (int)S.ntasks,
-                                                                        b->iters, b->eps);
+                                                                        iters, b->eps);
       if (cudaGetLastError() != cudaSuccess || cudaEventRecord(b->ev_join, b->side) != cudaSuccess)
         return NTT_ERR_CUDA;
     }
-    NTT_TRY_B(enqueue_large_stage(b, s, A, cores, ws, st, sms));
+    NTT_TRY_B(enqueue_large_stage(b, s, A, cores, ws, st, sms, h, hdev, iters, ev ? ev + 2 * s : nullptr));
     if (S.ntasks) {
       if (cudaStreamWaitEvent(st, b->ev_join, 0) != cudaSuccess) return NTT_ERR_CUDA;
       select_kernel<<<dim3(1, (unsigned)S.njobs), 256, 0, st>>>(djobs + S.job_base);
       if (cudaGetLastError() != cudaSuccess) return NTT_ERR_CUDA;
     }
   }
-  if (cudaEventRecord(b->ev_tables, st) != cudaSuccess) return NTT_ERR_CUDA;
-  b->tables_pending = true;
+  return NTT_OK;
+}
+
+ntt_status alloc_mapped_b(size_t bytes, char** host, char** dev) {
+  void* hp = nullptr;
+  void* dp = nullptr;
+  if (cudaHostAlloc(&hp, bytes, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return NTT_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(hp);
+    return NTT_ERR_CUDA;
+  }
+  *host = reinterpret_cast<char*>(hp);
+  *dev = reinterpret_cast<char*>(dp);
   return NTT_OK;
 }
 
@@ -751,13 +814,42 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
     S.off_resmap = stake((size_t)S.res_blocks * sizeof(int));
     S.off_sel = stake(S.large.size() * sizeof(SelectJob));
     S.tab_bytes = so - b->off_stage;
-    // the engine's own tables follow directly, so the host staging stays one block
-    if (group_plan(shapes, sms, so, false, true, &S.gp) != NTT_OK) {
+    // the engine's own tables follow directly, so the host staging stays one
+    // block; sized for every CTA split the autotuner may choose
+    S.shapes = shapes;
+    S.gp_base = so;
+    size_t gp_end = 0, host_bytes = 0;
+    for (int div : {1, 2, 4, 8}) {
+      GroupPlan g;
+      if (group_plan(shapes, sms, so, false, true, &g, div) != NTT_OK) {
+        delete b;
+        return NTT_ERR_UNSUPPORTED;
+      }
+      gp_end = std::max(gp_end, g.bytes);
+      host_bytes = std::max(host_bytes, align256(g.off_tables + g.table_bytes - b->off_stage));
+    }
+    if (group_plan(shapes, sms, so, false, true, &S.gp, S.split) != NTT_OK) {
       delete b;
       return NTT_ERR_UNSUPPORTED;
     }
-    so = S.gp.bytes;
-    const size_t host_bytes = align256(S.gp.off_tables + S.gp.table_bytes - b->off_stage);
+    // signature of the stage's grouped problems (FNV-1a over their shapes)
+    uint64_t sig = 1469598103934665603ULL;
+    auto mixin = [&](uint64_t v) {
+      for (int k = 0; k < 8; ++k) {
+        sig ^= (v >> (8 * k)) & 0xFF;
+        sig *= 1099511628211ULL;
+      }
+    };
+    mixin((uint64_t)sms);
+    for (const auto& sh : shapes) {
+      mixin((uint64_t)sh.n);
+      mixin((uint64_t)sh.m);
+      mixin((uint64_t)sh.re);
+      mixin((uint64_t)sh.blk);
+    }
+    S.sig = sig;
+    so = gp_end;
+    S.host_bytes = align256(S.gp.off_tables + S.gp.table_bytes - b->off_stage);
     S.off_respart = stake((size_t)S.res_blocks * sizeof(double));
     for (size_t li = 0; li < S.large.size(); ++li) {
       const auto& I = b->inst[S.large[li]];
@@ -772,16 +864,10 @@ ntt_status ntt_batch_create(int B, const int* d, const int64_t* dims, const int6
   }
   off = b->off_stage + stage_max;
   b->bytes = align256(off);
-  // ---- pinned host tables
+  // ---- host tables (allocated per cached graph, mapped pinned)
   b->h_tasks_off = host_total;
   b->h_jobs_off = align256(b->h_tasks_off + b->n_tasks * sizeof(SmallTask));
   b->h_bytes = align256(b->h_jobs_off + b->n_jobs * sizeof(SelectJob)) + 256;
-  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_pinned), b->h_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    b->h_pinned = nullptr;
-    delete b;
-    return NTT_ERR_OOM;
-  }
   *out = b;
   return NTT_OK;
 }
@@ -811,21 +897,175 @@ ntt_status ntt_decompose_batched(ntt_batch b, const float* A, float* cores, void
   if (!b || !A || !cores || !workspace) return NTT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return NTT_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const ntt_status e = enqueue_batch(b, A, cores, reinterpret_cast<char*>(workspace), st);
-  if (e != NTT_OK) {
-    // work already queued may still read the pinned tables: let it drain
-    cudaStreamSynchronize(st);
-    cudaGetLastError();
-    b->tables_pending = false;
-    return e;
+  char* ws = reinterpret_cast<char*>(workspace);
+  NTT_TRY_B(batch_setup(b));
+  ntt_batch_s::Graph* G = nullptr;
+  for (auto& g : b->graphs)
+    if (g.exec && g.A == A && g.cores == cores && g.ws == workspace) G = &g;
+  if (!G) {
+    G = &b->graphs[b->victim];
+    b->victim ^= 1;
+    // the entry's tables are rewritten by the capture: its last launch must be done
+    if (G->launched && cudaEventSynchronize(G->done) != cudaSuccess) return NTT_ERR_CUDA;
+    G->launched = false;
+    if (G->exec) {
+      cudaGraphExecDestroy(G->exec);
+      G->exec = nullptr;
+    }
+    if (!G->done && cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess) return NTT_ERR_CUDA;
+    if (!G->h) NTT_TRY_B(alloc_mapped_b(b->h_bytes, &G->h, &G->hdev));
+    if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return NTT_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NTT_ERR_CUDA;
+    const ntt_status e = enqueue_batch(b, A, cores, ws, b->cap, G->h, G->hdev, b->iters, nullptr);
+    const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+    if (e != NTT_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return e != NTT_OK ? e : NTT_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&G->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      G->exec = nullptr;
+      return NTT_ERR_CUDA;
+    }
+    G->A = A;
+    G->cores = cores;
+    G->ws = workspace;
   }
-  int status = 0;
-  if (cudaMemcpyAsync(&status, reinterpret_cast<char*>(workspace) + b->off_status, sizeof(int),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  if (cudaGraphLaunch(G->exec, st) != cudaSuccess || cudaEventRecord(G->done, st) != cudaSuccess) {
+    cudaGetLastError();
     return NTT_ERR_CUDA;
-  b->tables_pending = false;
-  return status == 0 ? NTT_OK : (ntt_status)status;
+  }
+  G->launched = true;
+  return NTT_OK;
+}
+
+namespace {
+
+bool read_tuning_cache(const char* path, uint64_t sig, int* split) {
+  if (!path || !path[0]) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char tag[32];
+  unsigned long long key = 0;
+  int val = 0;
+  bool found = false;
+  while (std::fscanf(f, "%31s %llx %d", tag, &key, &val) == 3)
+    if (std::strcmp(tag, "gsplit") == 0 && key == sig && (val == 1 || val == 2 || val == 4 || val == 8)) {
+      *split = val;   // the last entry for a signature wins
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void append_tuning_cache(const char* path, uint64_t sig, int split, float ms) {
+  if (!path || !path[0]) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "gsplit %016llx %d %.4f\n", (unsigned long long)sig, split, ms);
+  std::fclose(f);
+}
+
+}  // namespace
+
+ntt_status ntt_batch_tune(ntt_batch b, const float* A, float* cores, void* workspace, void* stream,
+                          int probe_iters, const char* cache_path) {
+  if (!b || !A || !cores || !workspace || probe_iters < 1) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  NTT_TRY_B(batch_setup(b));
+  const int sms = device_sms();
+  b->tuned_from_cache = 0;
+  b->tuned_timed = 0;
+  std::vector<int> todo;
+  for (int s = 0; s < b->max_stages; ++s) {
+    auto& S = b->stage[s];
+    if (S.large.empty()) continue;
+    int split = 0;
+    if (read_tuning_cache(cache_path, S.sig, &split)) {
+      S.split = split;
+      S.tuned = true;
+      ++b->tuned_from_cache;
+    } else {
+      todo.push_back(s);
+    }
+  }
+  // the cached graphs hold tables of the old splits
+  b->drop_graphs();
+  auto replan = [&](int s) -> ntt_status {
+    auto& S = b->stage[s];
+    if (group_plan(S.shapes, sms, S.gp_base, false, true, &S.gp, S.split) != NTT_OK) return NTT_ERR_UNSUPPORTED;
+    S.host_bytes = align256(S.gp.off_tables + S.gp.table_bytes - b->off_stage);
+    return NTT_OK;
+  };
+  for (int s = 0; s < b->max_stages; ++s)
+    if (!b->stage[s].large.empty()) NTT_TRY_B(replan(s));
+  if (todo.empty()) return NTT_OK;
+  if (!b->h_tune) NTT_TRY_B(alloc_mapped_b(b->h_bytes, &b->h_tune, &b->h_tune_dev));
+  std::vector<cudaEvent_t> ev(2 * b->max_stages, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return NTT_ERR_CUDA;
+  auto free_ev = [&]() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+  };
+  const int cands[4] = {1, 2, 4, 8};
+  std::vector<float> best(b->max_stages, 1e30f);
+  std::vector<int> best_split(b->max_stages, 4);
+  // eager runs of the whole batch with probe_iters iterations, every untuned
+  // stage on candidate c; the grouped iterations of each stage timed by events
+  for (int c : cands) {
+    for (int s : todo) {
+      b->stage[s].split = c;
+      const ntt_status e = replan(s);
+      if (e != NTT_OK) {
+        free_ev();
+        return e;
+      }
+    }
+    ntt_status e = enqueue_batch(b, A, cores, ws, st, b->h_tune, b->h_tune_dev, probe_iters, ev.data());
+    if (e == NTT_OK && cudaStreamSynchronize(st) != cudaSuccess) e = NTT_ERR_CUDA;
+    if (e != NTT_OK) {
+      free_ev();
+      return e;
+    }
+    for (int s : todo) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ev[2 * s], ev[2 * s + 1]) != cudaSuccess) {
+        free_ev();
+        return NTT_ERR_CUDA;
+      }
+      if (ms < best[s]) {
+        best[s] = ms;
+        best_split[s] = c;
+      }
+    }
+  }
+  free_ev();
+  for (int s : todo) {
+    auto& S = b->stage[s];
+    S.split = best_split[s];
+    S.tuned = true;
+    NTT_TRY_B(replan(s));
+    append_tuning_cache(cache_path, S.sig, S.split, best[s]);
+    ++b->tuned_timed;
+  }
+  return NTT_OK;
+}
+
+ntt_status ntt_batch_get_tuning(ntt_batch b, int max_stages, int* split, int* from_cache, int* timed) {
+  if (!b || max_stages < 0 || (max_stages > 0 && !split)) return NTT_ERR_INVALID_ARG;
+  for (int s = 0; s < max_stages; ++s)
+    split[s] = s < b->max_stages && !b->stage[s].large.empty() ? b->stage[s].split : 0;
+  if (from_cache) *from_cache = b->tuned_from_cache;
+  if (timed) *timed = b->tuned_timed;
+  return NTT_OK;
 }
 
 ntt_status ntt_batch_destroy(ntt_batch b) {

@@ -122,3 +122,47 @@ def test_batched_recipe_subsample_matches_oracle(ntt):
         ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
         eg, eo = oracle.rel_error(T, views[i]), oracle.rel_error(T, ref)
         assert abs(eg - eo) <= 1e-3, f"instance {i} {dims}: {eg} vs {eo}"
+
+
+def test_batched_graph_relaunch_and_autotune(ntt, tmp_path):
+    """The batched form as one cached graph: two launches on the same buffers
+    give bitwise the same cores; the autotuner picks a CTA split per stage
+    with grouped work, writes its cache file, a second batch of the same
+    shapes reads it instead of timing, and the tuned batch still matches the
+    oracle's final error."""
+    inst = synth.batched_instances(12, seed=41, n_range=(8, 11))
+    instances = [(i["dims"], i["ranks"]) for i in inst] + [INSTANCES[2]]
+    seed, restarts, iters = 5, 8, 40
+    b = ntt.ntt_batch_create(instances, iters, restarts, 1e-12, seed)
+    A = torch.zeros(b.input_floats, dtype=torch.float32)
+    tensors = []
+    for i, (dims, ranks) in enumerate(instances):
+        T, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=700 + i)
+        tensors.append(T)
+        A[b.input_off[i]:b.input_off[i] + T.size] = torch.from_numpy(T.ravel())
+    Ad = A.cuda()
+    ws = ntt.empty_workspace(b.workspace_bytes)
+    outs = []
+    for _ in range(2):
+        cores = torch.zeros(b.core_floats, dtype=torch.float32, device="cuda")
+        ntt.ntt_decompose_batched(b, Ad, cores, ws)
+        outs.append(cores)
+    torch.cuda.synchronize()
+    assert ntt.ntt_status_of_workspace(ws) == "NTT_OK"
+    assert torch.equal(outs[0], outs[1])
+    cache = str(tmp_path / "gsplit.txt")
+    cores = torch.zeros(b.core_floats, dtype=torch.float32, device="cuda")
+    t1 = ntt.ntt_batch_tune(b, Ad, cores, ws, probe_iters=5, cache_path=cache)
+    assert t1["timed"] >= 1 and t1["from_cache"] == 0
+    assert all(v in (0, 1, 2, 4, 8) for v in t1["split"]) and any(v > 0 for v in t1["split"])
+    lines = open(cache).read().split("\n")
+    assert sum(1 for ln in lines if ln.startswith("gsplit ")) == t1["timed"]
+    b2 = ntt.ntt_batch_create(instances, iters, restarts, 1e-12, seed)
+    t2 = ntt.ntt_batch_tune(b2, Ad, cores, ws, probe_iters=5, cache_path=cache)
+    assert t2["timed"] == 0 and t2["from_cache"] == t1["timed"] and t2["split"] == t1["split"]
+    ntt.ntt_decompose_batched(b2, Ad, cores, ws)
+    views = [[c.cpu().numpy() for c in lst] for lst in b2.core_views(cores)]
+    for i, ((dims, ranks), T) in enumerate(zip(instances, tensors)):
+        ref, _ = oracle.ntt_decompose(T, ranks, iters, seed=seed + i, restarts=restarts, record=False)
+        eg, eo = oracle.rel_error(T, views[i]), oracle.rel_error(T, ref)
+        assert abs(eg - eo) <= 1e-3, f"instance {i} {dims}: {eg} vs {eo}"
