@@ -949,15 +949,19 @@ bool read_tuning_cache(const char* path, uint64_t sig, int* split) {
   if (!path || !path[0]) return false;
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
-  char tag[32];
-  unsigned long long key = 0;
-  int val = 0;
+  char line[256];
   bool found = false;
-  while (std::fscanf(f, "%31s %llx %d", tag, &key, &val) == 3)
-    if (std::strcmp(tag, "gsplit") == 0 && key == sig && (val == 1 || val == 2 || val == 4 || val == 8)) {
+  // one entry per line: "gsplit <signature hex> <split> <probe ms>"
+  while (std::fgets(line, sizeof(line), f)) {
+    char tag[32];
+    unsigned long long key = 0;
+    int val = 0;
+    if (std::sscanf(line, "%31s %llx %d", tag, &key, &val) == 3 && std::strcmp(tag, "gsplit") == 0 &&
+        key == sig && (val == 1 || val == 2 || val == 4 || val == 8)) {
       *split = val;   // the last entry for a signature wins
       found = true;
     }
+  }
   std::fclose(f);
   return found;
 }
