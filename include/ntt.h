@@ -227,6 +227,37 @@ ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_d
                        void* ws, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Column-sharded multiplicative updates: the 1-D column distribution of
+ * Section III-B with one GPU per shard.  Every rank holds a contiguous block of
+ * n_shard columns of X (m x n_shard FP32, device) and of H (r x n_shard) and a
+ * replica of W (m x r).  One iteration:
+ *   nmf_mu_shard_pass   (local)  H update of the local columns, then the
+ *                                local [P ; Q] = [X ; H] H^T reduced into FP64
+ *   all-reduce (sum) of [P ; Q] over the ranks -- the caller's collective, the
+ *                                exchange step of Algorithms 4-6
+ *   nmf_mu_shard_update (replicated) W <- max(0, W o P / (W Q + eps)) and the
+ *                                objective 1/2 (||X||^2 - 2 <W,P> + <W^T W, Q>)
+ * The shards exchange neither X nor H.  [P ; Q] is pq_count doubles in the
+ * library's layout (nmf_mu_shard_sizes); m <= NTT_MAX_ROWS, r <= NTT_MAX_RANK.
+ * ------------------------------------------------------------------------ */
+ntt_status nmf_mu_shard_sizes(int64_t m, int64_t n_shard, int r, size_t* ws_bytes, size_t* pq_count);
+
+/* out_dev (device, one double) = ||X||_F^2 of the local columns (FP64 sum);
+ * its all-reduce gives the xnorm2 of nmf_mu_shard_update.  ws: as below. */
+ntt_status nmf_mu_shard_norm(int64_t m, int64_t n_shard, const float* X, double* out_dev, void* ws, void* stream);
+
+/* The local half-iteration.  W: device m x r (read); H: device r x n_shard
+ * (updated); pq_out: device pq_count doubles (written); ws: ws_bytes. */
+ntt_status nmf_mu_shard_pass(int64_t m, int64_t n_shard, int r, const float* X, const float* W, float* H,
+                             float eps_mu, double* pq_out, void* ws, void* stream);
+
+/* The replicated W half from the all-reduced pq (device, pq_count doubles).
+ * xnorm2: ||X||_F^2 of the whole (unsharded) X; obj_dev (nullable): one
+ * double receiving the objective of (W_new, H).  ws: as for the pass. */
+ntt_status nmf_mu_shard_update(int64_t m, int r, const double* pq, float* W, float eps_mu, double xnorm2,
+                               double* obj_dev, void* ws, void* stream);
+
+/* ------------------------------------------------------------------------
  * Algorithm 3 (distBCDnmf) on one GPU: block coordinate descent with
  * prox-linear block steps, extrapolation and the correction test, as the
  * APG-BCD method the paper cites defines them:

@@ -55,6 +55,7 @@ EXPORTS = (
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
     "nmf_mu_step_route", "nmf_mu_workspace_size_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
     "ntt_singular_values", "ntt_select_rank", "nmf_bcd_workspace_size", "nmf_bcd_step",
+    "nmf_mu_shard_sizes", "nmf_mu_shard_norm", "nmf_mu_shard_pass", "nmf_mu_shard_update",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
@@ -172,6 +173,10 @@ def lib():
     L.ntt_wait_probe.argtypes = [vp, i64, vp]
     L.ntt_plan_get_ranks.argtypes = [vp, p64]
     L.nmf_bcd_workspace_size.argtypes = [i64, i64, i32, psz]
+    L.nmf_mu_shard_sizes.argtypes = [i64, i64, i32, psz, psz]
+    L.nmf_mu_shard_norm.argtypes = [i64, i64, vp, vp, vp, vp]
+    L.nmf_mu_shard_pass.argtypes = [i64, i64, i32, vp, vp, vp, ctypes.c_float, vp, vp, vp]
+    L.nmf_mu_shard_update.argtypes = [i64, i32, vp, vp, ctypes.c_float, ctypes.c_double, vp, vp, vp]
     L.nmf_bcd_step.argtypes = [i64, i64, i32, vp, vp, vp, i32, vp, vp, vp]
     L.ntt_rank_workspace_size.argtypes = [i64, i64, psz]
     L.ntt_singular_values.argtypes = [i64, i64, vp, vp, vp, vp]
@@ -444,6 +449,67 @@ def nmf_bcd_step(X, W, H, iters, obj=None, workspace=None, stream=None):
                               _dev_ptr(H, torch.float32, "H"), int(iters), optr, _dev_ptr(workspace, None, "ws"),
                               _stream_ptr(stream)), "nmf_bcd_step")
     return workspace
+
+
+class ShardOps:
+    """The device halves of one rank's column-sharded MU iteration (include/ntt.h
+    nmf_mu_shard_*): X_shard m x n_shard, H_shard r x n_shard, W m x r (CUDA float32)."""
+
+    def __init__(self, m, n_shard, r, eps_mu=1e-12, device=None, stream=None):
+        import torch
+        wsb, pqn = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().nmf_mu_shard_sizes(int(m), int(n_shard), int(r), ctypes.byref(wsb), ctypes.byref(pqn)),
+               "nmf_mu_shard_sizes")
+        self.m, self.n, self.r, self.eps, self.stream = int(m), int(n_shard), int(r), float(eps_mu), stream
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.ws = empty_workspace(wsb.value, dev)
+        self.pq = torch.zeros(pqn.value, dtype=torch.float64, device=dev)
+        self.xn = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def norm2(self, X):
+        import torch
+        _check(lib().nmf_mu_shard_norm(self.m, self.n, _dev_ptr(X, torch.float32, "X"),
+                                       _dev_ptr(self.xn, torch.float64, "out"), _dev_ptr(self.ws, None, "ws"),
+                                       _stream_ptr(self.stream)), "nmf_mu_shard_norm")
+        return self.xn
+
+    def local_pass(self, X, W, H):
+        import torch
+        _check(lib().nmf_mu_shard_pass(self.m, self.n, self.r, _dev_ptr(X, torch.float32, "X"),
+                                       _dev_ptr(W, torch.float32, "W"), _dev_ptr(H, torch.float32, "H"),
+                                       ctypes.c_float(self.eps), _dev_ptr(self.pq, torch.float64, "pq"),
+                                       _dev_ptr(self.ws, None, "ws"), _stream_ptr(self.stream)), "nmf_mu_shard_pass")
+        return self.pq
+
+    def update(self, pq, W, xnorm2, obj=None):
+        import torch
+        optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
+        _check(lib().nmf_mu_shard_update(self.m, self.r, _dev_ptr(pq, torch.float64, "pq"),
+                                         _dev_ptr(W, torch.float32, "W"), ctypes.c_float(self.eps),
+                                         ctypes.c_double(float(xnorm2)), optr, _dev_ptr(self.ws, None, "ws"),
+                                         _stream_ptr(self.stream)), "nmf_mu_shard_update")
+
+
+def sharded_nmf_mu(X_shard, W, H_shard, iters, ops, all_reduce=None):
+    """Column-sharded multiplicative updates (Section III-B's 1-D column
+    distribution): this rank updates its H columns and W (replicated) in place.
+    ops: ShardOps of this rank (or any object with norm2 / local_pass / update);
+    all_reduce: in-place sum of a tensor over the ranks (e.g.
+    torch.distributed.all_reduce), None on one rank.  Per iteration the only
+    exchange is the all-reduce of [P ; Q].  Returns the objective after each
+    iteration (a list of floats)."""
+    reduce = all_reduce or (lambda t: None)
+    xn = ops.norm2(X_shard)
+    reduce(xn)
+    xnorm2 = float(xn[0])
+    trace = []
+    for _ in range(int(iters)):
+        pq = ops.local_pass(X_shard, W, H_shard)
+        reduce(pq)
+        obj = pq.new_zeros(1)
+        ops.update(pq, W, xnorm2, obj)
+        trace.append(float(obj[0]))
+    return trace
 
 
 def _many_args(Xs, Ws, Hs):

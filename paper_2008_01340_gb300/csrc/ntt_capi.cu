@@ -1093,6 +1093,77 @@ ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dty
   return run_mu_iters(s, dev, eps_mu, iters, 0, st, engine_out);
 }
 
+ntt_status nmf_mu_shard_sizes(int64_t m, int64_t n_shard, int r, size_t* ws_bytes, size_t* pq_count) {
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n_shard, r, 0, device_sms(), &s));
+  size_t total = 0;
+  mu_ws_layout(s, &total);
+  if (ws_bytes) *ws_bytes = total;
+  if (pq_count) *pq_count = (size_t)s.part_stride();
+  return NTT_OK;
+}
+
+ntt_status nmf_mu_shard_norm(int64_t m, int64_t n_shard, const float* X, double* out_dev, void* ws, void* stream) {
+  if (!X || !out_dev || !ws || m < 1 || n_shard < 1) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n_shard, 1, 0, device_sms(), &s));
+  size_t total = 0;
+  MuWs L = mu_ws_layout(s, &total);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  unsigned* tickets = reinterpret_cast<unsigned*>(w + L.tickets);
+  NTT_CUDA_TRY(launch_zero(tickets, 64, st));
+  return resid_into(X, 0, nullptr, nullptr, m, n_shard, 0, 0, 1.0, out_dev, nullptr,
+                    reinterpret_cast<double*>(w + L.part64), tickets + 1, st);
+}
+
+ntt_status nmf_mu_shard_pass(int64_t m, int64_t n_shard, int r, const float* X, const float* W, float* H,
+                             float eps_mu, double* pq_out, void* ws, void* stream) {
+  if (!X || !W || !H || !pq_out || !ws || !(eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  if (r > m) return NTT_ERR_RANK_INFEASIBLE;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, n_shard, r, 0, device_sms(), &s));
+  size_t total = 0;
+  MuWs L = mu_ws_layout(s, &total);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  NTT_CUDA_TRY(launch_zero(w + L.status, L.tickets + 64 - L.status, st));
+  MuDev dev;
+  dev.X = X;
+  dev.W = const_cast<float*>(W);
+  dev.H = H;
+  dev.G = reinterpret_cast<float*>(w + L.G);
+  dev.part = reinterpret_cast<float*>(w + L.part);
+  dev.red = reinterpret_cast<float*>(w + L.red);
+  dev.ticket = reinterpret_cast<unsigned*>(w + L.tickets);
+  dev.status = reinterpret_cast<int*>(w + L.status);
+  NTT_CUDA_TRY(launch_gram(s, dev, st));
+  mu_finalize_shape(&s, X, H, device_sms());
+  CUtensorMap mx, mh;
+  std::memset(&mx, 0, sizeof(mx));
+  std::memset(&mh, 0, sizeof(mh));
+  if (s.tma) NTT_TRY(mu_encode_maps(s, X, H, &mx, &mh));
+  NTT_CUDA_TRY(launch_mu_pass(s, dev, eps_mu, mx, mh, st));
+  NTT_CUDA_TRY(launch_shard_reduce(dev.part, s.grid, s.part_stride(), pq_out, st));
+  return NTT_OK;
+}
+
+ntt_status nmf_mu_shard_update(int64_t m, int r, const double* pq, float* W, float eps_mu, double xnorm2,
+                               double* obj_dev, void* ws, void* stream) {
+  if (!pq || !W || !ws || !(eps_mu >= 0.0f) || m < 1 || r < 1) return NTT_ERR_INVALID_ARG;
+  if (m > NTT_MAX_ROWS || r > NTT_MAX_RANK) return NTT_ERR_UNSUPPORTED;
+  MuShape s;
+  NTT_TRY(mu_choose_shape(m, 1 << 20, r, 0, device_sms(), &s));   // MP, R of the [P ; Q] layout
+  size_t total = 0;
+  MuWs L = mu_ws_layout(s, &total);
+  char* w = reinterpret_cast<char*>(ws);
+  NTT_CUDA_TRY(launch_shard_update(pq, (int)m, r, s.MP, s.R, W, reinterpret_cast<float*>(w + L.G), eps_mu, xnorm2,
+                                   obj_dev, reinterpret_cast<cudaStream_t>(stream)));
+  return NTT_OK;
+}
+
 ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes) {
   if (!bytes) return NTT_ERR_INVALID_ARG;
   MuShape s;

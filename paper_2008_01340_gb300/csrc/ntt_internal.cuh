@@ -449,6 +449,13 @@ RankWs rank_ws_layout(int64_t m, int64_t n, int num_sms);
 cudaError_t launch_rank_select(const float* X, int64_t m, int64_t n, double eps_rank, int rank_cap,
                                const RankWs& w, char* ws, double* sigma_out, int* rank_out, cudaStream_t st);
 
+// Column-sharded NMF (mu_shard.cu): the fixed-order reduction of one pass's
+// partials into FP64 [P ; Q] ((MP + R) x R), and the replicated W half of the
+// iteration from the all-reduced [P ; Q].
+cudaError_t launch_shard_reduce(const float* part, int nb, int E, double* pq, cudaStream_t st);
+cudaError_t launch_shard_update(const double* pq, int m, int r, int MP, int R, float* W, float* G, float eps,
+                                double xnorm2, double* obj, cudaStream_t st);
+
 // Number of SMs of the current device (cached; 152 when no device).
 int device_sms();
 
