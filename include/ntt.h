@@ -227,6 +227,29 @@ ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_d
                        void* ws, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Out-of-core multiplicative updates: X larger than device memory (the
+ * paper's Section IV runs a 550 GB synthetic tensor) stays in host memory and
+ * every iteration streams it to the device in column chunks of chunk_cols
+ * columns (a multiple of 4) through two device buffers; the copy of the next
+ * chunk (host row pitch n) overlaps the fused pass over the current one, whose
+ * H columns are read and written in place.  Each chunk's [P ; Q] is reduced in
+ * FP64 and added in chunk order, then W is updated once per iteration.  Pinned
+ * host memory (cudaHostAlloc / cudaHostRegister) is needed for the copies to
+ * run asynchronously at the link rate.  With n <= chunk_cols X is copied once.
+ * m <= NTT_MAX_ROWS, r <= NTT_MAX_RANK.
+ * ------------------------------------------------------------------------ */
+ntt_status nmf_mu_host_workspace_size(int64_t m, int64_t n, int r, int64_t chunk_cols, size_t* bytes);
+
+/* `iters` MU iterations with X_host (host m x n FP32, C order) streamed; W
+ * (m x r) and H (r x n) device FP32, in place; obj_dev (nullable, `iters`
+ * doubles) the FP64 Gram-form objective after each iteration.  ws: device,
+ * nmf_mu_host_workspace_size bytes (two chunk buffers of 4 m chunk_cols bytes
+ * dominate).  Returns after enqueueing; X_host must stay unchanged until the
+ * stream has passed the call. */
+ntt_status nmf_mu_step_host(int64_t m, int64_t n, int r, const float* X_host, float* W, float* H, int iters,
+                            float eps_mu, double* obj_dev, int64_t chunk_cols, void* ws, void* stream);
+
+/* ------------------------------------------------------------------------
  * Column-sharded multiplicative updates: the 1-D column distribution of
  * Section III-B with one GPU per shard.  Every rank holds a contiguous block of
  * n_shard columns of X (m x n_shard FP32, device) and of H (r x n_shard) and a

@@ -56,6 +56,7 @@ EXPORTS = (
     "nmf_mu_step_route", "nmf_mu_workspace_size_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
     "ntt_singular_values", "ntt_select_rank", "nmf_bcd_workspace_size", "nmf_bcd_step",
     "nmf_mu_shard_sizes", "nmf_mu_shard_norm", "nmf_mu_shard_pass", "nmf_mu_shard_update",
+    "nmf_mu_host_workspace_size", "nmf_mu_step_host",
     "ntt_status_of_workspace", "ntt_uniform_init", "ntt_reconstruct_workspace_size",
     "ntt_reconstruct", "ntt_rel_error", "ntt_compression_ratio", "nmf_mu_step_noalloc",
     "ntt_batch_create", "ntt_batch_sizes", "ntt_batch_offsets", "ntt_decompose_batched",
@@ -174,6 +175,8 @@ def lib():
     L.ntt_plan_get_ranks.argtypes = [vp, p64]
     L.nmf_bcd_workspace_size.argtypes = [i64, i64, i32, psz]
     L.nmf_mu_shard_sizes.argtypes = [i64, i64, i32, psz, psz]
+    L.nmf_mu_host_workspace_size.argtypes = [i64, i64, i32, i64, psz]
+    L.nmf_mu_step_host.argtypes = [i64, i64, i32, vp, vp, vp, i32, ctypes.c_float, vp, i64, vp, vp]
     L.nmf_mu_shard_norm.argtypes = [i64, i64, vp, vp, vp, vp]
     L.nmf_mu_shard_pass.argtypes = [i64, i64, i32, vp, vp, vp, ctypes.c_float, vp, vp, vp]
     L.nmf_mu_shard_update.argtypes = [i64, i32, vp, vp, ctypes.c_float, ctypes.c_double, vp, vp, vp]
@@ -448,6 +451,29 @@ def nmf_bcd_step(X, W, H, iters, obj=None, workspace=None, stream=None):
     _check(lib().nmf_bcd_step(m, n, r, _dev_ptr(X, torch.float32, "X"), _dev_ptr(W, torch.float32, "W"),
                               _dev_ptr(H, torch.float32, "H"), int(iters), optr, _dev_ptr(workspace, None, "ws"),
                               _stream_ptr(stream)), "nmf_bcd_step")
+    return workspace
+
+
+def nmf_mu_step_host(X_host, W, H, iters, chunk_cols, eps_mu=1e-12, obj=None, workspace=None, stream=None):
+    """Out-of-core MU: X_host is a CPU float32 tensor (pin it for asynchronous
+    copies), streamed in column chunks every iteration; W, H CUDA float32 in place."""
+    import torch
+    if X_host.is_cuda or X_host.dtype != torch.float32 or not X_host.is_contiguous():
+        raise TypeError("X_host must be a contiguous CPU float32 tensor")
+    m, n = X_host.shape
+    r = W.shape[1]
+    if W.shape[0] != m or H.shape != (r, n):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        b = ctypes.c_size_t()
+        _check(lib().nmf_mu_host_workspace_size(m, n, r, int(chunk_cols), ctypes.byref(b)),
+               "nmf_mu_host_workspace_size")
+        workspace = empty_workspace(b.value, W.device)
+    optr = _dev_ptr(obj, torch.float64, "obj") if obj is not None else None
+    _check(lib().nmf_mu_step_host(m, n, r, ctypes.c_void_p(X_host.data_ptr()), _dev_ptr(W, torch.float32, "W"),
+                                  _dev_ptr(H, torch.float32, "H"), int(iters), ctypes.c_float(eps_mu), optr,
+                                  int(chunk_cols), _dev_ptr(workspace, None, "ws"), _stream_ptr(stream)),
+           "nmf_mu_step_host")
     return workspace
 
 

@@ -175,7 +175,8 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
 bool mu_tma_ok(const MuShape& s, const void* X, const float* H) {
   const int xb = s.bf16 ? 2 : 4;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(H) & 15)) return false;
-  if ((s.n * xb) % 16 != 0 || (s.n * 4) % 16 != 0) return false;
+  const int64_t ldh = s.ldh > 0 ? s.ldh : s.n;
+  if ((s.n * xb) % 16 != 0 || (ldh * 4) % 16 != 0) return false;
   return true;
 }
 
@@ -216,7 +217,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
   }
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.r};
-    cuuint64_t strides[1] = {(cuuint64_t)(s.n * 4)};
+    cuuint64_t strides[1] = {(cuuint64_t)((s.ldh > 0 ? s.ldh : s.n) * 4)};
     cuuint32_t box[2] = {(cuuint32_t)(s.narrow ? 32 : s.T), (cuuint32_t)s.R};
     cuuint32_t es[2] = {1, 1};
     CUresult e = fn(mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(H), dims, strides,

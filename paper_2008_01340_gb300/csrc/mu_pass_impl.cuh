@@ -143,6 +143,7 @@ struct PassParams {
   // BCD mode
   float* Hb[3];              // the three H buffers (cooperative loader / stores)
   const BcdState* bcd;       // rotation, w_h, L_h
+  int64_t ldh;               // row stride of H (n, or more for a column block of a wider H)
   int bcd_init;              // accumulate P, Q of the accepted H only
   double* res_part;          // BCD: per CTA, sum over its tiles of ||x_c - W h_new_c||^2
 };
@@ -256,8 +257,8 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
       for (int idx = tid; idx < R * T; idx += NT) {
         const int k = idx / T, c = idx % T;
         const int64_t col = col0 + c;
-        Hw[idx] = (k < r && col < n) ? Hld[(int64_t)k * n + col] : 0.0f;
-        if constexpr (C::BCD) Hw[R * T + idx] = (k < r && col < n) ? Hp[(int64_t)k * n + col] : 0.0f;
+        Hw[idx] = (k < r && col < n) ? Hld[(int64_t)k * p.ldh + col] : 0.0f;
+        if constexpr (C::BCD) Hw[R * T + idx] = (k < r && col < n) ? Hp[(int64_t)k * p.ldh + col] : 0.0f;
       }
       __syncthreads();
     }
@@ -336,7 +337,7 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
             hn = Lh > 0.0f ? fmaxf(0.0f, hk - __fdiv_rn(gh - y, Lh)) : hk;
           }
           Hn[k * T + c] = hn;
-          if (!tma && !p.bcd_init && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
+          if (!tma && !p.bcd_init && k < r && col < n) Hst[(int64_t)k * p.ldh + col] = hn;
         }
       }
     } else {
@@ -370,7 +371,7 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
             const float den = ((k & 1) ? gh[k / 2].y : gh[k / 2].x) + p.eps;
             const float hn = fmaxf(0.0f, __fdividef(h[k] * y, den));
             Hn[k * T + c] = hn;
-            if (!tma && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
+            if (!tma && k < r && col < n) Hst[(int64_t)k * p.ldh + col] = hn;
           }
         } else {
 #pragma unroll
@@ -394,7 +395,7 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
               if (j == k) hk = h[j];
             const float hn = fmaxf(0.0f, __fdividef(hk * y, gh + p.eps));
             Hn[k * T + c] = hn;
-            if (!tma && k < r && col < n) Hst[(int64_t)k * n + col] = hn;
+            if (!tma && k < r && col < n) Hst[(int64_t)k * p.ldh + col] = hn;
           }
         }
       }
@@ -572,6 +573,7 @@ cudaError_t launch_pass_bcd_cfg(const MuShape& s, const MuDev& d, const CUtensor
   p.ntiles = (int)((s.n + C::T - 1) / C::T);
   p.use_tma = s.tma;
   p.eps = 0.0f;
+  p.ldh = s.ldh > 0 ? s.ldh : s.n;
   for (int i = 0; i < 3; ++i) p.Hb[i] = Hb[i];
   p.bcd = st_dev;
   p.bcd_init = init;
@@ -604,6 +606,7 @@ cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const C
   p.ntiles = (int)((s.n + C::T - 1) / C::T);
   p.use_tma = s.tma;
   p.eps = eps;
+  p.ldh = s.ldh > 0 ? s.ldh : s.n;
   p.Hb[0] = p.Hb[1] = p.Hb[2] = d.H;
   p.bcd = nullptr;
   p.bcd_init = 0;

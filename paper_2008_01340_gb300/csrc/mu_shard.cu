@@ -24,7 +24,9 @@ constexpr int kShardChunks = kAuxThreads / kShardEntries;   // 8
 
 // pq[e] = sum over the pass CTAs of part[cta][e]: eight FP32 chunks of CTAs,
 // then an FP64 pairwise sum of the chunks (a fixed order).
-__global__ void __launch_bounds__(kAuxThreads) shard_reduce_kernel(const float* part, int nb, int E, double* pq) {
+// accumulate: pq[e] += the sum (column chunks of one pass, added in chunk order).
+__global__ void __launch_bounds__(kAuxThreads) shard_reduce_kernel(const float* part, int nb, int E, double* pq,
+                                                                   int accumulate) {
   __shared__ float chunk[kShardChunks][kShardEntries];
   const int tid = threadIdx.x;
   const int el = tid % kShardEntries, j = tid / kShardEntries;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(kAuxThreads) shard_reduce_kernel(const float* 
     for (int w = 1; w < kShardChunks; w *= 2)
 #pragma unroll
       for (int c = 0; c + w < kShardChunks; c += 2 * w) t[c] += t[c + w];
-    pq[e] = t[0];
+    pq[e] = accumulate ? pq[e] + t[0] : t[0];
   }
 }
 
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kAuxThreads) shard_reduce_kernel(const float* 
 // single-GPU combine uses them, W, G.
 __global__ void __launch_bounds__(kAuxThreads) shard_update_kernel(const double* pq, int m, int r, int MP, int R,
                                                                    float* W, float* G, float eps, double xnorm2,
-                                                                   double* obj) {
+                                                                   const double* xn_dev, double* obj) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
   const int E = (MP + R) * R;
@@ -118,19 +120,20 @@ __global__ void __launch_bounds__(kAuxThreads) shard_update_kernel(const double*
       As += dsh[w];
       Bs += dsh[nw + w];
     }
-    *obj = 0.5 * (xnorm2 - 2.0 * As + Bs);
+    *obj = 0.5 * ((xn_dev ? *xn_dev : xnorm2) - 2.0 * As + Bs);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_shard_reduce(const float* part, int nb, int E, double* pq, cudaStream_t st) {
-  shard_reduce_kernel<<<(E + kShardEntries - 1) / kShardEntries, kAuxThreads, 0, st>>>(part, nb, E, pq);
+cudaError_t launch_shard_reduce(const float* part, int nb, int E, double* pq, cudaStream_t st, bool accumulate) {
+  shard_reduce_kernel<<<(E + kShardEntries - 1) / kShardEntries, kAuxThreads, 0, st>>>(part, nb, E, pq,
+                                                                                     accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_shard_update(const double* pq, int m, int r, int MP, int R, float* W, float* G, float eps,
-                                double xnorm2, double* obj, cudaStream_t st) {
+                                double xnorm2, double* obj, cudaStream_t st, const double* xn_dev) {
   static bool attr_set = false;
   if (!attr_set) {
     const cudaError_t e =
@@ -139,7 +142,7 @@ cudaError_t launch_shard_update(const double* pq, int m, int r, int MP, int R, f
     attr_set = true;
   }
   const size_t smem = (size_t)((MP + R) * R + m * r + R * R) * sizeof(float);
-  shard_update_kernel<<<1, kAuxThreads, smem, st>>>(pq, m, r, MP, R, W, G, eps, xnorm2, obj);
+  shard_update_kernel<<<1, kAuxThreads, smem, st>>>(pq, m, r, MP, R, W, G, eps, xnorm2, xn_dev, obj);
   return cudaGetLastError();
 }
 

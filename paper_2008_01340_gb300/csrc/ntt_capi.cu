@@ -1164,6 +1164,20 @@ ntt_status nmf_mu_shard_update(int64_t m, int r, const double* pq, float* W, flo
   return NTT_OK;
 }
 
+ntt_status nmf_mu_host_workspace_size(int64_t m, int64_t n, int r, int64_t chunk_cols, size_t* bytes) {
+  if (!bytes) return NTT_ERR_INVALID_ARG;
+  return stream_ws_size(m, n, r, chunk_cols, bytes);
+}
+
+ntt_status nmf_mu_step_host(int64_t m, int64_t n, int r, const float* X_host, float* W, float* H, int iters,
+                            float eps_mu, double* obj_dev, int64_t chunk_cols, void* ws, void* stream) {
+  if (!X_host || !W || !H || !ws || iters < 0 || !(eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NTT_ERR_INVALID_ARG;
+  if (r > m || r > n) return NTT_ERR_RANK_INFEASIBLE;
+  return stream_mu(m, n, r, X_host, W, H, iters, eps_mu, obj_dev, chunk_cols, ws,
+                   reinterpret_cast<cudaStream_t>(stream));
+}
+
 ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes) {
   if (!bytes) return NTT_ERR_INVALID_ARG;
   MuShape s;

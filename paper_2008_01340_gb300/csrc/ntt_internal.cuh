@@ -296,6 +296,7 @@ struct MuShape {
   int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
   int route = NTT_ROUTE_AUTO;   // ntt_route restricting the pass choice
   int split_ok = 0;  // scratch for the two BF16 terms of X exists (MuDev::xs)
+  int64_t ldh = 0;   // row stride of H when it is a column block of a wider H (generic pass only)
   size_t smem = 0;   // dynamic shared memory of the pass kernel
   int part_stride() const { return (MP + R) * R; }
 };
@@ -452,9 +453,16 @@ cudaError_t launch_rank_select(const float* X, int64_t m, int64_t n, double eps_
 // Column-sharded NMF (mu_shard.cu): the fixed-order reduction of one pass's
 // partials into FP64 [P ; Q] ((MP + R) x R), and the replicated W half of the
 // iteration from the all-reduced [P ; Q].
-cudaError_t launch_shard_reduce(const float* part, int nb, int E, double* pq, cudaStream_t st);
+cudaError_t launch_shard_reduce(const float* part, int nb, int E, double* pq, cudaStream_t st,
+                                bool accumulate = false);
+// xn_dev (nullable) overrides xnorm2 with a device value.
 cudaError_t launch_shard_update(const double* pq, int m, int r, int MP, int R, float* W, float* G, float eps,
-                                double xnorm2, double* obj, cudaStream_t st);
+                                double xnorm2, double* obj, cudaStream_t st, const double* xn_dev = nullptr);
+
+// Out-of-core MU (ntt_stream.cu): X in host memory streamed in column chunks.
+ntt_status stream_ws_size(int64_t m, int64_t n, int r, int64_t chunk_cols, size_t* bytes);
+ntt_status stream_mu(int64_t m, int64_t n, int r, const float* X_host, float* W, float* H, int iters, float eps,
+                     double* obj_dev, int64_t chunk_cols, void* workspace, cudaStream_t st);
 
 // Number of SMs of the current device (cached; 152 when no device).
 int device_sms();
