@@ -45,7 +45,8 @@ def test_sharded_iterates_match_unsharded(ntt, m, n, r, bounds):
     W = torch.from_numpy(W0.copy()).cuda()
     ops = [ntt.ShardOps(m, b - a, r) for a, b in shards]
     xn = sum(float(o.norm2(x)[0]) for o, x in zip(ops, Xs))
-    assert abs(xn - float(np.sum(X.astype(np.float64) ** 2))) <= 1e-12 * xn
+    # FP32 squares summed in FP64: within 2^-24 relative of the FP64 sum
+    assert abs(xn - float(np.sum(X.astype(np.float64) ** 2))) <= 6e-8 * xn
     trace = []
     for _ in range(iters):
         pq = sum(o.local_pass(x, W, h).clone() for o, x, h in zip(ops, Xs, Hs))   # the all-reduce
