@@ -273,6 +273,19 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   };
 
   for (int q = 0; q < C::STAGES - 1; ++q) issue(q, (int)blockIdx.x + q * (int)gridDim.x, q < count);
+  // old H of a tile's column, all ranks; with rank bucket 16 the next tile's
+  // values are loaded one tile ahead (registers), so their latency overlaps
+  // the current tile
+  constexpr bool PREFETCH_H = R <= 16;
+  auto load_h = [&](int tile_, float* hv) {
+    const int64_t col_ = (int64_t)tile_ * C::TC + cc;
+#pragma unroll
+    for (int l = 0; l < R; ++l) hv[l] = (owner && l < r && col_ < n) ? p.H[(int64_t)l * n + col_] : 0.0f;
+  };
+  float hnext[PREFETCH_H ? R : 1];
+  if constexpr (PREFETCH_H) {
+    if (count > 0) load_h((int)blockIdx.x, hnext);
+  }
   int j = 0;
   for (; j < count; ++j) {
     const int s = j % C::STAGES;
@@ -291,19 +304,34 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
                  dW + (uint64_t)((((kk >> 2) * N3 * 128) + (kk & 3) * 32) >> 4), C::IDA, kk > 0 ? 1u : 0u);
       mma_commit(barA);
     }
-    // old H of this column, all ranks (overlaps the MMAs)
+    // tile j + STAGES - 1 into the stage of tile j - 1 as soon as phase B of
+    // tile j - 1 (its last reader) is complete: the load runs beside phase A
+    // and the epilogue of tile j (phase B of tile j is not issued yet, so barB
+    // is at most at that phase)
+    {
+      bool okB = true;
+      if (j > 0) {
+        okB = mbar_wait_bounded(barB, (uint32_t)((j - 1) & 1));
+        if (!okB) s_err = 1;
+        tc_fence_after();
+      }
+      issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x,
+            okB && j + C::STAGES - 1 < count);
+    }
     float h[R];
+    if constexpr (PREFETCH_H) {
 #pragma unroll
-    for (int l = 0; l < R; ++l) h[l] = (owner && l < r && col < n) ? p.H[(int64_t)l * n + col] : 0.0f;
+      for (int l = 0; l < R; ++l) h[l] = hnext[l];
+      if (j + 1 < count) load_h(tile + (int)gridDim.x, hnext);
+    } else {
+      load_h(tile, h);   // overlaps the MMAs
+    }
     if (!mbar_wait_bounded(barA, (uint32_t)(j & 1))) s_err = 1;
     tc_fence_after();
     __syncthreads();
     if (s_err) break;
     // phase B of tile j-1 is complete: end the TMEM run every FLUSH tiles
     if (j > 0 && j % C::FLUSH == 0) flush();
-    // tile j + STAGES - 1 into the stage of tile j - 1, whose readers (phases A
-    // and B of tile j - 1) are done
-    issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x, j + C::STAGES - 1 < count);
     // ---- epilogue
     float y[KH];
     {
