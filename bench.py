@@ -148,6 +148,26 @@ class ClockSampler:
 # CPU baseline: the FP64 oracle on a bounded sample of the job
 # ---------------------------------------------------------------------------
 
+def cpu_model():
+    """CPU model of this host (lscpu's model name, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(A, cfg, budget_s=15.0):
     """Time the oracle's MU iterations on column samples of every stage's
     unfolding (about budget_s seconds in total) and extrapolate the whole job
@@ -186,9 +206,10 @@ def cpu_baseline(A, cfg, budget_s=15.0):
         total_s += dt * iters * (n / cols)
         desc.append(f"stage {s+1}: {k} iters on {m}x{cols} of {m}x{n} ({src})")
     cores = os.cpu_count() or 1
-    return {"value": 1.0 / total_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": 1.0 / total_s, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": "; ".join(desc) + f"; extrapolated to {iters} iters x all columns per stage "
-                      f"(extrapolated job time {total_s:.1f} s)",
+                      f"(extrapolated job time {total_s:.1f} s; iterations per stage sample until the "
+                      f"stage's share of a {budget_s:.0f} s budget or 50 are spent)",
             "seconds_spent": round(spent, 2)}
 
 
@@ -212,7 +233,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "note": "FP64 numpy oracle on host cores"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                         "sample": cb["sample"]},
+                         "cpu_model": cb["cpu_model"], "sample": cb["sample"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -326,7 +326,9 @@ namespace {
 // the single-problem pass on GB300), else the pass; BF16 stages the tensor-core
 // pass takes (128/256 rows; with NTT_ROUTE_TC also 16/32 rows) stay on the
 // single-problem path.  The plan's route restricts the choice (ntt_route).
-bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route) {
+// split_ok: the split tensor-core form may take FP32 stages (not in precision-form
+// plans, whose FP32 refinement iterations exist to restore full FP32 X).
+bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route, bool split_ok = true) {
   const int MP = group_mp_bucket((int)m), R = group_r_bucket(r);
   if (MP < 0 || R < 0) return false;
   if (xbf16 && (!gpass_bf16_supported(MP, R) || n % 8 != 0)) return false;
@@ -335,7 +337,7 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route) {
   if (route == NTT_ROUTE_TC && ((xbf16 && tcb_pass_supported(MP, R)) || (!xbf16 && tc_pass_supported(MP, R))))
     return false;
   // FP32 stages of 128/256 rows at rank 16/32: the split tensor-core form
-  if (!xbf16 && tcs_route_ok(m, n, r, route)) return false;
+  if (!xbf16 && split_ok && tcs_route_ok(m, n, r, route)) return false;
   if (route != NTT_ROUTE_FMA && xbf16 && tcb_pass_supported(MP, R) && MP >= 128) return false;
   return MP <= 256 && R >= 16;
 }
@@ -371,7 +373,7 @@ size_t plan_stage_routes(ntt_plan p, ntt_plan_s::Stage& S, int sms, size_t base,
     if (p->solver != NTT_SOLVER_MU) continue;   // the grouped engine runs multiplicative updates only
     if (xb && p->xdt != NTT_BF16) continue;
     if (xb == 0 && p->xdt == NTT_BF16 && p->refine == 0) continue;
-    if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route)) continue;
+    if (!plan_route_group(S.m, S.n, S.r, xb != 0, p->route, p->xdt == NTT_F32)) continue;
     // a main loop with a stopping test runs on the single-problem passes
     const bool main_loop = xb != 0 || p->xdt != NTT_BF16;
     if (main_loop && p->tol > 0.0) continue;
@@ -717,7 +719,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
   p->h_bytes = hb;
   // split-form terms (2 m n BF16) for FP32 stages the split tensor-core pass may take
   size_t xs_bytes = 0;
-  if (p->solver == NTT_SOLVER_MU)
+  if (p->solver == NTT_SOLVER_MU && p->xdt == NTT_F32)
     for (int s = 0; s < d - 1; ++s) {
       const int64_t n = prod(dims, s + 1, d);
       for (int64_t rp = auto_rank ? 1 : p->ranks_max[s]; rp <= p->ranks_max[s]; ++rp) {
