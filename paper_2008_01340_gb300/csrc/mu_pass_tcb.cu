@@ -304,20 +304,6 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
                  dW + (uint64_t)((((kk >> 2) * N3 * 128) + (kk & 3) * 32) >> 4), C::IDA, kk > 0 ? 1u : 0u);
       mma_commit(barA);
     }
-    // tile j + STAGES - 1 into the stage of tile j - 1 as soon as phase B of
-    // tile j - 1 (its last reader) is complete: the load runs beside phase A
-    // and the epilogue of tile j (phase B of tile j is not issued yet, so barB
-    // is at most at that phase)
-    {
-      bool okB = true;
-      if (j > 0) {
-        okB = mbar_wait_bounded(barB, (uint32_t)((j - 1) & 1));
-        if (!okB) s_err = 1;
-        tc_fence_after();
-      }
-      issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x,
-            okB && j + C::STAGES - 1 < count);
-    }
     float h[R];
     if constexpr (PREFETCH_H) {
 #pragma unroll
@@ -332,6 +318,11 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     if (s_err) break;
     // phase B of tile j-1 is complete: end the TMEM run every FLUSH tiles
     if (j > 0 && j % C::FLUSH == 0) flush();
+    // tile j + STAGES - 1 into the stage of tile j - 1, whose readers (phases A
+    // and B of tile j - 1) are done.  (Issuing it earlier, after a wait for
+    // phase B of tile j - 1 right behind phase A's issue, measured slower: the
+    // wait holds back the H loads that otherwise overlap the MMAs.)
+    issue((j + C::STAGES - 1) % C::STAGES, tile + (C::STAGES - 1) * (int)gridDim.x, j + C::STAGES - 1 < count);
     // ---- epilogue
     float y[KH];
     {
