@@ -41,6 +41,8 @@
 // X2^T W in lanes 64 + c, summed in the epilogue, and phase B (K = 128 over
 // both atoms, the H_new terms written into both atoms of the stack) sums
 // (X1 + X2) H_new^T; Q = H_new H_new^T runs over the first atom only.
+#include <cstring>
+
 #include "ntt_internal.cuh"
 
 namespace ntt {
@@ -143,8 +145,12 @@ struct TbParams {
   float eps;
 };
 
+// tmX1 / tmX2: split form only, TMA maps of X1 and X2 (64-column boxes of SR
+// rows, 128-byte swizzle: the layout of a tile's two atoms).
 template <class C>
-__global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbParams p) {
+__global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid_constant__ CUtensorMap tmX1,
+                                                                    const __grid_constant__ CUtensorMap tmX2,
+                                                                    const TbParams p) {
   constexpr int MP = C::MP, R = C::R, T = C::T, N3 = C::N3, KH = C::KH;
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
@@ -182,6 +188,10 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     s_err = 0;
     mbar_init(barA, 1);
     mbar_init(barB, 1);
+    if constexpr (C::SPLIT) {
+      mbar_init(smem_u32(&bars[2]), 1);   // TMA stage barriers of the split form
+      mbar_init(smem_u32(&bars[3]), 1);
+    }
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -198,9 +208,22 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
 
   // ---- X tile loader: rows < m, 8 BF16 values per 16-byte copy, zero fill past
   // n; tiles past the CTA's range issue nothing but still commit a group
+  int tma_issued = 0;   // split form: tiles whose TMA copies thread 0 has issued
   auto issue = [&](int stage, int tile, bool valid) {
     uint8_t* dst = smem + C::OFF_X + stage * C::XST;
     const int64_t col0 = (int64_t)tile * C::TC;
+    if constexpr (C::SPLIT) {
+      // X1 into the tile's first atom, X2 into its second: two copies on the
+      // stage's barrier (rows past m and columns past n arrive as zeros)
+      if (tid == 0 && valid) {
+        const uint32_t bar = smem_u32(&bars[2 + stage]);
+        mbar_arrive_expect_tx(bar, (uint32_t)(2 * C::SR * 64 * 2));
+        tma_load_2d(smem_u32(dst), &tmX1, (int)col0, 0, bar);
+        tma_load_2d(smem_u32(dst + C::SR * 128), &tmX2, (int)col0, 0, bar);
+        ++tma_issued;
+      }
+      return;
+    }
     for (int e = tid; valid && e < m * (T / 8); e += kTbThreads) {
       const int row = e / (T / 8), ch = e % (T / 8);
       // split form: chunks 0..7 from X1, 8..15 from X2 (the same 64 columns)
@@ -287,13 +310,19 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
     if (count > 0) load_h((int)blockIdx.x, hnext);
   }
   int j = 0;
+  int a_issued = -1;   // thread 0: the last tile whose phase A it issued
   for (; j < count; ++j) {
     const int s = j % C::STAGES;
     const int tile = (int)blockIdx.x + j * (int)gridDim.x;
     const int64_t col = (int64_t)tile * C::TC + cc;
-    asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
-    fence_proxy_async_smem();
+    if constexpr (C::SPLIT) {
+      if (!mbar_wait_bounded(smem_u32(&bars[2 + s]), (uint32_t)((j / C::STAGES) & 1))) s_err = 1;
+    } else {
+      asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
+      fence_proxy_async_smem();
+    }
     __syncthreads();
+    if (s_err) break;
     // ---- phase A
     if (tid == 0) {
       tc_fence_after();
@@ -303,6 +332,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
         mma_bf16(dA, dXa + (uint64_t)((kk * 2048) >> 4),
                  dW + (uint64_t)((((kk >> 2) * N3 * 128) + (kk & 3) * 32) >> 4), C::IDA, kk > 0 ? 1u : 0u);
       mma_commit(barA);
+      a_issued = j;
     }
     float h[R];
     if constexpr (PREFETCH_H) {
@@ -379,9 +409,6 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
       for (int t = 0; t < 3; ++t) {
         *reinterpret_cast<__nv_bfloat16*>(smem + (C::STACK ? C::OFF_X + s * C::XST : C::OFF_HN) +
                                           swz(C::HROW0 + t * R + k, c, C::HSR)) = t3[t];
-        // split form: the same terms under the X2 atom of the tile
-        if constexpr (C::SPLIT)
-          *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_HN + swz(C::HROW0 + t * R + k, c + 64, C::HSR)) = t3[t];
       }
     }
     fence_proxy_async_smem();
@@ -400,7 +427,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
           mma_bf16(dB(0), smem_desc(base, 16, 1024, kLayoutSw128),
                    smem_desc(base + C::HROW0 * 128, 16, 1024, kLayoutSw128), C::IDB, acc);
         } else {
-          const uint32_t ho = (uint32_t)((kk >> 2) * C::HROWS * 128 + (kk & 3) * 32);
+          // split form: the X2 atom's K steps read the same H_new columns (atom 0)
+          const uint32_t ho = (uint32_t)((C::SPLIT ? 0 : (kk >> 2)) * C::HROWS * 128 + (kk & 3) * 32);
 #pragma unroll
           for (int mb = 0; mb < C::NMB; ++mb)
             mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
@@ -417,9 +445,15 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   if (count > 0 && !s_err) {
     if (!mbar_wait_bounded(barB, (uint32_t)((count - 1) & 1))) s_err = 1;
   }
+  if constexpr (C::SPLIT) {
+    // TMA copies still in flight (issued, not yet waited for): drain them (bounded)
+    if (s_err && tid == 0)
+      for (int c2 = j; c2 < tma_issued; ++c2)
+        (void)mbar_wait_bounded(smem_u32(&bars[2 + c2 % C::STAGES]), (uint32_t)((c2 / C::STAGES) & 1));
+  }
   if (s_err && tid == 0) {
     // MMAs may still be in flight: phase A of tile j and phase B of tile j - 1 (bounded)
-    if (j < count) (void)mbar_wait_bounded(barA, (uint32_t)(j & 1));
+    if (j < count && a_issued == j) (void)mbar_wait_bounded(barA, (uint32_t)(j & 1));
     if (j >= 1) (void)mbar_wait_bounded(barB, (uint32_t)((j - 1) & 1));
   }
   tc_fence_after();
@@ -461,7 +495,15 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.ntiles = (int)((s.n + C::TC - 1) / C::TC);
   p.eps = eps;
   p.X2 = reinterpret_cast<const __nv_bfloat16*>(d.X2);
-  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(p);
+  CUtensorMap m1, m2;
+  std::memset(&m1, 0, sizeof(m1));
+  std::memset(&m2, 0, sizeof(m2));
+  if constexpr (C::SPLIT) {
+    if (encode_bf16_atom_map(d.X, s.m, s.n, C::SR, &m1) != NTT_OK ||
+        encode_bf16_atom_map(d.X2, s.m, s.n, C::SR, &m2) != NTT_OK)
+      return cudaErrorInvalidValue;
+  }
+  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(m1, m2, p);
   return cudaGetLastError();
 }
 

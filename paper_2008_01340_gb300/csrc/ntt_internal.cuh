@@ -360,6 +360,10 @@ bool tcs_route_ok(int64_t m, int64_t n, int r, int route);
 bool mu_tma_ok(const MuShape& s, const void* X, const float* H);
 // Decide TMA / tensor-core pass for these pointers (may change T and grid).
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms);
+// TMA map of a row-major BF16 matrix (rows x cols, 16-byte aligned rows) in
+// boxes of 64 columns x box_rows rows with the 128-byte swizzle of 16-byte
+// chunks: one box is one 64-column atom of the tensor-core passes' tiles.
+ntt_status encode_bf16_atom_map(const void* base, int64_t rows, int64_t cols, int box_rows, CUtensorMap* out);
 // Encode the two tensor maps (X: m x n, H: r x n) for a TMA pass.
 ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUtensorMap* mx,
                           CUtensorMap* mh);
