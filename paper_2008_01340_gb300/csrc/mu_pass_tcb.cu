@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   // c (split form: c % 64, lanes 64.. holding the X2 part of the same column)
   const int c = (warp % 4) * 32 + lane;
   const int cc = C::SPLIT ? c % 64 : c;
-  const bool owner = !C::SPLIT || c < 64;   // threads that update H
+  const bool owner = !C::SPLIT || c < 64;   // split form: the thread of the X1 lane of its column
   const int kh0 = (warp / 4) * KH;
   const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
 
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   auto load_h = [&](int tile_, float* hv) {
     const int64_t col_ = (int64_t)tile_ * C::TC + cc;
 #pragma unroll
-    for (int l = 0; l < R; ++l) hv[l] = (owner && l < r && col_ < n) ? p.H[(int64_t)l * n + col_] : 0.0f;
+    for (int l = 0; l < R; ++l) hv[l] = (l < r && col_ < n) ? p.H[(int64_t)l * n + col_] : 0.0f;
   };
   float hnext[PREFETCH_H ? R : 1];
   if constexpr (PREFETCH_H) {
@@ -369,19 +369,9 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
       }
     }
     tc_fence_before();
-    if constexpr (C::SPLIT) {
-      // Y = X1^T W (lane c) + X2^T W (lane 64 + c)
-      if (!owner)
-#pragma unroll
-        for (int q = 0; q < KH; ++q) ys[(c - 64) * R + kh0 + q] = y[q];
-      __syncthreads();
-      if (owner)
-#pragma unroll
-        for (int q = 0; q < KH; ++q) y[q] += ys[c * R + kh0 + q];
-    }
-    float hn[KH];
-#pragma unroll
-    for (int q = 0; q < KH; ++q) {
+    // H update of column cc, rank kh0 + q: H_new to HBM and its three BF16
+    // terms into the H_new stack
+    auto update_rank = [&](int q) {
       const int k = kh0 + q;
       float gh = 0.0f;
 #pragma unroll
@@ -396,20 +386,45 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
 #pragma unroll
       for (int l = 0; l < R; ++l)
         if (l == k) hk = h[l];
-      hn[q] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
-    }
-#pragma unroll
-    for (int q = 0; q < KH; ++q) {
-      if (!owner) break;
-      const int k = kh0 + q;
-      if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[q];
+      const float hn = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
+      if (k < r && col < n) p.H[(int64_t)k * n + col] = hn;
       __nv_bfloat16 t3[3];
-      split3(hn[q], t3);
+      split3(hn, t3);
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
+      for (int t = 0; t < 3; ++t)
         *reinterpret_cast<__nv_bfloat16*>(smem + (C::STACK ? C::OFF_X + s * C::XST : C::OFF_HN) +
-                                          swz(C::HROW0 + t * R + k, c, C::HSR)) = t3[t];
+                                          swz(C::HROW0 + t * R + k, cc, C::HSR)) = t3[t];
+    };
+    if constexpr (C::SPLIT) {
+      // Y = X1^T W (lane cc) + X2^T W (lane 64 + cc).  The two threads of a
+      // column share its ranks: the X1 lane's thread takes the first half of
+      // kh0 .. kh0 + KH, the X2 lane's thread the second; each hands the other
+      // its part of the other half through shared memory.
+      constexpr int HALF = KH / 2;
+      if (owner) {
+#pragma unroll
+        for (int q = HALF; q < KH; ++q) ys[cc * R + kh0 + q] = y[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < HALF; ++q) ys[cc * R + kh0 + q] = y[q];
       }
+      __syncthreads();
+      if (owner) {
+#pragma unroll
+        for (int q = 0; q < HALF; ++q) {
+          y[q] += ys[cc * R + kh0 + q];
+          update_rank(q);
+        }
+      } else {
+#pragma unroll
+        for (int q = HALF; q < KH; ++q) {
+          y[q] += ys[cc * R + kh0 + q];
+          update_rank(q);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < KH; ++q) update_rank(q);
     }
     fence_proxy_async_smem();
     tc_fence_before();
