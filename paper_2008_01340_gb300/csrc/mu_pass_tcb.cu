@@ -32,18 +32,8 @@
 // earlier, has then completed too), and overlaps the epilogue and phase B.
 // Every wait is bounded; on expiry the kernel sets the status word, drains
 // its MMAs and copies, frees its TMEM and returns.
-//
-// Split form (FP32 X, 128/256 rows): the unfolding is first split once per
-// stage into two BF16 matrices X1 = bf16(X), X2 = bf16(X - X1) (16
-// significand bits of X; the same HBM bytes per iteration as FP32 X).  A tile
-// then covers 64 columns: its first 64-column atom holds X1 and the second X2,
-// so phase A (M = 128 over both atoms) leaves X1^T W in TMEM lanes c and
-// X2^T W in lanes 64 + c, summed in the epilogue, and phase B (K = 128 over
-// both atoms, the H_new terms written into both atoms of the stack) sums
-// (X1 + X2) H_new^T; Q = H_new H_new^T runs over the first atom only.
-#include <cstring>
 
-#include "ntt_internal.cuh"
+#include "tc_bf16.cuh"
 
 namespace ntt {
 
@@ -51,47 +41,12 @@ namespace {
 
 constexpr int kTbThreads = 256;
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// Instruction descriptor of kind::f16 with BF16 A and B and FP32 D.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Byte offset of BF16 element (row, col) in a tile of `rows` rows kept as
-// 64-column atoms of 128-byte rows, 16-byte chunks swizzled over 8 rows.
-__device__ __forceinline__ uint32_t swz(int row, int col, int rows) {
-  return (uint32_t)((col >> 6) * rows * 128 + row * 128 + ((((col >> 3) & 7) ^ (row & 7)) << 4) +
-                    ((col & 7) << 1));
-}
-
-__device__ __forceinline__ void split3(float a, __nv_bfloat16* t) {
-  const __nv_bfloat16 a1 = __float2bfloat16_rn(a);
-  const float r1 = a - __bfloat162float(a1);
-  const __nv_bfloat16 a2 = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(a2);
-  t[0] = a1;
-  t[1] = a2;
-  t[2] = __float2bfloat16_rn(r2);
-}
-
-template <int MP_, int R_, bool SPLIT_ = false>
+template <int MP_, int R_>
 struct TbCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
-  static constexpr bool SPLIT = SPLIT_;            // X = X1 + X2 in two BF16 matrices
   static constexpr int T = 128;                    // tile width in shared memory (MMA M of phase A)
-  static constexpr int TC = SPLIT ? 64 : T;        // columns of X per tile
-  static constexpr int FLUSH = 2048 / TC;          // tiles per TMEM accumulation run of D_B
+  static constexpr int FLUSH = 2048 / T;           // tiles per TMEM accumulation run of D_B
   static constexpr int N3 = 3 * R;                 // MMA N: three terms of R ranks
   static constexpr int KH = R / 2;                 // ranks per thread in the epilogue
   // Stacked form (MP <= 32): a stage holds 128 rows, X in rows 0..MP-1 and the
@@ -113,18 +68,13 @@ struct TbCfg {
   static constexpr int OFF_W = OFF_HN + HNS;
   static constexpr int OFF_G = OFF_W + WOP;
   static constexpr int OFF_QS = OFF_G + R * R * 4;   // 3R x R scratch of the Q term rows
-  // split form: X2 parts of Y (64 x R); they share the Q term scratch when it is
-  // large enough (the flush that uses it and the epilogue never overlap)
-  static constexpr bool YS_IN_QS = 3 * R * R >= 64 * R;
-  static constexpr int OFF_YS = YS_IN_QS ? OFF_QS : OFF_QS + 3 * R * R * 4;
-  static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4 + (SPLIT && !YS_IN_QS ? 64 * R * 4 : 0);
+  static constexpr int OFF_BAR = OFF_QS + 3 * R * R * 4;
   static constexpr int USED = OFF_BAR + 64;
   static constexpr int SMEM = USED + 1024;         // + alignment of the 1024-byte atoms
   static constexpr uint32_t TMEM_COLS = STACK ? 256 : 512;   // D_A (N3) + D_B ((NMB + 1) N3)
   static constexpr uint32_t IDA = idesc_bf16(128, N3, true, false);
   static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
   static_assert((MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
-  static_assert(!SPLIT || !STACK, "the split form needs a separate H_new stack");
   static_assert(!STACK || MP + 3 * R <= 128, "stacked rows fit one M block");
   static_assert(N3 * (NMB + 2) <= (int)TMEM_COLS, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -133,7 +83,6 @@ struct TbCfg {
 
 struct TbParams {
   const __nv_bfloat16* X;   // m x n BF16, row stride n (n % 8 == 0, 16-byte aligned)
-  const __nv_bfloat16* X2;  // split form: the second term X - X1 (same layout)
   float* H;                 // r x n FP32, updated in place
   const float* W;           // m x r
   const float* G;           // R x R
@@ -145,12 +94,8 @@ struct TbParams {
   float eps;
 };
 
-// tmX1 / tmX2: split form only, TMA maps of X1 and X2 (64-column boxes of SR
-// rows, 128-byte swizzle: the layout of a tile's two atoms).
 template <class C>
-__global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid_constant__ CUtensorMap tmX1,
-                                                                    const __grid_constant__ CUtensorMap tmX2,
-                                                                    const TbParams p) {
+__global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbParams p) {
   constexpr int MP = C::MP, R = C::R, T = C::T, N3 = C::N3, KH = C::KH;
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
@@ -188,10 +133,6 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
     s_err = 0;
     mbar_init(barA, 1);
     mbar_init(barB, 1);
-    if constexpr (C::SPLIT) {
-      mbar_init(smem_u32(&bars[2]), 1);   // TMA stage barriers of the split form
-      mbar_init(smem_u32(&bars[3]), 1);
-    }
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -208,30 +149,15 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
 
   // ---- X tile loader: rows < m, 8 BF16 values per 16-byte copy, zero fill past
   // n; tiles past the CTA's range issue nothing but still commit a group
-  int tma_issued = 0;   // split form: tiles whose TMA copies thread 0 has issued
   auto issue = [&](int stage, int tile, bool valid) {
     uint8_t* dst = smem + C::OFF_X + stage * C::XST;
-    const int64_t col0 = (int64_t)tile * C::TC;
-    if constexpr (C::SPLIT) {
-      // X1 into the tile's first atom, X2 into its second: two copies on the
-      // stage's barrier (rows past m and columns past n arrive as zeros)
-      if (tid == 0 && valid) {
-        const uint32_t bar = smem_u32(&bars[2 + stage]);
-        mbar_arrive_expect_tx(bar, (uint32_t)(2 * C::SR * 64 * 2));
-        tma_load_2d(smem_u32(dst), &tmX1, (int)col0, 0, bar);
-        tma_load_2d(smem_u32(dst + C::SR * 128), &tmX2, (int)col0, 0, bar);
-        ++tma_issued;
-      }
-      return;
-    }
+    const int64_t col0 = (int64_t)tile * T;
     for (int e = tid; valid && e < m * (T / 8); e += kTbThreads) {
       const int row = e / (T / 8), ch = e % (T / 8);
-      // split form: chunks 0..7 from X1, 8..15 from X2 (the same 64 columns)
-      const int term = C::SPLIT ? ch / 8 : 0;
-      const int64_t col = col0 + 8 * (C::SPLIT ? ch % 8 : ch);
+      const int64_t col = col0 + 8 * ch;
       const int64_t left = n - col;
       const int bytes = left >= 8 ? 16 : (left > 0 ? (int)left * 2 : 0);
-      const __nv_bfloat16* src = (term ? p.X2 : p.X) + (int64_t)row * n + (bytes ? col : 0);
+      const __nv_bfloat16* src = p.X + (int64_t)row * n + (bytes ? col : 0);
       const uint32_t off = swz(row, 8 * ch, C::SR);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + off)), "l"(src),
                    "r"(bytes)
@@ -244,11 +170,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   const uint64_t dW = smem_desc(sbase + C::OFF_W, 16, 1024, kLayoutSw128);
   const uint64_t dH = smem_desc(sbase + C::OFF_HN, 16, 1024, kLayoutSw128);
 
-  // epilogue role: TMEM lane c, ranks kh0 .. kh0 + KH - 1; the tile column is
-  // c (split form: c % 64, lanes 64.. holding the X2 part of the same column)
+  // epilogue role: TMEM lane = tile column c, ranks kh0 .. kh0 + KH - 1
   const int c = (warp % 4) * 32 + lane;
-  const int cc = C::SPLIT ? c % 64 : c;
-  const bool owner = !C::SPLIT || c < 64;   // split form: the thread of the X1 lane of its column
   const int kh0 = (warp / 4) * KH;
   const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
 
@@ -256,7 +179,6 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   float* out = p.part + (size_t)blockIdx.x * ((MP + R) * R);
   for (int e = tid; e < (MP + R) * R; e += kTbThreads) out[e] = 0.0f;
   float* qs = reinterpret_cast<float*>(smem + C::OFF_QS);
-  float* ys = reinterpret_cast<float*>(smem + C::OFF_YS);   // split form: X2 parts of Y
   // Add the finished TMEM run of D_B: P rows (X blocks) straight into `out`
   // (each entry owned by one thread), Q through the term sums in `qs`.
   auto flush = [&]() {
@@ -301,7 +223,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   // the current tile
   constexpr bool PREFETCH_H = R <= 16;
   auto load_h = [&](int tile_, float* hv) {
-    const int64_t col_ = (int64_t)tile_ * C::TC + cc;
+    const int64_t col_ = (int64_t)tile_ * T + c;
 #pragma unroll
     for (int l = 0; l < R; ++l) hv[l] = (l < r && col_ < n) ? p.H[(int64_t)l * n + col_] : 0.0f;
   };
@@ -314,13 +236,9 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   for (; j < count; ++j) {
     const int s = j % C::STAGES;
     const int tile = (int)blockIdx.x + j * (int)gridDim.x;
-    const int64_t col = (int64_t)tile * C::TC + cc;
-    if constexpr (C::SPLIT) {
-      if (!mbar_wait_bounded(smem_u32(&bars[2 + s]), (uint32_t)((j / C::STAGES) & 1))) s_err = 1;
-    } else {
-      asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
-      fence_proxy_async_smem();
-    }
+    const int64_t col = (int64_t)tile * T + c;
+    asm volatile("cp.async.wait_group %0;" ::"n"(C::STAGES - 2) : "memory");
+    fence_proxy_async_smem();
     __syncthreads();
     if (s_err) break;
     // ---- phase A
@@ -369,7 +287,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
       }
     }
     tc_fence_before();
-    // H update of column cc, rank kh0 + q: H_new to HBM and its three BF16
+    // H update of column c, rank kh0 + q: H_new to HBM and its three BF16
     // terms into the H_new stack
     auto update_rank = [&](int q) {
       const int k = kh0 + q;
@@ -382,10 +300,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
         gh = fmaf(g.z, h[l + 2], gh);
         gh = fmaf(g.w, h[l + 3], gh);
       }
-      float hk = 0.0f;
-#pragma unroll
-      for (int l = 0; l < R; ++l)
-        if (l == k) hk = h[l];
+      const float hk = warp >= 4 ? h[KH + q] : h[q];
       const float hn = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
       if (k < r && col < n) p.H[(int64_t)k * n + col] = hn;
       __nv_bfloat16 t3[3];
@@ -393,39 +308,10 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
 #pragma unroll
       for (int t = 0; t < 3; ++t)
         *reinterpret_cast<__nv_bfloat16*>(smem + (C::STACK ? C::OFF_X + s * C::XST : C::OFF_HN) +
-                                          swz(C::HROW0 + t * R + k, cc, C::HSR)) = t3[t];
+                                          swz(C::HROW0 + t * R + k, c, C::HSR)) = t3[t];
     };
-    if constexpr (C::SPLIT) {
-      // Y = X1^T W (lane cc) + X2^T W (lane 64 + cc).  The two threads of a
-      // column share its ranks: the X1 lane's thread takes the first half of
-      // kh0 .. kh0 + KH, the X2 lane's thread the second; each hands the other
-      // its part of the other half through shared memory.
-      constexpr int HALF = KH / 2;
-      if (owner) {
 #pragma unroll
-        for (int q = HALF; q < KH; ++q) ys[cc * R + kh0 + q] = y[q];
-      } else {
-#pragma unroll
-        for (int q = 0; q < HALF; ++q) ys[cc * R + kh0 + q] = y[q];
-      }
-      __syncthreads();
-      if (owner) {
-#pragma unroll
-        for (int q = 0; q < HALF; ++q) {
-          y[q] += ys[cc * R + kh0 + q];
-          update_rank(q);
-        }
-      } else {
-#pragma unroll
-        for (int q = HALF; q < KH; ++q) {
-          y[q] += ys[cc * R + kh0 + q];
-          update_rank(q);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < KH; ++q) update_rank(q);
-    }
+    for (int q = 0; q < KH; ++q) update_rank(q);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -442,14 +328,12 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
           mma_bf16(dB(0), smem_desc(base, 16, 1024, kLayoutSw128),
                    smem_desc(base + C::HROW0 * 128, 16, 1024, kLayoutSw128), C::IDB, acc);
         } else {
-          // split form: the X2 atom's K steps read the same H_new columns (atom 0)
-          const uint32_t ho = (uint32_t)((C::SPLIT ? 0 : (kk >> 2)) * C::HROWS * 128 + (kk & 3) * 32);
+          const uint32_t ho = (uint32_t)((kk >> 2) * C::HROWS * 128 + (kk & 3) * 32);
 #pragma unroll
           for (int mb = 0; mb < C::NMB; ++mb)
             mma_bf16(dB(mb), smem_desc(sbase + C::OFF_X + s * C::XST + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128),
                      dH + (uint64_t)(ho >> 4), C::IDB, acc);
-          // Q once per column: the split form's second atom repeats the H terms
-          if (!C::SPLIT || kk < 4) mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
+          mma_bf16(dB(C::NMB), dH + (uint64_t)(ho >> 4), dH + (uint64_t)(ho >> 4), C::IDB, acc);
         }
       }
       mma_commit(barB);
@@ -459,12 +343,6 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const __grid
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (count > 0 && !s_err) {
     if (!mbar_wait_bounded(barB, (uint32_t)((count - 1) & 1))) s_err = 1;
-  }
-  if constexpr (C::SPLIT) {
-    // TMA copies still in flight (issued, not yet waited for): drain them (bounded)
-    if (s_err && tid == 0)
-      for (int c2 = j; c2 < tma_issued; ++c2)
-        (void)mbar_wait_bounded(smem_u32(&bars[2 + c2 % C::STAGES]), (uint32_t)((c2 / C::STAGES) & 1));
   }
   if (s_err && tid == 0) {
     // MMAs may still be in flight: phase A of tile j and phase B of tile j - 1 (bounded)
@@ -507,18 +385,9 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.n = s.n;
   p.m = (int)s.m;
   p.r = s.r;
-  p.ntiles = (int)((s.n + C::TC - 1) / C::TC);
+  p.ntiles = (int)((s.n + C::T - 1) / C::T);
   p.eps = eps;
-  p.X2 = reinterpret_cast<const __nv_bfloat16*>(d.X2);
-  CUtensorMap m1, m2;
-  std::memset(&m1, 0, sizeof(m1));
-  std::memset(&m2, 0, sizeof(m2));
-  if constexpr (C::SPLIT) {
-    if (encode_bf16_atom_map(d.X, s.m, s.n, C::SR, &m1) != NTT_OK ||
-        encode_bf16_atom_map(d.X2, s.m, s.n, C::SR, &m2) != NTT_OK)
-      return cudaErrorInvalidValue;
-  }
-  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(m1, m2, p);
+  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -526,16 +395,6 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
 
 bool tcb_pass_supported(int MP, int R) {
   return (MP == 16 || MP == 32 || MP == 128 || MP == 256) && (R == 16 || R == 32);
-}
-
-bool tcs_pass_supported(int MP, int R) { return (MP == 128 || MP == 256) && (R == 16 || R == 32); }
-
-cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
-  if (s.MP == 128 && s.R == 16) return launch_tcb_cfg<TbCfg<128, 16, true>>(s, d, eps, st);
-  if (s.MP == 128 && s.R == 32) return launch_tcb_cfg<TbCfg<128, 32, true>>(s, d, eps, st);
-  if (s.MP == 256 && s.R == 16) return launch_tcb_cfg<TbCfg<256, 16, true>>(s, d, eps, st);
-  if (s.MP == 256 && s.R == 32) return launch_tcb_cfg<TbCfg<256, 32, true>>(s, d, eps, st);
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
