@@ -188,9 +188,21 @@ __device__ __forceinline__ void mu_pass_body(const CUtensorMap& tmX, const CUten
     }
   }
   // W (zero padded to MP x R), G (R x R), zero padding rows of both H_new stacks
-  for (int idx = tid; idx < MP * R; idx += NT) {
-    const int i = idx / R, k = idx % R;
-    Ws[idx] = (i < m && k < r) ? p.W[i * r + k] : 0.0f;
+  {
+    // W loads in batches of eight in flight
+    constexpr int NWL = (MP * R + NT - 1) / NT, WB = NWL < 8 ? NWL : 8;
+#pragma unroll 1
+    for (int u0 = 0; u0 < NWL; u0 += WB) {
+      float wv[WB];
+#pragma unroll
+      for (int u = 0; u < WB; ++u) {
+        const int idx = tid + (u0 + u) * NT, i = idx / R, k = idx % R;
+        wv[u] = (idx < MP * R && i < m && k < r) ? p.W[i * r + k] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < WB; ++u)
+        if (tid + (u0 + u) * NT < MP * R) Ws[tid + (u0 + u) * NT] = wv[u];
+    }
   }
   for (int idx = tid; idx < R * R; idx += NT) Gs[idx] = p.G[idx];
   for (int b = 0; b < 2; ++b)

@@ -115,9 +115,20 @@ __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbPara
   // ---- setup: zero the X stages and the H_new stack, W terms, G, barriers, TMEM
   for (int i = tid; i < (C::OFF_W) / 16; i += kTbThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < MP * R; e += kTbThreads) {
+  // all of a thread's W loads in flight at once, then the splits
+  constexpr int NWL = (MP * R + kTbThreads - 1) / kTbThreads;
+  float wv[NWL];
+#pragma unroll
+  for (int u = 0; u < NWL; ++u) {
+    const int e = tid + u * kTbThreads, i = e / R, k = e % R;
+    wv[u] = (e < MP * R && i < m && k < r) ? p.W[i * r + k] : 0.0f;
+  }
+#pragma unroll
+  for (int u = 0; u < NWL; ++u) {
+    const int e = tid + u * kTbThreads;
+    if (e >= MP * R) break;
     const int i = e / R, k = e % R;   // W row i (K index), rank k
-    const float w = (i < m && k < r) ? p.W[i * r + k] : 0.0f;
+    const float w = wv[u];
     __nv_bfloat16 t3[3];
     split3(w, t3);
 #pragma unroll

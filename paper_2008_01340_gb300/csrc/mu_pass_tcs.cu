@@ -1,5 +1,6 @@
 // Fused MU pass for FP32 X on the BF16 tensor cores (the split form), for
-// unfoldings of 128 or 256 rows at rank buckets 16 and 32.
+// unfoldings of 128 or 256 rows at rank buckets 16 and 32 and of 512 rows at
+// rank bucket 16.
 //
 // The unfolding is split once per stage into two BF16 matrices X1 = bf16(X)
 // and X2 = bf16(X - X1) (16 significand bits of X; the same HBM bytes per
@@ -25,7 +26,10 @@
 // issues every MMA; warp 9 lane 0 issues the TMA copies.  D_A and the H_new
 // stack are double-buffered, so the epilogue of tile j runs while the tensor
 // pipe does phase B of tile j-1 and phase A of tile j+1, and the copies of
-// later tiles fill the other X stages (three at 256 rows and rank 16).
+// later tiles fill the other X stages (three at 256 rows and rank 16).  At
+// 512 rows a stage takes 128 KB and only one fits: phase A of a tile then
+// waits for phase B of the previous one (the X of a 512-row unfolding of the
+// sizes routed here is resident in L2).
 // Hand-offs are mbarriers:
 //   full[s]   copies of stage s landed        -> MMA thread
 //   empty[s]  phase B of stage s's tile done  -> TMA thread
@@ -37,6 +41,7 @@
 // its MMAs and the TMA thread for its copies, TMEM is freed, the partials are
 // zeroed and the status word is set.
 #include <cstring>
+#include <type_traits>
 
 #include "tc_bf16.cuh"
 
@@ -66,6 +71,7 @@ struct TsCfg {
   static constexpr int FIXED = 2 * HS + WOP + R * R * 4 + BARB + 1024;
   static constexpr int FIT = (227 * 1024 - FIXED) / XST;
   static constexpr int S = FIT < 6 ? FIT : 6;   // X stages
+  static constexpr int BOXR = MP < 256 ? MP : 256; // TMA box rows (two boxes per atom at 512 rows)
   // The stacks come first: the 128-row A operand of the Q MMA reads past a
   // stack's 3R rows into the following shared memory; those rows only reach
   // TMEM lanes >= 3R, which are never read.
@@ -80,8 +86,8 @@ struct TsCfg {
   static constexpr uint32_t IDA = idesc_bf16(128, N2, true, false);
   static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
   static constexpr uint32_t TX = 2u * MP * 128u;   // bytes of one stage's two copies
-  static_assert((MP == 128 || MP == 256) && (R == 16 || R == 32), "bucket");
-  static_assert(S >= 2 && SMEM <= 227 * 1024, "shared memory");
+  static_assert(((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16), "bucket");
+  static_assert(S >= 1 && SMEM <= 227 * 1024, "shared memory");
   static_assert(TMEM_USED <= 512, "TMEM columns");
   static_assert(HS % 1024 == 0 && OFF_X % 1024 == 0 && OFF_W % 1024 == 0 && (N2 * 128) % 1024 == 0,
                 "atom alignment");
@@ -161,9 +167,20 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
 
   // ---- setup: W terms (K-major B operand of phase A), G, barriers, TMEM,
   // this CTA's partial block zeroed
-  for (int e = tid; e < MP * R; e += kTsThreads) {
+  // all of a thread's W loads in flight at once, then the splits
+  constexpr int NWL = (MP * R + kTsThreads - 1) / kTsThreads;
+  float wv[NWL];
+#pragma unroll
+  for (int u = 0; u < NWL; ++u) {
+    const int e = tid + u * kTsThreads, i = e / R, k = e % R;
+    wv[u] = (e < MP * R && i < m && k < r) ? p.W[i * r + k] : 0.0f;
+  }
+#pragma unroll
+  for (int u = 0; u < NWL; ++u) {
+    const int e = tid + u * kTsThreads;
+    if (e >= MP * R) break;
     const int i = e / R, k = e % R;   // W row i (K index), rank k
-    const float w = (i < m && k < r) ? p.W[i * r + k] : 0.0f;
+    const float w = wv[u];
     const __nv_bfloat16 w1 = __float2bfloat16_rn(w);
     const __nv_bfloat16 w2 = __float2bfloat16_rn(w - __bfloat162float(w1));
 #pragma unroll
@@ -219,8 +236,11 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         const int col0 = ((int)blockIdx.x + t * (int)gridDim.x) * C::TC;
         const uint32_t dst = sbase + C::OFF_X + s * C::XST;
         mbar_arrive_expect_tx(full(s), C::TX);
-        tma_load_2d(dst, &tmX1, col0, 0, full(s));
-        tma_load_2d(dst + MP * 128, &tmX2, col0, 0, full(s));
+#pragma unroll
+        for (int h = 0; h < MP / C::BOXR; ++h) {
+          tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
+          tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX2, col0, h * C::BOXR, full(s));
+        }
       }
       // every copy issued has landed before the CTA ends (the last one of each stage)
       for (int u = t - S < 0 ? 0 : t - S; u < t; ++u) (void)mbar_wait_bounded(full(u % S), (uint32_t)((u / S) & 1));
@@ -265,21 +285,34 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         mma_commit(empty(s));
         mma_commit(bdone);
       };
-      if (wait(full(0), 0u)) {
-        tc_fence_after();
-        phase_a(0, 0);
-      }
-      for (int j = 0; ok && j < count; ++j) {
-        if (j + 1 < count) {
-          // D_A[(j+1) & 1] was read by the epilogue of tile j - 1 (waited for below, one round earlier)
-          if (!wait(full((j + 1) % S), (uint32_t)(((j + 1) / S) & 1))) break;
+      if constexpr (S == 1) {
+        // one stage: phase A of tile j after phase B of tile j - 1 has freed it
+        for (int j = 0; ok && j < count; ++j) {
+          if (!wait(full(0), (uint32_t)(j & 1))) break;
           tc_fence_after();
-          phase_a(j + 1, (j + 1) % S);
+          phase_a(j, 0);
+          if (!wait(epi(j & 1), (uint32_t)((j >> 1) & 1))) break;
+          tc_fence_after();
+          phase_b(j, 0);
+          if (read_flag(s_err)) break;
         }
-        if (!wait(epi(j & 1), (uint32_t)((j >> 1) & 1))) break;
-        tc_fence_after();
-        phase_b(j, j % S);
-        if (read_flag(s_err)) break;
+      } else {
+        if (wait(full(0), 0u)) {
+          tc_fence_after();
+          phase_a(0, 0);
+        }
+        for (int j = 0; ok && j < count; ++j) {
+          if (j + 1 < count) {
+            // D_A[(j+1) & 1] was read by the epilogue of tile j - 1 (waited for below, one round earlier)
+            if (!wait(full((j + 1) % S), (uint32_t)(((j + 1) / S) & 1))) break;
+            tc_fence_after();
+            phase_a(j + 1, (j + 1) % S);
+          }
+          if (!wait(epi(j & 1), (uint32_t)((j >> 1) & 1))) break;
+          tc_fence_after();
+          phase_b(j, j % S);
+          if (read_flag(s_err)) break;
+        }
       }
       // every MMA issued has completed before TMEM is released
       mma_commit(drain);
@@ -306,6 +339,18 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
     float hnext[PREFETCH_H ? R : 1];
     if constexpr (PREFETCH_H) {
       if (count > 0) load_h((int)blockIdx.x, hnext);
+    }
+    // rank bucket 16: the G rows of this thread's ranks in registers (their
+    // shared-memory reads otherwise take a large share of the pass's
+    // shared-memory bandwidth, which the MMA operands need)
+    constexpr bool GREG = R <= 16;
+    float gk[GREG ? HALF : 1][GREG ? R : 1];
+    if constexpr (GREG) {
+      const int kq = kh0 + (owner ? 0 : HALF);
+#pragma unroll
+      for (int qi = 0; qi < HALF; ++qi)
+#pragma unroll
+        for (int l = 0; l < R; ++l) gk[qi][l] = Gs[(kq + qi) * R + l];
     }
     // Add the finished TMEM run of D_B: P rows straight into `out` (each
     // entry owned by one thread), Q through its term rows in `qs`.
@@ -400,32 +445,47 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
       epi_sync();   // the exchange area is the stack, written next
       // H update of column cc, rank kh0 + q: H_new to HBM, its three BF16
       // terms into the stack
-      auto update_rank = [&](int q) {
-        const int k = kh0 + q;
-        float gh = 0.0f;
+      // H update of column cc at this thread's ranks kh0 + Q0 + qi: all of
+      // them first (independent chains), then H_new to HBM and its three BF16
+      // terms into the stack
+      auto update_half = [&](auto q0c) {
+        constexpr int Q0 = decltype(q0c)::value;
+        float hn[HALF];
 #pragma unroll
-        for (int l = 0; l < R; l += 4) {
-          const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
-          gh = fmaf(g.x, h[l], gh);
-          gh = fmaf(g.y, h[l + 1], gh);
-          gh = fmaf(g.z, h[l + 2], gh);
-          gh = fmaf(g.w, h[l + 3], gh);
+        for (int qi = 0; qi < HALF; ++qi) {
+          const int q = Q0 + qi;
+          float gh = 0.0f;
+          if constexpr (GREG) {
+#pragma unroll
+            for (int l = 0; l < R; ++l) gh = fmaf(gk[qi][l], h[l], gh);
+          } else {
+            const int k = kh0 + q;
+#pragma unroll
+            for (int l = 0; l < R; l += 4) {
+              const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
+              gh = fmaf(g.x, h[l], gh);
+              gh = fmaf(g.y, h[l + 1], gh);
+              gh = fmaf(g.z, h[l + 2], gh);
+              gh = fmaf(g.w, h[l + 3], gh);
+            }
+          }
+          const float hk = hi ? h[KH + q] : h[q];
+          hn[qi] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
         }
-        const float hk = hi ? h[KH + q] : h[q];
-        const float hn = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
-        if (k < r && col < n) p.H[(int64_t)k * n + col] = hn;
-        __nv_bfloat16 t3[3];
-        split3(hn, t3);
 #pragma unroll
-        for (int t = 0; t < 3; ++t) *reinterpret_cast<__nv_bfloat16*>(stk + swz(t * R + k, cc, N3)) = t3[t];
+        for (int qi = 0; qi < HALF; ++qi) {
+          const int k = kh0 + Q0 + qi;
+          if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[qi];
+          __nv_bfloat16 t3[3];
+          split3(hn[qi], t3);
+#pragma unroll
+          for (int t = 0; t < 3; ++t) *reinterpret_cast<__nv_bfloat16*>(stk + swz(t * R + k, cc, N3)) = t3[t];
+        }
       };
-      if (owner) {
-#pragma unroll
-        for (int q = 0; q < HALF; ++q) update_rank(q);
-      } else {
-#pragma unroll
-        for (int q = HALF; q < KH; ++q) update_rank(q);
-      }
+      if (owner)
+        update_half(std::integral_constant<int, 0>{});
+      else
+        update_half(std::integral_constant<int, HALF>{});
       fence_proxy_async_smem();
       tc_fence_before();
       mbar_arrive(epi(b));
@@ -477,8 +537,8 @@ cudaError_t launch_tcs_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   CUtensorMap m1, m2;
   std::memset(&m1, 0, sizeof(m1));
   std::memset(&m2, 0, sizeof(m2));
-  if (encode_bf16_atom_map(d.X, s.m, s.n, C::MP, &m1) != NTT_OK ||
-      encode_bf16_atom_map(d.X2, s.m, s.n, C::MP, &m2) != NTT_OK)
+  if (encode_bf16_atom_map(d.X, s.m, s.n, C::BOXR, &m1) != NTT_OK ||
+      encode_bf16_atom_map(d.X2, s.m, s.n, C::BOXR, &m2) != NTT_OK)
     return cudaErrorInvalidValue;
   mu_pass_tcs_kernel<C><<<s.grid, kTsThreads, C::SMEM, st>>>(m1, m2, p);
   return cudaGetLastError();
@@ -486,13 +546,16 @@ cudaError_t launch_tcs_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
 
 }  // namespace
 
-bool tcs_pass_supported(int MP, int R) { return (MP == 128 || MP == 256) && (R == 16 || R == 32); }
+bool tcs_pass_supported(int MP, int R) {
+  return ((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16);
+}
 
 cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
   if (s.MP == 128 && s.R == 16) return launch_tcs_cfg<TsCfg<128, 16>>(s, d, eps, st);
   if (s.MP == 128 && s.R == 32) return launch_tcs_cfg<TsCfg<128, 32>>(s, d, eps, st);
   if (s.MP == 256 && s.R == 16) return launch_tcs_cfg<TsCfg<256, 16>>(s, d, eps, st);
   if (s.MP == 256 && s.R == 32) return launch_tcs_cfg<TsCfg<256, 32>>(s, d, eps, st);
+  if (s.MP == 512 && s.R == 16) return launch_tcs_cfg<TsCfg<512, 16>>(s, d, eps, st);
   return cudaErrorInvalidValue;
 }
 

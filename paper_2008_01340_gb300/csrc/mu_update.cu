@@ -6,10 +6,13 @@
 //   f      <- 1/2 (||X||^2 - 2 <W, P> + <G_W, Q>)              (objective, FP64)
 //
 // The reduction is the single-GPU replacement of the all-reduce of
-// Algorithm 4 and the reduce-scatter of Algorithm 5.  Every block reduces 32
-// entries with 8 partial-chunks per entry (FP32 within a chunk, FP64 across
-// chunks, fixed order); the last block to finish (ticket counter, no spin)
-// performs the W update, the Gram and the objective and resets the ticket.
+// Algorithm 4 and the reduce-scatter of Algorithm 5.  Two launches: every
+// block of the first reduces 32 entries with 8 partial-chunks per entry (FP32
+// within a chunk, FP64 across chunks, fixed order); every block of the second
+// updates 32 rows of W and forms their share of G_W and of the objective
+// (<G_W, Q> as the sum over rows of W_i Q W_i^T), and the last block to finish
+// (ticket counter, no spin) adds the shares in block order and runs the
+// stopping test.
 #include "ntt_internal.cuh"
 
 namespace ntt {
@@ -35,6 +38,7 @@ struct CombineParams {
   int* stop;   // nullable stop word of the loop (see MuDev)
   double tol;
   int check, t0;
+  float* scratch;   // the W half's per-block partials (the pass partial buffer, consumed by then)
 };
 
 // G = W^T W (R x R, zero outside r x r) from W (m x r) by the whole block.
@@ -60,79 +64,140 @@ __device__ void gram_block(const float* W, int m, int r, int R, float* G, float*
   }
 }
 
-// W <- max(0, W o P / (W Q + eps)) for the rows of W in shared memory (in place;
-// a thread owns whole rows).  RM bounds the rank so the rank loops unroll to the
-// padded bucket; the sum over j runs in index order.  blk > 0 keeps Q's diagonal
-// blk x blk blocks only.
-template <int RM>
-__device__ __forceinline__ void w_update_rows(const float* red_s, float* Wn, int m, int r, int R, int MP,
-                                              int blk, float eps) {
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    float w[RM];
-#pragma unroll
-    for (int k = 0; k < RM; ++k) w[k] = (k < r) ? Wn[i * r + k] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < RM; ++k) {
-      if (k < r) {
-        float wq = 0.0f;
-        if (blk <= 0) {
-#pragma unroll
-          for (int j = 0; j < RM; ++j)
-            if (j < r) wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
-        } else {
-          const int g = k / blk;
-#pragma unroll
-          for (int j = 0; j < RM; ++j)
-            if (j < r && j / blk == g) wq = fmaf(w[j], red_s[(MP + j) * R + k], wq);
-        }
-        Wn[i * r + k] = fmaxf(0.0f, __fdiv_rn(w[k] * red_s[i * R + k], wq + eps));
-      }
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombineParams p) {
-  extern __shared__ float sm[];
+// [P ; Q] = sum over the pass CTAs of their partials, 32 entries per block:
+// eight chunks of CTAs summed in FP32, the chunks in FP64 pairwise (a fixed
+// order), rounded to FP32 into red.
+__global__ void __launch_bounds__(kAuxThreads) combine_reduce_kernel(const CombineParams p) {
   __shared__ float chunk[kChunks][kEntriesPerBlock];
-  __shared__ double dsh[kAuxThreads];
-  __shared__ int s_last;
   const int tid = threadIdx.x;
   const int E = (p.MP + p.R) * p.R;
   if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
-
-  // ---- 1. reduce 32 entries over all partials: 8 chunks x FP32, then FP64
-  {
-    const int el = tid % kEntriesPerBlock;
-    const int j = tid / kEntriesPerBlock;
-    const int e = blockIdx.x * kEntriesPerBlock + el;
-    const int per = (p.nb + kChunks - 1) / kChunks;
-    const int b0 = j * per;
-    const int b1 = min(p.nb, b0 + per);
-    float s = 0.0f;
-    if (e < E) {
-      // batches of eight independent loads, summed in partial order
-      constexpr int U = 8;
-      for (int bb = b0; bb < b1; bb += U) {
-        float v[U];
+  const int el = tid % kEntriesPerBlock;
+  const int j = tid / kEntriesPerBlock;
+  const int e = blockIdx.x * kEntriesPerBlock + el;
+  const int per = (p.nb + kChunks - 1) / kChunks;
+  const int b0 = j * per;
+  const int b1 = min(p.nb, b0 + per);
+  float s = 0.0f;
+  if (e < E) {
+    // batches of eight independent loads, summed in partial order
+    constexpr int U = 8;
+    for (int bb = b0; bb < b1; bb += U) {
+      float v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = bb + u < b1 ? __ldcg(&p.part[(size_t)(bb + u) * E + e]) : 0.0f;
+      for (int u = 0; u < U; ++u) v[u] = bb + u < b1 ? __ldcg(&p.part[(size_t)(bb + u) * E + e]) : 0.0f;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (bb + u < b1) s += v[u];
-      }
+      for (int u = 0; u < U; ++u)
+        if (bb + u < b1) s += v[u];
     }
-    chunk[j][el] = s;
+  }
+  chunk[j][el] = s;
+  __syncthreads();
+  if (tid < kEntriesPerBlock && e < E) {
+    double t[kChunks];
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) t[c] = (double)chunk[c][tid];
+#pragma unroll
+    for (int w = 1; w < kChunks; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < kChunks; c += 2 * w) t[c] += t[c + w];
+    p.red[e] = (float)t[0];
+  }
+}
+
+// The W half, kRowsW rows of W per block:
+//   W_i <- max(0, W_i o P_i / (W_i Q + eps))      (the sum over j in index order)
+//   G partial = sum over the block's rows of W_i^T W_i   (compensated, rows in order)
+//   objective partials  a = <W, P>_rows,  b = sum_i W_i Q W_i^T  (FP64; <G, Q> = sum_i W_i Q W_i^T)
+// and in the last block to finish (ticket): G = the partials summed in block
+// order, f = 1/2 (||X||^2 - 2 a + b) with a, b summed in block order, the
+// stopping test.  blk > 0 keeps Q's and G's diagonal blk x blk blocks only.
+// The partials live in the pass partial buffer (consumed by the reduction).
+constexpr int kRowsW = 32;
+
+__global__ void __launch_bounds__(kAuxThreads) combine_w_kernel(const CombineParams p) {
+  __shared__ float Qs[NTT_MAX_RANK * NTT_MAX_RANK];
+  __shared__ float Pb[kRowsW * NTT_MAX_RANK];
+  __shared__ float Wb[kRowsW * NTT_MAX_RANK];
+  __shared__ float Wn[kRowsW * NTT_MAX_RANK];
+  __shared__ double dsh[2 * kAuxThreads / 32];
+  __shared__ int s_last;
+  if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int m = p.m, r = p.r, R = p.R, MP = p.MP, blk = p.blk;
+  const int i0 = blockIdx.x * kRowsW;
+  const int rows = min(kRowsW, m - i0);
+  auto same = [&](int k, int l) { return blk <= 0 || k / blk == l / blk; };
+  for (int e = tid; e < r * r; e += nt) {
+    const int jj = e / r, k = e % r;
+    Qs[jj * R + k] = __ldcg(&p.red[(MP + jj) * R + k]);
+  }
+  for (int e = tid; e < rows * r; e += nt) {
+    const int i = e / r, k = e % r;
+    Pb[i * R + k] = __ldcg(&p.red[(i0 + i) * R + k]);
+    Wb[i * R + k] = p.W[(i0 + i) * r + k];
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * r; e += nt) {
+    const int i = e / r, k = e % r;
+    float wq = 0.0f;
+    for (int jj = 0; jj < r; ++jj)
+      if (same(jj, k)) wq = fmaf(Wb[i * R + jj], Qs[jj * R + k], wq);
+    const float w = fmaxf(0.0f, __fdiv_rn(Wb[i * R + k] * Pb[i * R + k], wq + p.eps));
+    Wn[i * R + k] = w;
+    p.W[(i0 + i) * r + k] = w;
+  }
+  __syncthreads();
+  float* gpart = p.scratch;
+  double* opart = reinterpret_cast<double*>(p.scratch + ((gridDim.x * R * R + 1) & ~1));
+  // G partial of the block's rows, compensated (exact products by FMA, error-free
+  // additions; Ogita, Rump & Oishi 2005): within about an ulp of W_b^T W_b
+  for (int kl = tid; kl < R * R; kl += nt) {
+    const int k = kl / R, l = kl % R;
+    float sum = 0.0f, comp = 0.0f;
+    if (k < r && l < r && same(k, l))
+      for (int i = 0; i < rows; ++i) {
+        const float a = Wn[i * R + k], b = Wn[i * R + l];
+        const float pr = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -pr);
+        const float t = __fadd_rn(sum, pr);
+        const float z = __fsub_rn(t, sum);
+        const float q = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(pr, z));
+        sum = t;
+        comp = __fadd_rn(comp, __fadd_rn(q, pe));
+      }
+    gpart[blockIdx.x * R * R + kl] = __fadd_rn(sum, comp);
+  }
+  if (p.obj) {
+    double a = 0.0, b = 0.0;
+    for (int e = tid; e < rows * r; e += nt) {
+      const int i = e / r, l = e % r;
+      float qw = 0.0f;
+      for (int k = 0; k < r; ++k)
+        if (same(k, l)) qw = fmaf(Wn[i * R + k], Qs[k * R + l], qw);
+      const double w = (double)Wn[i * R + l];
+      a += w * (double)Pb[i * R + l];
+      b += w * (double)qw;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int nw = nt / 32;
+    if ((tid & 31) == 0) {
+      dsh[tid / 32] = a;
+      dsh[nw + tid / 32] = b;
+    }
     __syncthreads();
-    if (tid < kEntriesPerBlock && e < E) {
-      // pairwise FP64 sum of the eight chunks (fixed order)
-      double t[kChunks];
-#pragma unroll
-      for (int c = 0; c < kChunks; ++c) t[c] = (double)chunk[c][tid];
-#pragma unroll
-      for (int w = 1; w < kChunks; w *= 2)
-#pragma unroll
-        for (int c = 0; c + w < kChunks; c += 2 * w) t[c] += t[c + w];
-      p.red[e] = (float)t[0];
+    if (tid == 0) {
+      double As = 0.0, Bs = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        As += dsh[w];
+        Bs += dsh[nw + w];
+      }
+      opart[2 * blockIdx.x] = As;
+      opart[2 * blockIdx.x + 1] = Bs;
     }
   }
   __threadfence();
@@ -141,74 +206,24 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-
-  // ---- 2. last block: W update, Gram, objective
-  const int m = p.m, r = p.r, R = p.R, MP = p.MP;
-  float* red_s = sm;                 // E
-  float* Wn = red_s + E;             // m * r: the current W, updated in place row by row
-  float* Gs = Wn + m * r;            // R * R
-  // [P ; Q] and W into shared memory, eight independent loads per batch
-  {
-    constexpr int U = 8;
-    const int mr = m * r;
-    for (int e0 = tid; e0 < E; e0 += U * kAuxThreads) {
-      float v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = e0 + u * kAuxThreads < E ? __ldcg(&p.red[e0 + u * kAuxThreads]) : 0.0f;
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (e0 + u * kAuxThreads < E) red_s[e0 + u * kAuxThreads] = v[u];
+  for (int kl = tid; kl < R * R; kl += nt) {
+    // the block partials in block order, compensated
+    float sum = 0.0f, comp = 0.0f;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const float v = __ldcg(&gpart[b * R * R + kl]);
+      const float t = __fadd_rn(sum, v);
+      const float z = __fsub_rn(t, sum);
+      comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(v, z)));
+      sum = t;
     }
-    for (int e0 = tid; e0 < mr; e0 += U * kAuxThreads) {
-      float v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = e0 + u * kAuxThreads < mr ? p.W[e0 + u * kAuxThreads] : 0.0f;
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (e0 + u * kAuxThreads < mr) Wn[e0 + u * kAuxThreads] = v[u];
-    }
+    p.G[kl] = __fadd_rn(sum, comp);
   }
-  __syncthreads();
-  if (R <= 8)
-    w_update_rows<8>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
-  else if (R <= 16)
-    w_update_rows<16>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
-  else
-    w_update_rows<NTT_MAX_RANK>(red_s, Wn, m, r, R, MP, p.blk, p.eps);
-  __syncthreads();
-  for (int e = tid; e < m * r; e += blockDim.x) p.W[e] = Wn[e];
-  gram_block(Wn, m, r, R, p.G, Gs, p.blk);
-  __syncthreads();
-  if (p.obj) {
-    // <W, P> by rows (two FP64 chains), <G_W, Q> by entries; one reduction of both
-    double a0 = 0.0, a1 = 0.0, b = 0.0;
-    for (int i = tid; i < m; i += blockDim.x)
-      for (int k = 0; k < r; ++k) {
-        const double t = (double)Wn[i * r + k] * (double)red_s[i * R + k];
-        if (k & 1) a1 += t; else a0 += t;
-      }
-    for (int kl = tid; kl < r * r; kl += blockDim.x) {
-      const int k = kl / r, l = kl - k * r;
-      if (p.blk <= 0 || k / p.blk == l / p.blk)
-        b += (double)Gs[k * R + l] * (double)red_s[(MP + k) * R + l];
-    }
-    double A = a0 + a1, B = b;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the warp sum
-      A += __shfl_xor_sync(0xffffffffu, A, o);
-      B += __shfl_xor_sync(0xffffffffu, B, o);
-    }
-    const int nw = blockDim.x / 32;
-    if ((tid & 31) == 0) {
-      dsh[tid / 32] = A;
-      dsh[nw + tid / 32] = B;
-    }
-    __syncthreads();
-    if (tid == 0) {
+  if (tid == 0) {
+    if (p.obj) {
       double As = 0.0, Bs = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        As += dsh[w];
-        Bs += dsh[nw + w];
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        As += __ldcg(&opart[2 * b]);
+        Bs += __ldcg(&opart[2 * b + 1]);
       }
       const double f = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
       p.obj[p.t] = f;
@@ -220,8 +235,8 @@ __global__ void __launch_bounds__(kAuxThreads) mu_combine_kernel(const CombinePa
         if (f0 - f <= p.tol * fabs(f0)) *p.stop = u;
       }
     }
+    *p.ticket = 0u;
   }
-  if (tid == 0) *p.ticket = 0u;
 }
 
 __global__ void __launch_bounds__(kAuxThreads) gram_kernel(const float* W, int m, int r, int R,
@@ -232,13 +247,6 @@ __global__ void __launch_bounds__(kAuxThreads) gram_kernel(const float* W, int m
 }  // namespace
 
 cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mu_combine_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   CombineParams p;
   p.part = d.part;
   p.nb = s.grid;
@@ -259,10 +267,15 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
   p.tol = d.tol;
   p.check = d.check;
   p.t0 = d.loop_t0;
+  p.scratch = d.part;
   const int E = s.part_stride();
-  const int blocks = (E + kEntriesPerBlock - 1) / kEntriesPerBlock;
-  const size_t smem = (size_t)(E + s.m * s.r + s.R * s.R) * sizeof(float);
-  mu_combine_kernel<<<blocks, kAuxThreads, smem, st>>>(p);
+  const int wblocks = (int)((s.m + kRowsW - 1) / kRowsW);
+  // the W half's partials fit the partial buffer the reduction has consumed
+  if ((size_t)wblocks * (s.R * s.R + 4) + 2 > (size_t)s.grid * E) return cudaErrorInvalidValue;
+  combine_reduce_kernel<<<(E + kEntriesPerBlock - 1) / kEntriesPerBlock, kAuxThreads, 0, st>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  combine_w_kernel<<<wblocks, kAuxThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
