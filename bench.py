@@ -256,7 +256,12 @@ def run_stage1_small(args):
 
     _build.build()
     route = "auto"
-    if args.case == "tcs_small":
+    if args.case == "tcn_small":
+        # stage-1 shape of the 32^6 job at 2^22 columns (FP32 X): the stacked split tensor-core form
+        m, n, r = 32, 1 << 22, 8
+        X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
+        route = "tc"
+    elif args.case == "tcs_small":
         # stage-2 shape of the 32^6 job at 2^21 columns (FP32 X): the split tensor-core form
         m, n, r = 256, 1 << 21, 16
         X = torch.from_numpy(synth.uniform_matrix((m, n), 1)).cuda()
@@ -547,7 +552,7 @@ def main():
     ap.add_argument("--engine", default="pass", choices=["pass", "group"],
                     help="stage1_small: single-problem pass or grouped engine")
     ap.add_argument("--case", default="full",
-                    choices=["full", "stage1_small", "tcb_small", "tcs_small", "stage3", "stream"],
+                    choices=["full", "stage1_small", "tcb_small", "tcs_small", "tcn_small", "stage3", "stream"],
                     help="stage1_small: MU iterations of the stage-1 shape on 32 x 4194304 "
                          "(512 MB, larger than L2) for profiler captures")
     args = ap.parse_args()
@@ -556,7 +561,7 @@ def main():
         return run_reference(args)
     if args.case == "stream":
         return run_stream(args)
-    if args.case in ("stage1_small", "tcb_small", "tcs_small", "stage3"):
+    if args.case in ("stage1_small", "tcb_small", "tcs_small", "tcn_small", "stage3"):
         return run_stage1_small(args)
     if args.workload == "c4_batched":
         return run_batched(args)

@@ -112,14 +112,18 @@ static bool tcb_enabled(int MP, int route) {
 
 static bool tc_enabled(int route) { return route == NTT_ROUTE_TC; }
 
-// FP32 X with 128 or 256 rows at rank bucket 16 or 32 (n a multiple of 8)
-// runs on the split tensor-core form (X in two BF16 matrices) where the
-// caller provides its scratch.
+// FP32 X with 128 or 256 rows at rank bucket 16 or 32, or 512 rows at rank
+// bucket 16 (n a multiple of 8), runs on the split tensor-core form (X in two
+// BF16 matrices) where the caller provides its scratch.
 bool tcs_route_ok(int64_t m, int64_t n, int r, int route) {
   if (route == NTT_ROUTE_FMA || route == NTT_ROUTE_GENERIC || route == NTT_ROUTE_GROUPED) return false;
   int MP = 16;
   while (MP < m) MP *= 2;
   const int R = r <= 8 ? 8 : (r <= 16 ? 16 : 32);
+  // at most 32 rows (the stacked form) only when asked for: the narrow FMA pass
+  // measured faster on the 32-row, rank-8 shape (0.222 vs 0.358 ms per
+  // iteration on 32 x 4,194,304)
+  if (MP <= 32 && route != NTT_ROUTE_TC) return false;
   return n % 8 == 0 && tcs_pass_supported(MP, R);
 }
 
@@ -133,7 +137,7 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->narrow = 0;
   if (!s->bf16 && s->tma && s->split_ok && tcs_route_ok(s->m, s->n, s->r, s->route)) {
     s->tcs = 1;
-    s->T = 64;
+    s->T = s->MP <= 32 ? 128 : 64;   // <= 32 rows: the stacked form's 128-column tiles
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
     int64_t grid = num_sms > 0 ? num_sms : 152;
     if (grid > ntiles) grid = ntiles;

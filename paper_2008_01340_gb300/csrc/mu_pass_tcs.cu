@@ -490,9 +490,11 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
       tc_fence_before();
       mbar_arrive(epi(b));
     }
-    // the last run
+    // the last run, once every MMA has completed (the drain commit; a parity
+    // wait on bdone could match an older phase: phase B of the last two tiles
+    // may both be outstanding here)
     if (ok && count > 0) {
-      const bool bad = !mbar_wait_bounded(bdone, (uint32_t)((count - 1) & 1));
+      const bool bad = !mbar_wait_bounded(drain, 0u);
       if (bad) *s_err = 1;
       if (!epi_any(bad)) {
         tc_fence_after();
@@ -547,10 +549,11 @@ cudaError_t launch_tcs_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
 }  // namespace
 
 bool tcs_pass_supported(int MP, int R) {
-  return ((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16);
+  return ((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16) || tcn_pass_supported(MP, R);
 }
 
 cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  if (s.MP <= 32) return launch_mu_pass_tcn(s, d, eps, st);
   if (s.MP == 128 && s.R == 16) return launch_tcs_cfg<TsCfg<128, 16>>(s, d, eps, st);
   if (s.MP == 128 && s.R == 32) return launch_tcs_cfg<TsCfg<128, 32>>(s, d, eps, st);
   if (s.MP == 256 && s.R == 16) return launch_tcs_cfg<TsCfg<256, 16>>(s, d, eps, st);

@@ -384,6 +384,10 @@ cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cuda
 // BF16 tensor-core pass, 64 columns per tile: 128 or 256 rows, rank buckets 16, 32.
 bool tcs_pass_supported(int MP, int R);
 cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
+// The split form for unfoldings of at most 32 rows (X1, X2 and the H_new terms
+// stacked in one 128-row block; 128-column tiles).
+bool tcn_pass_supported(int MP, int R);
+cudaError_t launch_mu_pass_tcn(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
 // X1 = bf16(X), X2 = bf16(X - X1) elementwise (round to nearest even).
 cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16* X2, int64_t count,
                                 cudaStream_t st);

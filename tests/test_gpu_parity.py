@@ -613,7 +613,10 @@ def test_mu_bf16_stacked_tensor_core_form(ntt, m, n, r):
                                         (200, 9000, 20, "lowrank"), (256, 64, 16, "uniform"),
                                         (130, 777 * 8, 12, "lowrank"), (256, 1 << 18, 16, "uniform"),
                                         (512, 1 << 15, 16, "lowrank"), (300, 1000 * 8, 14, "uniform"),
-                                        (512, 1 << 10, 16, "uniform")])
+                                        (512, 1 << 10, 16, "uniform"), (32, 1 << 18, 8, "uniform"),
+                                        (32, 40008, 8, "lowrank"), (20, 9000, 6, "lowrank"),
+                                        (16, 4096, 12, "uniform"), (32, 5000 * 8, 16, "lowrank"),
+                                        (32, 8, 8, "uniform")])
 def test_mu_fp32_split_tensor_core_form(ntt, m, n, r, kind):
     """FP32 X split once into bf16(X) + bf16(X - bf16(X)) on the BF16 tensor-core
     pass (route "tc"): iterates within the FP32 bound of the FP64 oracle on the
