@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(kAuxThreads) combine_reduce_kernel(const Combi
 // stopping test.  blk > 0 keeps Q's and G's diagonal blk x blk blocks only.
 // The partials live in the pass partial buffer (consumed by the reduction).
 constexpr int kRowsW = 32;
+constexpr int kMaxWBlocks = 16;   // 512 rows at most
 
 __global__ void __launch_bounds__(kAuxThreads) combine_w_kernel(const CombineParams p) {
   __shared__ float Qs[NTT_MAX_RANK * NTT_MAX_RANK];
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(kAuxThreads) combine_w_kernel(const CombinePar
   __shared__ float Wb[kRowsW * NTT_MAX_RANK];
   __shared__ float Wn[kRowsW * NTT_MAX_RANK];
   __shared__ double dsh[2 * kAuxThreads / 32];
+  __shared__ double osh[2 * kMaxWBlocks];
   __shared__ int s_last;
   if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -206,24 +208,33 @@ __global__ void __launch_bounds__(kAuxThreads) combine_w_kernel(const CombinePar
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // the other blocks' shares: every load of a thread in flight at once, then
+  // the sums in block order
+  const int nb = (int)gridDim.x;
+  for (int i = tid; p.obj && i < 2 * nb; i += nt) osh[i] = __ldcg(&opart[i]);
   for (int kl = tid; kl < R * R; kl += nt) {
-    // the block partials in block order, compensated
+    float v[kMaxWBlocks];
+#pragma unroll
+    for (int b = 0; b < kMaxWBlocks; ++b) v[b] = b < nb ? __ldcg(&gpart[b * R * R + kl]) : 0.0f;
+    // compensated sum of the block partials in block order
     float sum = 0.0f, comp = 0.0f;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const float v = __ldcg(&gpart[b * R * R + kl]);
-      const float t = __fadd_rn(sum, v);
+#pragma unroll
+    for (int b = 0; b < kMaxWBlocks; ++b) {
+      if (b >= nb) break;
+      const float t = __fadd_rn(sum, v[b]);
       const float z = __fsub_rn(t, sum);
-      comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(v, z)));
+      comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(v[b], z)));
       sum = t;
     }
     p.G[kl] = __fadd_rn(sum, comp);
   }
+  __syncthreads();
   if (tid == 0) {
     if (p.obj) {
       double As = 0.0, Bs = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        As += __ldcg(&opart[2 * b]);
-        Bs += __ldcg(&opart[2 * b + 1]);
+      for (int b = 0; b < nb; ++b) {
+        As += osh[2 * b];
+        Bs += osh[2 * b + 1];
       }
       const double f = 0.5 * (*p.xnorm2 - 2.0 * As + Bs);
       p.obj[p.t] = f;
@@ -270,6 +281,7 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
   p.scratch = d.part;
   const int E = s.part_stride();
   const int wblocks = (int)((s.m + kRowsW - 1) / kRowsW);
+  if (wblocks > kMaxWBlocks) return cudaErrorInvalidValue;
   // the W half's partials fit the partial buffer the reduction has consumed
   if ((size_t)wblocks * (s.R * s.R + 4) + 2 > (size_t)s.grid * E) return cudaErrorInvalidValue;
   combine_reduce_kernel<<<(E + kEntriesPerBlock - 1) / kEntriesPerBlock, kAuxThreads, 0, st>>>(p);

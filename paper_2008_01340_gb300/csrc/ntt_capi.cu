@@ -466,6 +466,9 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
       int eng = NTT_ENGINE_FMA_PASS;
       const ntt_status e = run_mu_iters(shp, dev, p->eps, iters, t0, st, &eng);
       if (main_loop) p->st[s].engine = eng;
+      // per iteration the pass and the combine's two launches; the split form's
+      // X1, X2 once per loop
+      launches += 3LL * iters + (eng == NTT_ENGINE_TC_SPLIT ? 1 : 0);
       return e;
     }
     if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;
@@ -478,7 +481,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
     g.xnorm2 = xnorm2;
     group_fill_tables(rt.gp, &g, ws, tab + rt.host_off);
     NTT_CUDA_TRY(launch_copy_words(ws + rt.gp.off_tables, tab_dev + rt.host_off, rt.gp.table_bytes, st));
-    launches += 3;   // table upload, ticket reset and the engine's own Gram launch
+    launches += 3 + 2LL * iters;   // table upload, ticket reset, Gram; per iteration pass and combine
     return group_launch(rt.gp, ws, ws + rt.gp.off_tables, iters, p->eps, st, t0);
   };
   if (p->solver == NTT_SOLVER_BCD) {
@@ -499,7 +502,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
     NTT_TRY(mu(S.gf32, S.f32, X, p->iters, 0));
   }
   NTT_CUDA_TRY(rec(4 * s + 3));
-  launches += 2LL * S.iters_total + (p->solver == NTT_SOLVER_BCD ? 2 : 0);
+  if (p->solver == NTT_SOLVER_BCD) launches += 2LL * S.iters_total + 2;
   // stage-end objective, direct FP64 pass: 1/2 ||X - W H||^2
   NTT_TRY(resid_into(X, 0, W, H, S.m, S.n, S.r, 1, 0.5, scal + NTT_MAX_D + s, nullptr,
                      reinterpret_cast<double*>(ws + p->off_part64), tickets + 1, st));
