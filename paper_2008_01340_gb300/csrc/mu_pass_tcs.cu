@@ -91,7 +91,7 @@ struct TsCfg {
   static_assert(TMEM_USED <= 512, "TMEM columns");
   static_assert(HS % 1024 == 0 && OFF_X % 1024 == 0 && OFF_W % 1024 == 0 && (N2 * 128) % 1024 == 0,
                 "atom alignment");
-  static_assert(3 * R * R * 4 <= HS && 64 * R * 4 <= HS, "scratch in an H_new stack");
+  static_assert(3 * R * R * 4 <= HS && 64 * (R + 1) * 4 <= HS, "scratch in an H_new stack");
   static_assert(OFF_HN + HS + 128 * 128 <= OFF_W, "Q operand rows past a stack stay in shared memory");
   static_assert(2 * 6 + 6 <= BARB / 8 - 2, "barrier slots");
 };
@@ -426,21 +426,22 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
       tc_fence_before();
       // Y = X1 part (lane cc) + X2 part (lane 64 + cc): the X1 lane's thread
       // updates the first HALF ranks of the group, the X2 lane's thread the
-      // rest; each hands the other its part of the other half
+      // rest; each hands the other its part of the other half (rows of R + 1
+      // floats: consecutive columns fall in different banks)
       if (owner) {
 #pragma unroll
-        for (int q = HALF; q < KH; ++q) scratch[cc * R + kh0 + q] = y[q];
+        for (int q = HALF; q < KH; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < HALF; ++q) scratch[cc * R + kh0 + q] = y[q];
+        for (int q = 0; q < HALF; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
       }
       epi_sync();
       if (owner) {
 #pragma unroll
-        for (int q = 0; q < HALF; ++q) y[q] += scratch[cc * R + kh0 + q];
+        for (int q = 0; q < HALF; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
       } else {
 #pragma unroll
-        for (int q = HALF; q < KH; ++q) y[q] += scratch[cc * R + kh0 + q];
+        for (int q = HALF; q < KH; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
       }
       epi_sync();   // the exchange area is the stack, written next
       // H update of column cc, rank kh0 + q: H_new to HBM, its three BF16
