@@ -189,6 +189,29 @@ ntt_status ntt_plan_workspace_size_host(ntt_plan plan, size_t* bytes);
 ntt_status ntt_decompose(ntt_plan plan, const float* A, float* const* cores,
                          void* workspace, void* stream);
 
+/* Stage-level checkpoint and resume (the paper keeps the tensor and the
+ * intermediate factors in a store between the stages of Algorithm 2,
+ * Section III-B).  Runs stages s0 .. s1-1 of the plan (0 <= s0 < s1 <= d-1;
+ * stage s computes core s and the next unfolding) on `stream`, without a
+ * graph:
+ *   X_in   device FP32: A when s0 == 0, else the unfolding H_{s0}
+ *          (ntt_unfolding_size floats, r_{s0} x n_{s0}, row-major) that an
+ *          earlier call returned in H_out;
+ *   cores  device pointers of all d cores; cores s0 .. s1-1 are written (and
+ *          core d-1 when s1 == d-1), the others are not touched;
+ *   H_out  device FP32 (nullable when s1 == d-1): receives H_{s1}, the input
+ *          of a later call with s0 = s1.
+ * Stage s draws its initial factors from (seed, s) only, so the cores of
+ * runs split at any stages are bitwise those of one ntt_decompose call.
+ * Plans with the rank rule (ranks == NULL) return NTT_ERR_UNSUPPORTED.
+ * The stage statistics cover the stages of the last call. */
+ntt_status ntt_decompose_stages(ntt_plan plan, int s0, int s1, const float* X_in, float* const* cores,
+                                float* H_out, void* workspace, void* stream);
+
+/* Floats of the unfolding H_s that stage s reads (1 <= s <= d-2):
+ * r_s x prod_{j >= s} n_j. */
+ntt_status ntt_unfolding_size(ntt_plan plan, int s, int64_t* floats);
+
 /* Same as ntt_decompose with A and the cores in HOST memory: A is copied to
  * the workspace, the decomposition runs, the cores are copied back, all on
  * `stream` (asynchronous with pinned host memory; sync before reading).

@@ -51,7 +51,8 @@ def _route(route):
 # Every symbol include/ntt.h declares.
 EXPORTS = (
     "ntt_status_string", "ntt_version", "ntt_plan_create", "ntt_plan_workspace_size",
-    "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host",
+    "ntt_plan_workspace_size_host", "ntt_decompose", "ntt_decompose_host", "ntt_decompose_stages",
+    "ntt_unfolding_size",
     "ntt_plan_get_stats", "ntt_plan_destroy", "nmf_mu_workspace_size", "nmf_mu_step",
     "nmf_mu_step_route", "nmf_mu_workspace_size_route", "ntt_wait_probe", "ntt_plan_get_ranks", "ntt_rank_workspace_size",
     "ntt_singular_values", "ntt_select_rank", "nmf_bcd_workspace_size", "nmf_bcd_step",
@@ -162,6 +163,8 @@ def lib():
     L.ntt_plan_workspace_size_host.argtypes = [vp, psz]
     L.ntt_decompose.argtypes = [vp, vp, ctypes.POINTER(vp), vp, vp]
     L.ntt_decompose_host.argtypes = [vp, vp, ctypes.POINTER(vp), vp, vp, vp]
+    L.ntt_decompose_stages.argtypes = [vp, i32, i32, vp, ctypes.POINTER(vp), vp, vp, vp]
+    L.ntt_unfolding_size.argtypes = [vp, i32, p64]
     L.ntt_plan_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     L.ntt_plan_destroy.argtypes = [vp]
     L.nmf_mu_workspace_size.argtypes = [i64, i64, i32, i32, psz]
@@ -254,6 +257,7 @@ class Plan:
     x_dtype: str
     refine_iters: int
     max_ranks: tuple = None
+    seed: int = 0
 
     def workspace_size(self):
         n = ctypes.c_size_t(0)
@@ -327,6 +331,7 @@ def ntt_plan_create(dims, ranks, iters, eps_mu=1e-12, x_dtype="f32", refine_iter
     _check(lib().ntt_plan_create(ctypes.byref(desc), ctypes.byref(h)), "ntt_plan_create")
     plan = Plan(h, dims, ranks, int(iters), x_dtype, int(refine_iters))
     plan.max_ranks = plan.current_ranks()
+    plan.seed = int(seed)
     return plan
 
 
@@ -341,6 +346,50 @@ def ntt_decompose(plan, A, cores, workspace, stream=None):
     cps = _ptr_array([_dev_ptr(c, torch.float32, "core") for c in cores])
     w = _dev_ptr(workspace, None, "workspace")
     _check(lib().ntt_decompose(plan.handle, a, cps, w, _stream_ptr(stream)), "ntt_decompose")
+
+
+def ntt_unfolding_size(plan, s):
+    """Floats of the unfolding H_s that stage s reads (1 <= s <= d - 2)."""
+    v = ctypes.c_int64()
+    _check(lib().ntt_unfolding_size(plan.handle, int(s), ctypes.byref(v)), "ntt_unfolding_size")
+    return v.value
+
+
+def ntt_decompose_stages(plan, s0, s1, X_in, cores, H_out, workspace, stream=None):
+    """Stages s0 .. s1-1 of the plan (checkpoint / resume at stage granularity):
+    X_in is A (s0 == 0) or the unfolding H_{s0} an earlier call returned in
+    H_out; cores s0 .. s1-1 are written (and the last core when s1 == d - 1);
+    H_out (CUDA float32 of ntt_unfolding_size(plan, s1) floats, or None when
+    s1 == d - 1) receives H_{s1}."""
+    import torch
+    x = _dev_ptr(X_in, torch.float32, "X_in")
+    cps = _ptr_array([_dev_ptr(c, torch.float32, "core") for c in cores])
+    h = None if H_out is None else _dev_ptr(H_out, torch.float32, "H_out")
+    w = _dev_ptr(workspace, None, "workspace")
+    _check(lib().ntt_decompose_stages(plan.handle, int(s0), int(s1), x, cps, h, w, _stream_ptr(stream)),
+           "ntt_decompose_stages")
+
+
+def save_checkpoint(path, plan, s, cores, H):
+    """Write a stage checkpoint to `path` (numpy .npz, host): the cores
+    0 .. s-1, the unfolding H_s that stage s reads, and the plan's dims, ranks
+    and seed (the initial factors of stage k come from (seed, k))."""
+    import numpy as np
+    np.savez(path, stage=np.int64(s), dims=np.asarray(plan.dims, np.int64), ranks=np.asarray(plan.ranks, np.int64),
+             seed=np.uint64(plan.seed), H=H.detach().cpu().numpy(),
+             **{f"core{k}": cores[k].detach().cpu().numpy() for k in range(s)})
+
+
+def load_checkpoint(path, plan):
+    """Read a checkpoint written by save_checkpoint for the same plan: returns
+    (stage, [host cores 0 .. stage-1], host H_stage)."""
+    import numpy as np
+    z = np.load(path)
+    if (tuple(z["dims"]) != tuple(plan.dims) or tuple(z["ranks"]) != tuple(plan.ranks)
+            or int(z["seed"]) != int(plan.seed)):
+        raise ValueError("checkpoint belongs to a different plan (dims, ranks or seed)")
+    s = int(z["stage"])
+    return s, [z[f"core{k}"] for k in range(s)], z["H"]
 
 
 def ntt_decompose_host(plan, A_host, cores_host, workspace, err_host=None, stream=None):

@@ -912,6 +912,51 @@ ntt_status ntt_decompose(ntt_plan p, const float* A, float* const* cores, void* 
   return NTT_OK;
 }
 
+ntt_status ntt_unfolding_size(ntt_plan p, int s, int64_t* floats) {
+  if (!p || !floats || s < 1 || s > p->d - 2) return NTT_ERR_INVALID_ARG;
+  *floats = p->ranks[s] * prod(p->dims.data(), s, p->d);
+  return NTT_OK;
+}
+
+ntt_status ntt_decompose_stages(ntt_plan p, int s0, int s1, const float* X_in, float* const* cores,
+                                float* H_out, void* workspace, void* stream) {
+  if (!p || !X_in || !cores || !workspace) return NTT_ERR_INVALID_ARG;
+  const int d = p->d;
+  if (s0 < 0 || s1 <= s0 || s1 > d - 1) return NTT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return NTT_ERR_INVALID_ARG;
+  if (p->auto_rank) return NTT_ERR_UNSUPPORTED;
+  for (int k = s0; k < s1; ++k)
+    if (!cores[k]) return NTT_ERR_INVALID_ARG;
+  if (s1 == d - 1 && !cores[d - 1]) return NTT_ERR_INVALID_ARG;
+  if (s1 < d - 1 && !H_out) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  if (p->ev.empty()) {
+    p->ev.assign(4 * d + 2, nullptr);
+    for (auto& e : p->ev) NTT_CUDA_TRY(cudaEventCreate(&e));
+  }
+  // eager launches; the eager tables are rewritten: the previous run must have read them
+  if (p->ran && p->last_stream) NTT_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  if (p->h_bytes && !p->h_eager) NTT_TRY(alloc_mapped(p->h_bytes, &p->h_eager, &p->h_eager_dev));
+  EnqueueCtx c;
+  NTT_TRY(enqueue_begin(p, ws, st, &c));
+  if (s0 > 0) {
+    // the saved unfolding where stage s0 reads its X
+    const size_t bytes = (size_t)(p->ranks[s0] * prod(p->dims.data(), s0, d)) * 4;
+    NTT_CUDA_TRY(cudaMemcpyAsync(ws + p->off_H[(s0 - 1) % 2], X_in, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  for (int s = s0; s < s1; ++s) NTT_TRY(enqueue_stage(p, s, X_in, cores, ws, st, p->h_eager, p->h_eager_dev, &c));
+  if (s1 < d - 1) {
+    const size_t bytes = (size_t)(p->ranks[s1] * prod(p->dims.data(), s1, d)) * 4;
+    NTT_CUDA_TRY(cudaMemcpyAsync(H_out, ws + p->off_H[(s1 - 1) % 2], bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  NTT_TRY(enqueue_end(p, st, &c));
+  p->last_stream = st;
+  p->last_ws = workspace;
+  p->ran = true;
+  return NTT_OK;
+}
+
 ntt_status ntt_decompose_host(ntt_plan p, const float* A_host, float* const* cores_host,
                               double* err_host, void* workspace, void* stream) {
   if (!p || !A_host || !cores_host || !workspace) return NTT_ERR_INVALID_ARG;

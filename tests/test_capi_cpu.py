@@ -142,6 +142,25 @@ def test_null_arguments_rejected_without_launch(lib):
                                  vp(256), None, 9, None) == 1                              # bad route
 
 
+def test_stage_range_validation_and_unfolding_sizes(lib):
+    """ntt_decompose_stages rejects empty or out-of-range stage ranges and
+    missing buffers before any launch; ntt_unfolding_size is r_s prod_{j>=s} n_j."""
+    dims, ranks = (8, 12, 10, 9, 7), (1, 4, 9, 6, 3, 1)
+    p = ntt.ntt_plan_create(dims, ranks, 5)
+    assert [ntt.ntt_unfolding_size(p, s) for s in (1, 2, 3)] == [4 * 12 * 10 * 9 * 7, 9 * 10 * 9 * 7, 6 * 9 * 7]
+    for s in (0, 4, -1):
+        with pytest.raises(ntt.NTTError):
+            ntt.ntt_unfolding_size(p, s)
+    vp = ctypes.c_void_p
+    cores = (vp * 5)(*[vp(256)] * 5)
+    for s0, s1 in ((0, 0), (2, 1), (-1, 2), (0, 5)):
+        assert lib.ntt_decompose_stages(p.handle, s0, s1, vp(256), cores, vp(256), vp(256), None) == 1
+    assert lib.ntt_decompose_stages(p.handle, 0, 2, vp(256), cores, None, vp(256), None) == 1   # H_out needed
+    assert lib.ntt_decompose_stages(p.handle, 0, 2, None, cores, vp(256), vp(256), None) == 1   # X_in needed
+    pr = ntt.ntt_plan_create(dims, None, 5, eps_rank=0.1)
+    assert lib.ntt_decompose_stages(pr.handle, 0, 2, vp(256), cores, vp(256), vp(256), None) == 6   # rank rule
+
+
 def test_batch_validation(lib):
     """Batched form: argument checks run on the host before any device call."""
     def code(instances, iters=10, restarts=4):
