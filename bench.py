@@ -673,8 +673,8 @@ def main():
     if (NCU_TRAFFIC["engine"] == st1.get("engine") and wl == WORKLOAD
             and NCU_TRAFFIC["kernel_sha"] == _kernel_sha(NCU_TRAFFIC["kernel_file"])):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    kernel_of = {"fma_pass": "mu_pass_kernel", "grouped": "gpass_kernel", "tc_bf16": "mu_pass_tcb_kernel",
-                 "tc_tf32": "mu_pass_tc_kernel", "fma_narrow": "mu_pass_narrow_kernel"}
+    kernel_of = {"fma_pass": "mu_pass_kernel", "grouped": "gpass_kernel", "tc_bf16": "mu_pass_tcs_kernel (BF16 form)",
+                 "tc_split": "mu_pass_tcs_kernel", "fma_narrow": "mu_pass_narrow_kernel"}
     kname = (f"{kernel_of.get(st1.get('engine'), st1.get('engine'))}<m={st1['m']},r={st1['r']},"
              f"{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
              f"stage {dom + 1} ({st1['m']} x {st1['n']}, r={st1['r']})")

@@ -136,7 +136,7 @@ typedef struct {
 #define NTT_ENGINE_FMA_PASS 0         /* single-problem fused pass, packed FP32 FMAs */
 #define NTT_ENGINE_GROUPED 1          /* grouped engine (register-tiled FMA pass) */
 #define NTT_ENGINE_TC_BF16 2          /* BF16-X tensor-core pass (tcgen05 kind::f16) */
-#define NTT_ENGINE_TC_TF32 3          /* TF32 tensor-core pass (only with NTT_ROUTE_TC) */
+#define NTT_ENGINE_TC_TF32 3          /* retired (a 3xTF32 pass, slower than the split form) */
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 #define NTT_ENGINE_BCD_PASS 5         /* the fused pass in its BCD (Algorithm 3) mode */
 #define NTT_ENGINE_TC_SPLIT 6         /* FP32 X split in two BF16 matrices on the tensor-core pass */

@@ -83,7 +83,6 @@ ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, M
   if (cap > (n + 15) / 16) cap = (n + 15) / 16;   // every pass tile is >= 16 columns
   s.grid_cap = (int)(cap > grid ? cap : grid);
   s.tma = 0;
-  s.tc = 0;
   *out = s;
   return NTT_OK;
 }
@@ -97,11 +96,6 @@ ntt_status mu_choose_shape(int64_t m, int64_t n, int r, int bf16, int num_sms, M
 //    column against 32 B of X, and one CTA per SM with its H loads in the
 //    epilogue leaves the latency exposed.  NTT_ROUTE_FMA / _GENERIC keep the
 //    packed-FMA pass.
-//  - The 3xTF32 tensor-core pass (FP32 X, m <= 64, r <= 16) runs only with
-//    NTT_ROUTE_TC.  Measured on GB300: a kind::tf32 M=128 K=8 MMA costs ~56
-//    cycles for any N <= 64, so the 3xTF32 form needs >= 10.5 tensor-pipe
-//    cycles per column of a 32-row unfolding against a 9-cycle HBM budget, and
-//    the FMA pass is faster.
 //  - FP32 X with at most 32 rows at rank bucket 8 runs on the warp-streamed
 //    pass (mu_pass_narrow.cu) unless the route is NTT_ROUTE_GENERIC.
 static bool tcb_enabled(int MP, int route) {
@@ -109,8 +103,6 @@ static bool tcb_enabled(int MP, int route) {
   if (MP <= 32) return route == NTT_ROUTE_TC;
   return true;
 }
-
-static bool tc_enabled(int route) { return route == NTT_ROUTE_TC; }
 
 // FP32 X with 128 or 256 rows at rank bucket 16 or 32, or 512 rows at rank
 // bucket 16 (n a multiple of 8), runs on the split tensor-core form (X in two
@@ -131,7 +123,6 @@ static bool narrow_enabled(int route) { return route != NTT_ROUTE_GENERIC; }
 
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
-  s->tc = 0;
   s->tcb = 0;
   s->tcs = 0;
   s->narrow = 0;
@@ -147,16 +138,6 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   }
   if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP, s->route)) {
     s->tcb = 1;
-    s->T = 128;
-    const int64_t ntiles = (s->n + s->T - 1) / s->T;
-    int64_t grid = num_sms > 0 ? num_sms : 152;
-    if (grid > ntiles) grid = ntiles;
-    if (grid > s->grid_cap) grid = s->grid_cap;
-    s->grid = (int)grid;
-    return;
-  }
-  if (s->tma && !s->bf16 && tc_pass_supported(s->MP, s->R) && tc_enabled(s->route)) {
-    s->tc = 1;
     s->T = 128;
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
     int64_t grid = num_sms > 0 ? num_sms : 152;
@@ -222,14 +203,12 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.m};
     cuuint64_t strides[1] = {(cuuint64_t)(s.n * xb)};
-    // tensor-core pass: 32-column boxes (128 bytes), 128-byte swizzle of 32-byte chunks;
     // narrow pass: 32-column boxes, 128-byte swizzle of 16-byte chunks
-    cuuint32_t box[2] = {(cuuint32_t)(s.tc || s.narrow ? 32 : s.T), (cuuint32_t)br};
+    cuuint32_t box[2] = {(cuuint32_t)(s.narrow ? 32 : s.T), (cuuint32_t)br};
     cuuint32_t es[2] = {1, 1};
     CUresult e = fn(mx, s.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     2, const_cast<void*>(X), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    s.tc ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B
-                         : (s.narrow ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE),
+                    s.narrow ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
   }
@@ -251,7 +230,6 @@ cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CU
                            const CUtensorMap& mh, cudaStream_t st) {
   if (s.tcs) return launch_mu_pass_tcs(s, d, eps, st);
   if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
-  if (s.tc) return launch_mu_pass_tc(s, d, eps, mx, mh, st);
   if (s.narrow) return launch_mu_pass_narrow(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \
   case MPV:                                                                 \

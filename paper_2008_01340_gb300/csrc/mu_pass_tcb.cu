@@ -413,10 +413,8 @@ cudaError_t launch_mu_pass_tcb(const MuShape& s, const MuDev& d, float eps, cuda
   if (s.MP == 16 && s.R == 32) return launch_tcb_cfg<TbCfg<16, 32>>(s, d, eps, st);
   if (s.MP == 32 && s.R == 16) return launch_tcb_cfg<TbCfg<32, 16>>(s, d, eps, st);
   if (s.MP == 32 && s.R == 32) return launch_tcb_cfg<TbCfg<32, 32>>(s, d, eps, st);
-  if (s.MP == 128 && s.R == 16) return launch_tcb_cfg<TbCfg<128, 16>>(s, d, eps, st);
-  if (s.MP == 128 && s.R == 32) return launch_tcb_cfg<TbCfg<128, 32>>(s, d, eps, st);
-  if (s.MP == 256 && s.R == 16) return launch_tcb_cfg<TbCfg<256, 16>>(s, d, eps, st);
-  if (s.MP == 256 && s.R == 32) return launch_tcb_cfg<TbCfg<256, 32>>(s, d, eps, st);
+  // 128/256 rows: the warp-specialised pass of mu_pass_tcs.cu in its BF16 form
+  if (s.MP == 128 || s.MP == 256) return launch_mu_pass_tcbx(s, d, eps, st);
   return cudaErrorInvalidValue;
 }
 

@@ -1,6 +1,10 @@
 // Fused MU pass for FP32 X on the BF16 tensor cores (the split form), for
 // unfoldings of 128 or 256 rows at rank buckets 16 and 32 and of 512 rows at
-// rank bucket 16.
+// rank bucket 16; with BX the same pass for BF16 X (the precision form) at 128
+// or 256 rows: X is then an exact operand, a tile covers 128 columns (its two
+// atoms), W takes three BF16 terms (24 bits), the H_new stack has one atom per
+// column half and Q runs over both, and each TMEM lane is its own column (no
+// exchange between threads).
 //
 // The unfolding is split once per stage into two BF16 matrices X1 = bf16(X)
 // and X2 = bf16(X - X1) (16 significand bits of X; the same HBM bytes per
@@ -52,23 +56,31 @@ namespace {
 constexpr int kTsEpi = 256;                 // epilogue threads (warps 0-7)
 constexpr int kTsThreads = kTsEpi + 64;     // + the MMA warp and the TMA warp
 
-template <int MP_, int R_>
+template <int MP_, int R_, bool BX_ = false>
 struct TsCfg {
   static constexpr int MP = MP_;
   static constexpr int R = R_;
-  static constexpr int TC = 64;                 // columns of X per tile
+  // BX: X itself is BF16 (the precision form): its values are exact operands,
+  // a tile's two atoms are 128 consecutive columns, W takes three terms
+  static constexpr bool BX = BX_;
+  static constexpr int TC = BX ? 128 : 64;      // columns of X per tile
   static constexpr int FLUSH = 2048 / TC;       // tiles per TMEM run of D_B
-  static constexpr int N2 = 2 * R;              // phase A N: two W terms
+  static constexpr int N2 = BX ? 3 * R : 2 * R; // phase A N: the W terms
   static constexpr int N3 = 3 * R;              // phase B N: three H_new terms
   static constexpr int KH = R / 2;              // ranks per TMEM lane group (two per column)
   static constexpr int HALF = KH / 2;           // ranks one epilogue thread updates
-  static constexpr int XST = MP * 128 * 2;      // one stage: X1 atom + X2 atom
-  static constexpr int HS = N3 * 128;           // one H_new stack: 3R rows of one atom
+  static constexpr int XST = MP * 128 * 2;      // one stage: two atoms (X1 and X2, or 128 columns of X)
+  static constexpr int HATOMS = BX ? 2 : 1;     // atoms of an H_new stack (its tile's columns)
+  static constexpr int HS = HATOMS * N3 * 128;  // one H_new stack: 3R rows per atom
+  // Split form: two stacks (the epilogue of tile j writes one while phase B of
+  // tile j - 1 reads the other).  BF16 form: one (shared memory), written once
+  // phase B of the previous tile has completed.
+  static constexpr int NSTK = BX ? 1 : 2;
   static constexpr int KAT = MP / 64;           // 64-row K atoms of the W operand
   static constexpr int WOP = KAT * N2 * 128;
   static constexpr int NMB = MP / 128;          // X row blocks of phase B
   static constexpr int BARB = 256;              // mbarriers and the TMEM slot
-  static constexpr int FIXED = 2 * HS + WOP + R * R * 4 + BARB + 1024;
+  static constexpr int FIXED = NSTK * HS + WOP + R * R * 4 + BARB + 1024;
   static constexpr int FIT = (227 * 1024 - FIXED) / XST;
   static constexpr int S = FIT < 6 ? FIT : 6;   // X stages
   static constexpr int BOXR = MP < 256 ? MP : 256; // TMA box rows (two boxes per atom at 512 rows)
@@ -76,7 +88,7 @@ struct TsCfg {
   // stack's 3R rows into the following shared memory; those rows only reach
   // TMEM lanes >= 3R, which are never read.
   static constexpr int OFF_HN = 0;
-  static constexpr int OFF_X = 2 * HS;
+  static constexpr int OFF_X = NSTK * HS;
   static constexpr int OFF_W = OFF_X + S * XST;
   static constexpr int OFF_G = OFF_W + WOP;
   static constexpr int OFF_BAR = OFF_G + R * R * 4;
@@ -86,13 +98,14 @@ struct TsCfg {
   static constexpr uint32_t IDA = idesc_bf16(128, N2, true, false);
   static constexpr uint32_t IDB = idesc_bf16(128, N3, false, false);
   static constexpr uint32_t TX = 2u * MP * 128u;   // bytes of one stage's two copies
-  static_assert(((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16), "bucket");
+  static_assert(((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (!BX && MP == 512 && R == 16), "bucket");
   static_assert(S >= 1 && SMEM <= 227 * 1024, "shared memory");
   static_assert(TMEM_USED <= 512, "TMEM columns");
   static_assert(HS % 1024 == 0 && OFF_X % 1024 == 0 && OFF_W % 1024 == 0 && (N2 * 128) % 1024 == 0,
                 "atom alignment");
-  static_assert(3 * R * R * 4 <= HS && 64 * (R + 1) * 4 <= HS, "scratch in an H_new stack");
-  static_assert(OFF_HN + HS + 128 * 128 <= OFF_W, "Q operand rows past a stack stay in shared memory");
+  static_assert(3 * R * R * 4 <= HS && (BX || 64 * (R + 1) * 4 <= HS), "scratch in an H_new stack");
+  static_assert(OFF_HN + (NSTK - 1) * HS + (HATOMS - 1) * N3 * 128 + 128 * 128 <= OFF_W,
+                "Q operand rows past a stack stay in shared memory");
   static_assert(2 * 6 + 6 <= BARB / 8 - 2, "barrier slots");
 };
 
@@ -181,14 +194,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
     if (e >= MP * R) break;
     const int i = e / R, k = e % R;   // W row i (K index), rank k
     const float w = wv[u];
-    const __nv_bfloat16 w1 = __float2bfloat16_rn(w);
-    const __nv_bfloat16 w2 = __float2bfloat16_rn(w - __bfloat162float(w1));
+    __nv_bfloat16 t3[3];
+    split3(w, t3);   // the split form takes the first two (16 bits, as its X)
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < N2 / R; ++t) {
       const int nrow = t * R + k;
       const uint32_t off = (uint32_t)((i >> 6) * N2 * 128) + nrow * 128 + ((((i & 63) >> 3) ^ (nrow & 7)) << 4) +
                            ((i & 7) << 1);
-      *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_W + off) = t == 0 ? w1 : w2;
+      *reinterpret_cast<__nv_bfloat16*>(smem + C::OFF_W + off) = t3[t];
     }
   }
   for (int e = tid; e < R * R; e += kTsThreads) Gs[e] = p.G[e];
@@ -219,7 +232,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
   const uint32_t tmem = *tmem_slot;
   auto dA = [&](int b) { return tmem + (uint32_t)(b * N2); };
   auto dB = [&](int blk) { return tmem + (uint32_t)(2 * N2 + blk * N3); };
-  auto stack_off = [&](int b) { return (uint32_t)(C::OFF_HN + b * C::HS); };
+  auto stack_off = [&](int b) { return (uint32_t)(C::OFF_HN + (C::NSTK == 2 ? b : 0) * C::HS); };
 
   if (warp == 9) {
     // =========================================================== TMA thread
@@ -238,8 +251,13 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         mbar_arrive_expect_tx(full(s), C::TX);
 #pragma unroll
         for (int h = 0; h < MP / C::BOXR; ++h) {
-          tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
-          tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX2, col0, h * C::BOXR, full(s));
+          if constexpr (C::BX) {   // columns col0 .. col0 + 63 and col0 + 64 .. col0 + 127 of X
+            tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
+            tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX1, col0 + 64, h * C::BOXR, full(s));
+          } else {                 // X1 and X2 of columns col0 .. col0 + 63
+            tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
+            tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX2, col0, h * C::BOXR, full(s));
+          }
         }
       }
       // every copy issued has landed before the CTA ends (the last one of each stage)
@@ -276,11 +294,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         for (int kk = 0; kk < 8; ++kk) {
           const uint32_t xo = (uint32_t)((kk >> 2) * MP * 128 + (kk & 3) * 32);
           const uint32_t acc = (t % C::FLUSH != 0 || kk > 0) ? 1u : 0u;
-          const uint64_t dh = smem_desc(hb + (kk & 3) * 32, 16, 1024, kLayoutSw128);
+          // BF16 form: the second atom holds columns 64.., so does the stack's;
+          // split form: both atoms are the same columns, Q once
+          const uint32_t ha = C::BX ? (uint32_t)((kk >> 2) * N3 * 128) : 0u;
+          const uint64_t dh = smem_desc(hb + ha + (kk & 3) * 32, 16, 1024, kLayoutSw128);
 #pragma unroll
           for (int mb = 0; mb < C::NMB; ++mb)
             mma_bf16(dB(mb), smem_desc(xb + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128), dh, C::IDB, acc);
-          if (kk < 4) mma_bf16(dB(C::NMB), dh, dh, C::IDB, acc);
+          if (C::BX || kk < 4) mma_bf16(dB(C::NMB), dh, dh, C::IDB, acc);
         }
         mma_commit(empty(s));
         mma_commit(bdone);
@@ -320,17 +341,18 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
     }
   } else {
     // =========================================================== epilogue
-    // TMEM lane c = the tile column cc (c < 64: its X1 part) or, for c >= 64,
-    // the X2 part of column c - 64; lane group kh0 .. kh0 + KH of the ranks
+    // TMEM lane c: split form, the tile column cc = c (its X1 part) or, for
+    // c >= 64, the X2 part of column c - 64; BF16 form, column c; lane group
+    // kh0 .. kh0 + KH of the ranks
     const int c = (warp % 4) * 32 + lane;
-    const int cc = c % 64;
-    const bool owner = c < 64;
+    const int cc = C::BX ? c : c % 64;
+    const bool owner = C::BX || c < 64;
     const bool hi = warp >= 4;
     const int kh0 = hi ? KH : 0;
     const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
     // old H of a tile's column, all ranks; with rank bucket 16 one tile ahead
     // (registers), so the loads' latency overlaps the current tile
-    constexpr bool PREFETCH_H = R <= 16;
+    constexpr bool PREFETCH_H = R <= 16 || C::BX;
     auto load_h = [&](int tile_, float* hv) {
       const int64_t col_ = (int64_t)tile_ * C::TC + cc;
 #pragma unroll
@@ -343,7 +365,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
     // rank bucket 16: the G rows of this thread's ranks in registers (their
     // shared-memory reads otherwise take a large share of the pass's
     // shared-memory bandwidth, which the MMA operands need)
-    constexpr bool GREG = R <= 16;
+    constexpr bool GREG = !C::BX && R <= 16;
     float gk[GREG ? HALF : 1][GREG ? R : 1];
     if constexpr (GREG) {
       const int kq = kh0 + (owner ? 0 : HALF);
@@ -413,80 +435,126 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         tc_fence_after();
         flush(scratch);
       }
-      // this lane's part of Y (the two W term groups)
+      // this lane's part of Y (the W term groups)
       float y[KH];
       {
         float v0[KH], v1[KH];
         tmem_ld_kh<KH>(dA(b) + lane_base + kh0, v0);
         tmem_ld_kh<KH>(dA(b) + lane_base + R + kh0, v1);
-        tmem_wait_ld();
+        if constexpr (C::BX) {
+          float v2[KH];
+          tmem_ld_kh<KH>(dA(b) + lane_base + 2 * R + kh0, v2);
+          tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < KH; ++q) y[q] = v0[q] + v1[q];
+          for (int q = 0; q < KH; ++q) y[q] = (v0[q] + v1[q]) + v2[q];
+        } else {
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < KH; ++q) y[q] = v0[q] + v1[q];
+        }
       }
       tc_fence_before();
-      // Y = X1 part (lane cc) + X2 part (lane 64 + cc): the X1 lane's thread
-      // updates the first HALF ranks of the group, the X2 lane's thread the
-      // rest; each hands the other its part of the other half (rows of R + 1
-      // floats: consecutive columns fall in different banks)
-      if (owner) {
+      if constexpr (C::BX) {
+        // H update of column cc at ranks kh0 + q (all of them first), then,
+        // once phase B of the previous tile has released the one stack,
+        // H_new to HBM and its three BF16 terms into the stack
+        float hn[KH];
 #pragma unroll
-        for (int q = HALF; q < KH; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
-      } else {
-#pragma unroll
-        for (int q = 0; q < HALF; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
-      }
-      epi_sync();
-      if (owner) {
-#pragma unroll
-        for (int q = 0; q < HALF; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
-      } else {
-#pragma unroll
-        for (int q = HALF; q < KH; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
-      }
-      epi_sync();   // the exchange area is the stack, written next
-      // H update of column cc, rank kh0 + q: H_new to HBM, its three BF16
-      // terms into the stack
-      // H update of column cc at this thread's ranks kh0 + Q0 + qi: all of
-      // them first (independent chains), then H_new to HBM and its three BF16
-      // terms into the stack
-      auto update_half = [&](auto q0c) {
-        constexpr int Q0 = decltype(q0c)::value;
-        float hn[HALF];
-#pragma unroll
-        for (int qi = 0; qi < HALF; ++qi) {
-          const int q = Q0 + qi;
+        for (int q = 0; q < KH; ++q) {
+          const int k = kh0 + q;
           float gh = 0.0f;
-          if constexpr (GREG) {
 #pragma unroll
-            for (int l = 0; l < R; ++l) gh = fmaf(gk[qi][l], h[l], gh);
-          } else {
-            const int k = kh0 + q;
-#pragma unroll
-            for (int l = 0; l < R; l += 4) {
-              const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
-              gh = fmaf(g.x, h[l], gh);
-              gh = fmaf(g.y, h[l + 1], gh);
-              gh = fmaf(g.z, h[l + 2], gh);
-              gh = fmaf(g.w, h[l + 3], gh);
-            }
+          for (int l = 0; l < R; l += 4) {
+            const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
+            gh = fmaf(g.x, h[l], gh);
+            gh = fmaf(g.y, h[l + 1], gh);
+            gh = fmaf(g.z, h[l + 2], gh);
+            gh = fmaf(g.w, h[l + 3], gh);
           }
           const float hk = hi ? h[KH + q] : h[q];
-          hn[qi] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
+          hn[q] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
+        }
+        if (j > 0) {
+          // phase A of tile j was issued after phase B of tile j - 2: unambiguous
+          bad = !mbar_wait_bounded(bdone, (uint32_t)((j - 1) & 1));
+          if (bad) *s_err = 1;
+          if (epi_any(bad)) {
+            ok = false;
+            break;
+          }
         }
 #pragma unroll
-        for (int qi = 0; qi < HALF; ++qi) {
-          const int k = kh0 + Q0 + qi;
-          if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[qi];
+        for (int q = 0; q < KH; ++q) {
+          const int k = kh0 + q;
+          if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[q];
           __nv_bfloat16 t3[3];
-          split3(hn[qi], t3);
+          split3(hn[q], t3);
 #pragma unroll
           for (int t = 0; t < 3; ++t) *reinterpret_cast<__nv_bfloat16*>(stk + swz(t * R + k, cc, N3)) = t3[t];
         }
-      };
-      if (owner)
-        update_half(std::integral_constant<int, 0>{});
-      else
-        update_half(std::integral_constant<int, HALF>{});
+      } else {
+        // Y = X1 part (lane cc) + X2 part (lane 64 + cc): the X1 lane's thread
+        // updates the first HALF ranks of the group, the X2 lane's thread the
+        // rest; each hands the other its part of the other half (rows of R + 1
+        // floats: consecutive columns fall in different banks)
+        if (owner) {
+#pragma unroll
+          for (int q = HALF; q < KH; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < HALF; ++q) scratch[cc * (R + 1) + kh0 + q] = y[q];
+        }
+        epi_sync();
+        if (owner) {
+#pragma unroll
+          for (int q = 0; q < HALF; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
+        } else {
+#pragma unroll
+          for (int q = HALF; q < KH; ++q) y[q] += scratch[cc * (R + 1) + kh0 + q];
+        }
+        epi_sync();   // the exchange area is the stack, written next
+        // H update of column cc at this thread's ranks kh0 + Q0 + qi: all of
+        // them first (independent chains), then H_new to HBM and its three BF16
+        // terms into the stack
+        auto update_half = [&](auto q0c) {
+          constexpr int Q0 = decltype(q0c)::value;
+          float hn[HALF];
+#pragma unroll
+          for (int qi = 0; qi < HALF; ++qi) {
+            const int q = Q0 + qi;
+            float gh = 0.0f;
+            if constexpr (GREG) {
+#pragma unroll
+              for (int l = 0; l < R; ++l) gh = fmaf(gk[qi][l], h[l], gh);
+            } else {
+              const int k = kh0 + q;
+#pragma unroll
+              for (int l = 0; l < R; l += 4) {
+                const float4 g = *reinterpret_cast<const float4*>(Gs + k * R + l);
+                gh = fmaf(g.x, h[l], gh);
+                gh = fmaf(g.y, h[l + 1], gh);
+                gh = fmaf(g.z, h[l + 2], gh);
+                gh = fmaf(g.w, h[l + 3], gh);
+              }
+            }
+            const float hk = hi ? h[KH + q] : h[q];
+            hn[qi] = fmaxf(0.0f, __fdividef(hk * y[q], gh + p.eps));
+          }
+#pragma unroll
+          for (int qi = 0; qi < HALF; ++qi) {
+            const int k = kh0 + Q0 + qi;
+            if (k < r && col < n) p.H[(int64_t)k * n + col] = hn[qi];
+            __nv_bfloat16 t3[3];
+            split3(hn[qi], t3);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) *reinterpret_cast<__nv_bfloat16*>(stk + swz(t * R + k, cc, N3)) = t3[t];
+          }
+        };
+        if (owner)
+          update_half(std::integral_constant<int, 0>{});
+        else
+          update_half(std::integral_constant<int, HALF>{});
+      }
       fence_proxy_async_smem();
       tc_fence_before();
       mbar_arrive(epi(b));
@@ -540,9 +608,8 @@ cudaError_t launch_tcs_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   CUtensorMap m1, m2;
   std::memset(&m1, 0, sizeof(m1));
   std::memset(&m2, 0, sizeof(m2));
-  if (encode_bf16_atom_map(d.X, s.m, s.n, C::BOXR, &m1) != NTT_OK ||
-      encode_bf16_atom_map(d.X2, s.m, s.n, C::BOXR, &m2) != NTT_OK)
-    return cudaErrorInvalidValue;
+  if (encode_bf16_atom_map(d.X, s.m, s.n, C::BOXR, &m1) != NTT_OK) return cudaErrorInvalidValue;
+  if (!C::BX && encode_bf16_atom_map(d.X2, s.m, s.n, C::BOXR, &m2) != NTT_OK) return cudaErrorInvalidValue;
   mu_pass_tcs_kernel<C><<<s.grid, kTsThreads, C::SMEM, st>>>(m1, m2, p);
   return cudaGetLastError();
 }
@@ -560,6 +627,14 @@ cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cuda
   if (s.MP == 256 && s.R == 16) return launch_tcs_cfg<TsCfg<256, 16>>(s, d, eps, st);
   if (s.MP == 256 && s.R == 32) return launch_tcs_cfg<TsCfg<256, 32>>(s, d, eps, st);
   if (s.MP == 512 && s.R == 16) return launch_tcs_cfg<TsCfg<512, 16>>(s, d, eps, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mu_pass_tcbx(const MuShape& s, const MuDev& d, float eps, cudaStream_t st) {
+  if (s.MP == 128 && s.R == 16) return launch_tcs_cfg<TsCfg<128, 16, true>>(s, d, eps, st);
+  if (s.MP == 128 && s.R == 32) return launch_tcs_cfg<TsCfg<128, 32, true>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 16) return launch_tcs_cfg<TsCfg<256, 16, true>>(s, d, eps, st);
+  if (s.MP == 256 && s.R == 32) return launch_tcs_cfg<TsCfg<256, 32, true>>(s, d, eps, st);
   return cudaErrorInvalidValue;
 }
 

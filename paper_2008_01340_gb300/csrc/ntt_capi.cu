@@ -38,7 +38,7 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
   if (engine)
     *engine = s.tcs ? NTT_ENGINE_TC_SPLIT
                     : (s.tcb ? NTT_ENGINE_TC_BF16
-                             : (s.tc ? NTT_ENGINE_TC_TF32 : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS)));
+                             : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS));
   MuDev d = dev;
   if (s.tcs) {
     // X = X1 + X2 (bf16(X) and bf16(X - bf16(X))), once for the whole loop
@@ -334,8 +334,7 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route, bool s
   if (xbf16 && (!gpass_bf16_supported(MP, R) || n % 8 != 0)) return false;
   if (route == NTT_ROUTE_PASS || route == NTT_ROUTE_GENERIC) return false;
   if (route == NTT_ROUTE_GROUPED) return true;
-  if (route == NTT_ROUTE_TC && ((xbf16 && tcb_pass_supported(MP, R)) || (!xbf16 && tc_pass_supported(MP, R))))
-    return false;
+  if (route == NTT_ROUTE_TC && xbf16 && tcb_pass_supported(MP, R)) return false;
   // FP32 stages of 128/256 rows at rank 16/32: the split tensor-core form
   if (!xbf16 && split_ok && tcs_route_ok(m, n, r, route)) return false;
   if (route != NTT_ROUTE_FMA && xbf16 && tcb_pass_supported(MP, R) && MP >= 128) return false;

@@ -290,7 +290,6 @@ struct MuShape {
   int grid_cap = 0;  // largest grid any pass may use (sizes the partial buffer)
   int bf16 = 0;      // X stored as BF16
   int tma = 0;       // X/H tiles loaded by TMA (else cooperative loads)
-  int tc = 0;        // tensor-core (tcgen05) pass instead of the FMA pass
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
   int tcs = 0;       // FP32 X split in two BF16 matrices on the same tensor-core pass
   int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
@@ -372,10 +371,6 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st);
 cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t, cudaStream_t st);
-// Tensor-core pass (tcgen05) for m <= 64 rows and r <= 16.
-bool tc_pass_supported(int MP, int R);
-cudaError_t launch_mu_pass_tc(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
-                              const CUtensorMap& mh, cudaStream_t st);
 cudaError_t launch_gram(const MuShape& s, const MuDev& d, cudaStream_t st);
 // BF16-X tensor-core pass (tcgen05 kind::f16) for 128 or 256 rows and rank buckets 16, 32.
 bool tcb_pass_supported(int MP, int R);
@@ -387,6 +382,8 @@ cudaError_t launch_mu_pass_tcs(const MuShape& s, const MuDev& d, float eps, cuda
 // The split form for unfoldings of at most 32 rows (X1, X2 and the H_new terms
 // stacked in one 128-row block; 128-column tiles).
 bool tcn_pass_supported(int MP, int R);
+// The warp-specialised form of mu_pass_tcs.cu for BF16 X at 128/256 rows.
+cudaError_t launch_mu_pass_tcbx(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
 cudaError_t launch_mu_pass_tcn(const MuShape& s, const MuDev& d, float eps, cudaStream_t st);
 // X1 = bf16(X), X2 = bf16(X - X1) elementwise (round to nearest even).
 cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16* X2, int64_t count,

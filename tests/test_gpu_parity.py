@@ -465,14 +465,15 @@ def test_c2_full_size_decompose_properties(ntt, c2_full):
 @pytest.mark.parametrize("m,n,r", [(32, 70000, 8), (16, 20000, 16), (24, 9000, 8), (32, 8192, 12),
                                    (32, 9000 * 128, 8)])
 def test_tensor_core_and_fma_passes_agree(ntt, m, n, r):
-    """The 3xTF32 tcgen05 pass (m <= 32, r <= 16, route "tc") and the default
-    FMA pass both match the oracle's iterates within the FP32 tolerance."""
+    """The stacked split tensor-core form (m <= 32, r <= 16, route "tc") and
+    the default FMA pass both match the oracle's iterates within the FP32
+    tolerance."""
     X = _x_matrix("lowrank", m, n, 77 + m)
     W0 = synth.uniform_matrix((m, r), 78)
     H0 = synth.uniform_matrix((r, n), 79)
     eng = []
     Wt, Ht, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="tc", engine=eng)
-    assert eng == ["tc_tf32"]
+    assert eng == ["tc_split"]
     Wf, Hf, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
     Wo, Ho, _ = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
     for Wg, Hg in ((Wt, Ht), (Wf, Hf)):
