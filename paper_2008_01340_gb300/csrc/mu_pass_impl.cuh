@@ -542,6 +542,8 @@ template <class C>
 __global__ void __launch_bounds__(kPassThreads, 1)
 mu_pass_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmH,
                const PassParams p) {
+  pdl_wait();      // the previous kernel's W, G and stop word
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   mu_pass_body<C>(tmX, tmH, tmH, tmH, p.H, p.H, p.H, 0.0f, 0.0f, p);
 }
@@ -623,8 +625,7 @@ cudaError_t launch_pass_cfg(const MuShape& s, const MuDev& d, float eps, const C
   p.bcd = nullptr;
   p.bcd_init = 0;
   p.res_part = nullptr;
-  mu_pass_kernel<C><<<s.grid, kPassThreads, C::SMEM, st>>>(mx, mh, p);
-  return cudaGetLastError();
+  return launch_pdl(mu_pass_kernel<C>, dim3(s.grid), dim3(kPassThreads), C::SMEM, st, mx, mh, p);
 }
 
 // Tile width and smem of a (MP, R, BF16) bucket, for host shape decisions.

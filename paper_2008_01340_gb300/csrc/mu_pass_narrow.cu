@@ -108,6 +108,8 @@ mu_pass_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
                       const NarrowParams p) {
   constexpr int RPL = C::RPL, MP = C::MP, S = C::STAGES;
   constexpr int kNarrowWarps = C::kNarrowWarps, kNarrowThreads = C::kNarrowThreads;
+  pdl_wait();      // the previous kernel's W, G and stop word
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -341,8 +343,7 @@ cudaError_t launch_narrow_cfg(const MuShape& s, const MuDev& d, float eps, const
   p.r = s.r;
   p.nbox = (int)((s.n + kBoxCols - 1) / kBoxCols);
   p.eps = eps;
-  mu_pass_narrow_kernel<C><<<s.grid, C::kNarrowThreads, C::SMEM, st>>>(mx, mh, p);
-  return cudaGetLastError();
+  return launch_pdl(mu_pass_narrow_kernel<C>, dim3(s.grid), dim3(C::kNarrowThreads), C::SMEM, st, mx, mh, p);
 }
 
 }  // namespace

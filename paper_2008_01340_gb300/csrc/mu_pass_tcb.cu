@@ -97,6 +97,8 @@ struct TbParams {
 template <class C>
 __global__ void __launch_bounds__(kTbThreads, 1) mu_pass_tcb_kernel(const TbParams p) {
   constexpr int MP = C::MP, R = C::R, T = C::T, N3 = C::N3, KH = C::KH;
+  pdl_wait();      // the previous kernel's W, G and stop word
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -398,8 +400,7 @@ cudaError_t launch_tcb_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.r = s.r;
   p.ntiles = (int)((s.n + C::T - 1) / C::T);
   p.eps = eps;
-  mu_pass_tcb_kernel<C><<<s.grid, kTbThreads, C::SMEM, st>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(mu_pass_tcb_kernel<C>, dim3(s.grid), dim3(kTbThreads), C::SMEM, st, p);
 }
 
 }  // namespace

@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(kTnThreads, 1) mu_pass_tcn_kernel(const __grid
                                                                     const __grid_constant__ CUtensorMap tmX2,
                                                                     const TnParams p) {
   constexpr int MP = C::MP, R = C::R, N2 = C::N2, N3 = C::N3, KH = C::KH, S = C::S;
+  pdl_wait();      // the previous kernel's W, G and stop word
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the stage's stopping test has fired
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -444,8 +446,7 @@ cudaError_t launch_tcn_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   if (encode_bf16_atom_map(d.X, s.m, s.n, C::MP, &m1) != NTT_OK ||
       encode_bf16_atom_map(d.X2, s.m, s.n, C::MP, &m2) != NTT_OK)
     return cudaErrorInvalidValue;
-  mu_pass_tcn_kernel<C><<<s.grid, kTnThreads, C::SMEM, st>>>(m1, m2, p);
-  return cudaGetLastError();
+  return launch_pdl(mu_pass_tcn_kernel<C>, dim3(s.grid), dim3(kTnThreads), C::SMEM, st, m1, m2, p);
 }
 
 }  // namespace

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(kAuxThreads) combine_reduce_kernel(const Combi
   __shared__ float chunk[kChunks][kEntriesPerBlock];
   const int tid = threadIdx.x;
   const int E = (p.MP + p.R) * p.R;
+  pdl_wait();      // the pass's partials
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
   const int el = tid % kEntriesPerBlock;
   const int j = tid / kEntriesPerBlock;
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(kAuxThreads) combine_w_kernel(const CombinePar
   __shared__ double dsh[2 * kAuxThreads / 32];
   __shared__ double osh[2 * kMaxWBlocks];
   __shared__ int s_last;
+  pdl_wait();      // the reduced [P ; Q]
+  pdl_trigger();
   if (p.stop && __ldcg(p.stop)) return;   // the loop's stopping test has fired
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = p.m, r = p.r, R = p.R, MP = p.MP, blk = p.blk;
@@ -284,11 +288,10 @@ cudaError_t launch_mu_combine(const MuShape& s, const MuDev& d, float eps, int t
   if (wblocks > kMaxWBlocks) return cudaErrorInvalidValue;
   // the W half's partials fit the partial buffer the reduction has consumed
   if ((size_t)wblocks * (s.R * s.R + 4) + 2 > (size_t)s.grid * E) return cudaErrorInvalidValue;
-  combine_reduce_kernel<<<(E + kEntriesPerBlock - 1) / kEntriesPerBlock, kAuxThreads, 0, st>>>(p);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e =
+      launch_pdl(combine_reduce_kernel, dim3((E + kEntriesPerBlock - 1) / kEntriesPerBlock), dim3(kAuxThreads), 0, st, p);
   if (e != cudaSuccess) return e;
-  combine_w_kernel<<<wblocks, kAuxThreads, 0, st>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(combine_w_kernel, dim3(wblocks), dim3(kAuxThreads), 0, st, p);
 }
 
 cudaError_t launch_gram(const MuShape& s, const MuDev& d, cudaStream_t st) {
