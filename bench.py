@@ -48,7 +48,7 @@ FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 f
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture, valid
 # only for the engine and kernel source it was measured on (hash of that file).
-NCU_TRAFFIC = {"engine": "fma_narrow", "kernel_file": "mu_pass_narrow.cu", "kernel_sha": "66019c8a0f70dcfa",
+NCU_TRAFFIC = {"engine": "fma_narrow", "kernel_file": "mu_pass_narrow.cu", "kernel_sha": "8c6b5110f25a4b89",
                "bytes_per_launch": 6.300e9}   # 787.5 MB on 32 x 4194304, x 8 for 33554432 columns
 
 
