@@ -140,6 +140,7 @@ typedef struct {
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 #define NTT_ENGINE_BCD_PASS 5         /* the fused pass in its BCD (Algorithm 3) mode */
 #define NTT_ENGINE_TC_SPLIT 6         /* FP32 X split in two BF16 matrices on the tensor-core pass */
+#define NTT_ENGINE_TC_NARROW 7        /* <= 32 rows, rank <= 8, FP32 X split in two BF16 terms: warp-level MMAs */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);
@@ -331,10 +332,13 @@ ntt_status nmf_bcd_workspace_size(int64_t m, int64_t n, int r, size_t* bytes);
 ntt_status nmf_bcd_step(int64_t m, int64_t n, int r, const float* X, float* W, float* H, int iters,
                         double* obj_dev, void* ws, void* stream);
 
-/* Workspace bytes of nmf_mu_step_route: with NTT_ROUTE_TC on an FP32 X of
- * 128 or 256 rows at rank 9..32 (n a multiple of 8) it adds 4 m n bytes for
- * the split tensor-core form's two BF16 terms of X; otherwise as
- * nmf_mu_workspace_size. */
+/* Workspace bytes of nmf_mu_step_route: it adds 4 m n bytes for two BF16
+ * terms of an FP32 X (X = bf16(X) + bf16(X - bf16(X))) where a tensor-core
+ * form that reads them may run -- with NTT_ROUTE_TC on 128 or 256 rows at rank
+ * 9..32 (n a multiple of 8), and on every route but NTT_ROUTE_FMA, _GENERIC
+ * and _TC on 17..32 rows at rank <= 8 (n a multiple of 64, the warp-level MMA
+ * form); otherwise as nmf_mu_workspace_size.  The plain nmf_mu_step never
+ * takes those forms. */
 ntt_status nmf_mu_workspace_size_route(int64_t m, int64_t n, int r, ntt_dtype x_dtype, int route,
                                       size_t* bytes);
 

@@ -136,7 +136,7 @@ class _Stats(ctypes.Structure):
 
 
 ENGINES = {0: "fma_pass", 1: "grouped", 2: "tc_bf16", 3: "tc_tf32", 4: "fma_narrow", 5: "bcd_pass",
-           6: "tc_split"}
+           6: "tc_split", 7: "tc_narrow"}
 SOLVERS = {"mu": 0, "bcd": 1}
 
 

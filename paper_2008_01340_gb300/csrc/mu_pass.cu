@@ -121,11 +121,21 @@ bool tcs_route_ok(int64_t m, int64_t n, int r, int route) {
 
 static bool narrow_enabled(int route) { return route != NTT_ROUTE_GENERIC; }
 
+// FP32 X of 17 to 32 rows at rank bucket 8 (n a multiple of 64) runs on the
+// warp-level MMA form (mu_pass_tcw.cu) where the caller provides the scratch of
+// its split X, except on the CUDA-core routes and on NTT_ROUTE_TC (which keeps
+// the stacked tcgen05 form there).
+bool tcw_route_ok(int64_t m, int64_t n, int r, int route) {
+  if (route == NTT_ROUTE_FMA || route == NTT_ROUTE_GENERIC || route == NTT_ROUTE_TC) return false;
+  return m > 16 && m <= 32 && r >= 1 && r <= 8 && n % 64 == 0;
+}
+
 void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
   s->tma = mu_tma_ok(*s, X, H) ? 1 : 0;
   s->tcb = 0;
   s->tcs = 0;
   s->narrow = 0;
+  s->tcw = 0;
   if (!s->bf16 && s->tma && s->split_ok && tcs_route_ok(s->m, s->n, s->r, s->route)) {
     s->tcs = 1;
     s->T = s->MP <= 32 ? 128 : 64;   // <= 32 rows: the stacked form's 128-column tiles
@@ -146,9 +156,21 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
     s->grid = (int)grid;
     return;
   }
+  if (!s->bf16 && s->tma && s->split_ok && tcw_route_ok(s->m, s->n, s->r, s->route)) {
+    s->tcw = 1;
+    s->T = 512;   // 8 warps x 64-column stages per CTA round
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+    return;
+  }
   if (s->tma && !s->bf16 && narrow_pass_supported(s->MP, s->R) && narrow_enabled(s->route)) {
-    s->narrow = 1;
-    s->T = 256;   // 8 warps x 32-column boxes per CTA round
+    // 32 rows with n a multiple of 32: the form whose copies move 256 bytes of
+    // every row (3-D tensor maps); else 32-column boxes
+    s->narrow = (s->MP == 32 && s->n % 32 == 0) ? 2 : 1;
+    s->T = s->narrow == 2 ? 512 : 256;   // 8 warps x 64- or 32-column stages per CTA round
     const int64_t ntiles = (s->n + s->T - 1) / s->T;
     int64_t grid = num_sms > 0 ? num_sms : 152;
     if (grid > ntiles) grid = ntiles;
@@ -194,12 +216,59 @@ ntt_status encode_bf16_atom_map(const void* base, int64_t rows, int64_t cols, in
   return e == CUDA_SUCCESS ? NTT_OK : NTT_ERR_CUDA;
 }
 
+ntt_status encode_tcw_maps(const MuShape& s, const __nv_bfloat16* X12, const float* H, CUtensorMap* mx,
+                           CUtensorMap* mh) {
+  auto fn = encode_fn();
+  if (!fn || s.n % 64 != 0) return NTT_ERR_CUDA;
+  {
+    // (64 columns, 2 n / 64 lines, rows): a box of one segment's two terms x all rows
+    cuuint64_t dims[3] = {64, (cuuint64_t)(2 * s.n / 64), (cuuint64_t)s.m};
+    cuuint64_t strides[2] = {128, (cuuint64_t)(s.n * 4)};
+    cuuint32_t box[3] = {64, 2, (cuuint32_t)s.MP};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (fn(mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(X12), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return NTT_ERR_CUDA;
+  }
+  {
+    // (32 columns, n / 32 halves, ranks): a box of two halves x the 8 rank rows
+    cuuint64_t dims[3] = {32, (cuuint64_t)(s.n / 32), (cuuint64_t)s.r};
+    cuuint64_t strides[2] = {128, (cuuint64_t)(s.n * 4)};
+    cuuint32_t box[3] = {32, 2, 8};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (fn(mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(H), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return NTT_ERR_CUDA;
+  }
+  return NTT_OK;
+}
+
 ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUtensorMap* mx,
                           CUtensorMap* mh) {
   auto fn = encode_fn();
   if (!fn) return NTT_ERR_CUDA;
   const int xb = s.bf16 ? 2 : 4;
   const int br = s.MP < 256 ? s.MP : 256;
+  if (s.narrow == 2) {
+    // (32 columns, n / 32 segments, rows): a box of 2 segments x all rows
+    // moves 256 contiguous bytes of every row; lines ordered (row, segment)
+    for (int t = 0; t < 2; ++t) {
+      const int64_t rows = t == 0 ? s.m : s.r;
+      const int64_t ld = t == 0 ? s.n : (s.ldh > 0 ? s.ldh : s.n);
+      cuuint64_t dims[3] = {32, (cuuint64_t)(s.n / 32), (cuuint64_t)rows};
+      cuuint64_t strides[2] = {128, (cuuint64_t)(ld * 4)};
+      cuuint32_t box[3] = {32, 2, (cuuint32_t)(t == 0 ? br : s.R)};
+      cuuint32_t es[3] = {1, 1, 1};
+      const CUresult e = fn(t == 0 ? mx : mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            t == 0 ? const_cast<void*>(X) : static_cast<void*>(const_cast<float*>(H)), dims, strides,
+                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (e != CUDA_SUCCESS) return NTT_ERR_CUDA;
+    }
+    return NTT_OK;
+  }
   {
     cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)s.m};
     cuuint64_t strides[1] = {(cuuint64_t)(s.n * xb)};
@@ -229,6 +298,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st) {
   if (s.tcs) return launch_mu_pass_tcs(s, d, eps, st);
+  if (s.tcw) return launch_mu_pass_tcw(s, d, eps, mx, mh, st);
   if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
   if (s.narrow) return launch_mu_pass_narrow(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \

@@ -37,8 +37,9 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
   mu_finalize_shape(&s, dev.X, dev.H, device_sms());
   if (engine)
     *engine = s.tcs ? NTT_ENGINE_TC_SPLIT
-                    : (s.tcb ? NTT_ENGINE_TC_BF16
-                             : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS));
+                    : (s.tcw ? NTT_ENGINE_TC_NARROW
+                             : (s.tcb ? NTT_ENGINE_TC_BF16
+                                      : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS)));
   MuDev d = dev;
   if (s.tcs) {
     // X = X1 + X2 (bf16(X) and bf16(X - bf16(X))), once for the whole loop
@@ -47,7 +48,13 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
     d.X = dev.xs;
     d.X2 = dev.xs + mn;
   }
-  if (s.tma && !s.tcs) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
+  if (s.tcw) {
+    // the same two terms, interleaved by 64-column segments, once for the whole loop
+    NTT_CUDA_TRY_NS(launch_split_x12(reinterpret_cast<const float*>(dev.X), dev.xs, s.m, s.n, st));
+    NTT_TRY_NS(encode_tcw_maps(s, dev.xs, dev.H, &mx, &mh));
+    d.X = dev.xs;
+  }
+  if (s.tma && !s.tcs && !s.tcw) NTT_TRY_NS(mu_encode_maps(s, dev.X, dev.H, &mx, &mh));
   for (int t = 0; t < iters; ++t) {
     NTT_CUDA_TRY_NS(launch_mu_pass(s, d, eps, mx, mh, st));
     NTT_CUDA_TRY_NS(launch_mu_combine(s, d, eps, t0 + t, st));
@@ -467,7 +474,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
       if (main_loop) p->st[s].engine = eng;
       // per iteration the pass and the combine's two launches; the split form's
       // X1, X2 once per loop
-      launches += 3LL * iters + (eng == NTT_ENGINE_TC_SPLIT ? 1 : 0);
+      launches += 3LL * iters + (eng == NTT_ENGINE_TC_SPLIT || eng == NTT_ENGINE_TC_NARROW ? 1 : 0);
       return e;
     }
     if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;
@@ -727,7 +734,8 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
       for (int64_t rp = auto_rank ? 1 : p->ranks_max[s]; rp <= p->ranks_max[s]; ++rp) {
         const int64_t m = rp * dims[s];
         for (int64_t r = auto_rank ? 1 : p->ranks_max[s + 1]; r <= p->ranks_max[s + 1]; ++r)
-          if (tcs_route_ok(m, n, (int)r, p->route) && !plan_route_group(m, n, (int)r, false, p->route))
+          if ((tcs_route_ok(m, n, (int)r, p->route) || tcw_route_ok(m, n, (int)r, p->route)) &&
+              !plan_route_group(m, n, (int)r, false, p->route))
             xs_bytes = std::max(xs_bytes, (size_t)(m * n) * 4);
       }
     }
@@ -1059,6 +1067,14 @@ ntt_status ntt_plan_get_stats(ntt_plan p, ntt_stats* out) {
 // ---------------------------------------------------------------------------
 // Single NMF
 // ---------------------------------------------------------------------------
+// Whether the single-NMF workspace holds the two BF16 terms of X: the split
+// tensor-core form with NTT_ROUTE_TC, the warp-level MMA form of <= 32 rows
+// wherever its route allows it.
+static bool mu_split_scratch(int64_t m, int64_t n, int r, ntt_dtype x_dtype, int route) {
+  if (x_dtype != NTT_F32) return false;
+  return (route == NTT_ROUTE_TC && tcs_route_ok(m, n, r, route)) || tcw_route_ok(m, n, r, route);
+}
+
 static MuWs mu_ws_layout(const MuShape& s, size_t* total, bool split = false) {
   Arena ar;
   MuWs w;
@@ -1081,8 +1097,7 @@ ntt_status nmf_mu_workspace_size_route(int64_t m, int64_t n, int r, ntt_dtype x_
   if (route < NTT_ROUTE_AUTO || route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
   MuShape s;
   NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
-  const bool split = route == NTT_ROUTE_TC && x_dtype == NTT_F32 && tcs_route_ok(m, n, r, route);
-  mu_ws_layout(s, bytes, split);
+  mu_ws_layout(s, bytes, mu_split_scratch(m, n, r, x_dtype, route));
   return NTT_OK;
 }
 
@@ -1095,16 +1110,29 @@ ntt_status nmf_mu_workspace_size(int64_t m, int64_t n, int r, ntt_dtype x_dtype,
   return NTT_OK;
 }
 
+static ntt_status nmf_mu_step_impl(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
+                                   float* H, int iters, float eps_mu, double* obj_dev, void* ws,
+                                   void* stream, int route, int* engine_out, bool split_ws);
+
+// The plain entry point keeps the workspace of nmf_mu_workspace_size (no
+// split X: the tensor-core forms that need one are left out).
 ntt_status nmf_mu_step(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
                        float* H, int iters, float eps_mu, double* obj_dev, void* ws,
                        void* stream) {
-  return nmf_mu_step_route(m, n, r, X, x_dtype, W, H, iters, eps_mu, obj_dev, ws, stream,
-                           NTT_ROUTE_AUTO, nullptr);
+  return nmf_mu_step_impl(m, n, r, X, x_dtype, W, H, iters, eps_mu, obj_dev, ws, stream,
+                          NTT_ROUTE_AUTO, nullptr, false);
 }
 
 ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
                              float* H, int iters, float eps_mu, double* obj_dev, void* ws,
                              void* stream, int route, int* engine_out) {
+  return nmf_mu_step_impl(m, n, r, X, x_dtype, W, H, iters, eps_mu, obj_dev, ws, stream, route,
+                          engine_out, true);
+}
+
+static ntt_status nmf_mu_step_impl(int64_t m, int64_t n, int r, const void* X, ntt_dtype x_dtype, float* W,
+                                   float* H, int iters, float eps_mu, double* obj_dev, void* ws,
+                                   void* stream, int route, int* engine_out, bool split_ws) {
   if (!X || !W || !H || !ws || iters < 0 || !(eps_mu >= 0.0f)) return NTT_ERR_INVALID_ARG;
   if (route < NTT_ROUTE_AUTO || route > NTT_ROUTE_TC) return NTT_ERR_INVALID_ARG;
   if (x_dtype != NTT_F32 && x_dtype != NTT_BF16) return NTT_ERR_INVALID_ARG;
@@ -1113,8 +1141,8 @@ ntt_status nmf_mu_step_route(int64_t m, int64_t n, int r, const void* X, ntt_dty
   MuShape s;
   NTT_TRY(mu_choose_shape(m, n, r, x_dtype == NTT_BF16, device_sms(), &s));
   size_t total = 0;
-  // the split tensor-core form only with NTT_ROUTE_TC (its terms take 4 m n bytes of workspace)
-  const bool split = route == NTT_ROUTE_TC && x_dtype == NTT_F32 && tcs_route_ok(m, n, r, route);
+  // the split X of the tensor-core forms takes 4 m n bytes of workspace
+  const bool split = split_ws && mu_split_scratch(m, n, r, x_dtype, route);
   MuWs L = mu_ws_layout(s, &total, split);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);

@@ -152,6 +152,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 // TMA tile store (shared -> global) tracked by the issuing thread's bulk group.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
   asm volatile(
@@ -318,7 +327,8 @@ struct MuShape {
   int tma = 0;       // X/H tiles loaded by TMA (else cooperative loads)
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
   int tcs = 0;       // FP32 X split in two BF16 matrices on the same tensor-core pass
-  int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X
+  int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X (2: its 3-D-copy form)
+  int tcw = 0;       // warp-level MMA pass on the interleaved split of FP32 X (<= 32 rows, rank bucket 8)
   int route = NTT_ROUTE_AUTO;   // ntt_route restricting the pass choice
   int split_ok = 0;  // scratch for the two BF16 terms of X exists (MuDev::xs)
   int64_t ldh = 0;   // row stride of H when it is a column block of a wider H (generic pass only)
@@ -416,6 +426,13 @@ cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16
                                 cudaStream_t st);
 // Warp-streamed FMA pass for 16/32-row buckets at rank bucket 8 (FP32 X, TMA-aligned).
 bool narrow_pass_supported(int MP, int R);
+bool tcw_pass_supported(int MP, int R, int64_t n);
+bool tcw_route_ok(int64_t m, int64_t n, int r, int route);
+cudaError_t launch_split_x12(const float* X, __nv_bfloat16* out, int64_t m, int64_t n, cudaStream_t st);
+ntt_status encode_tcw_maps(const MuShape& s, const __nv_bfloat16* X12, const float* H, CUtensorMap* mx,
+                           CUtensorMap* mh);
+cudaError_t launch_mu_pass_tcw(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
+                               const CUtensorMap& mh, cudaStream_t st);
 cudaError_t launch_mu_pass_narrow(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                                   const CUtensorMap& mh, cudaStream_t st);
 

@@ -486,18 +486,18 @@ def test_tensor_core_and_fma_passes_agree(ntt, m, n, r):
 @pytest.mark.parametrize("m,n,r", [(32, 40000, 8), (20, 36004, 5), (16, 8196, 8), (9, 100, 2),
                                    (32, 64, 8), (32, 2_000_000, 8), (1, 4096, 1)])
 def test_narrow_and_wide_passes_agree(ntt, m, n, r):
-    """The warp-streamed pass (FP32 X, <= 32 rows, rank <= 8: the default there)
+    """The warp-streamed FMA pass (FP32 X, <= 32 rows, rank <= 8: route "fma")
     and the generic pass (route "generic") both match the oracle's iterates
     within the FP32 tolerance, and the narrow pass repeats bitwise."""
     X = _x_matrix("lowrank", m, n, 91 + m)
     W0 = synth.uniform_matrix((m, r), 92)
     H0 = synth.uniform_matrix((r, n), 93)
     eng = []
-    Wn, Hn, on = _run_gpu_mu(ntt, X, W0, H0, 10, engine=eng)
-    Wn2, Hn2, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    Wn, Hn, on = _run_gpu_mu(ntt, X, W0, H0, 10, engine=eng, route="fma")
+    Wn2, Hn2, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="fma")
     assert np.array_equal(Wn, Wn2) and np.array_equal(Hn, Hn2)
     Ww, Hw, _ = _run_gpu_mu(ntt, X, W0, H0, 10, route="generic", engine=eng)
-    if n % 4 == 0:   # TMA-aligned rows: the narrow pass takes the default route
+    if n % 4 == 0:   # TMA-aligned rows: the narrow pass takes the FMA route
         assert eng == ["fma_narrow", "fma_pass"]
     Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
     for Wg, Hg in ((Wn, Hn), (Ww, Hw)):
@@ -508,12 +508,56 @@ def test_narrow_and_wide_passes_agree(ntt, m, n, r):
 
 
 def test_narrow_pass_reported_for_first_stage(ntt):
-    """A 32-row, rank-8 first stage of a plan runs on the narrow pass and says so."""
+    """A 32-row, rank-8 first stage of a plan runs on the warp-level MMA form
+    by default and on the narrow FMA pass with route "fma", and says so."""
     dims, ranks = (32, 16, 16, 8), (1, 8, 8, 4, 1)
     A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=5)
     cores, stats, *_ = _decompose(ntt, A, ranks, 5, 3)
     assert stats["status"] == "NTT_OK"
-    assert stats["stages"][0]["engine"] == "fma_narrow"
+    assert stats["stages"][0]["engine"] == "tc_narrow"
+    cores_f, stats_f, *_ = _decompose(ntt, A, ranks, 5, 3, route="fma")
+    assert stats_f["stages"][0]["engine"] == "fma_narrow"
+    cores_o, _ = oracle.ntt_decompose(A, ranks, 5, seed=3)
+    for k, (g, f, o) in enumerate(zip(cores, cores_f, cores_o)):
+        assert _fro_rel(g, o) <= REL_ITERATE * (k + 1), f"core {k}"
+        assert _fro_rel(f, o) <= REL_ITERATE * (k + 1), f"core {k}"
+
+
+# (m, n, r): 32 rows, rows below the bucket (17 .. 31), rank below the bucket,
+# one 64-column stage, fewer stages than warps, many stages per warp
+@pytest.mark.parametrize("m,n,r,kind", [(32, 40000, 8, "lowrank"), (32, 1 << 18, 8, "uniform"),
+                                        (20, 64 * 500, 6, "lowrank"), (17, 64 * 70, 8, "uniform"),
+                                        (32, 64, 8, "uniform"), (24, 1_999_936, 5, "lowrank"),
+                                        (32, 64 * 1217, 1, "uniform")])
+def test_mu_fp32_warp_mma_form(ntt, m, n, r, kind):
+    """FP32 X of 17..32 rows at rank <= 8, n a multiple of 64: the default
+    route runs the warp-level MMA form on X split once into bf16(X) and
+    bf16(X - bf16(X)); iterates within the FP32 bound of the FP64 oracle on
+    the unsplit X after 10 updates, the engine reported, a bitwise repeat."""
+    X = _x_matrix(kind, m, n, 23 + m)
+    W0 = synth.uniform_matrix((m, r), 24)
+    H0 = synth.uniform_matrix((r, n), 25)
+    eng = []
+    Wg, Hg, og = _run_gpu_mu(ntt, X, W0, H0, 10, engine=eng)
+    assert eng == ["tc_narrow"]
+    Wg2, Hg2, _ = _run_gpu_mu(ntt, X, W0, H0, 10)
+    assert np.array_equal(Wg, Wg2) and np.array_equal(Hg, Hg2)
+    Wo, Ho, tr = oracle.nmf_mu(X.astype(np.float64), W0, H0, 10)
+    assert _fro_rel(Wg, Wo) <= REL_ITERATE, _fro_rel(Wg, Wo)
+    assert _fro_rel(Hg, Ho) <= REL_ITERATE, _fro_rel(Hg, Ho)
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    assert np.allclose(og, tr, rtol=2e-3, atol=1e-6 * float(np.sum(X.astype(np.float64) ** 2)))
+
+
+@pytest.mark.parametrize("m,n", [(32, 40008), (16, 4096), (33, 4096)])
+def test_warp_mma_form_not_taken_outside_its_shapes(ntt, m, n):
+    """n not a multiple of 64, 16 rows or fewer, more than 32 rows: another pass runs."""
+    X = _x_matrix("uniform", m, n, 29)
+    W0 = synth.uniform_matrix((m, 8), 30)
+    H0 = synth.uniform_matrix((8, n), 31)
+    eng = []
+    _run_gpu_mu(ntt, X, W0, H0, 2, engine=eng)
+    assert eng and eng[0] != "tc_narrow"
 
 
 @pytest.mark.parametrize("x_dtype,refine", [("f32", 0), ("bf16", 3)])
