@@ -52,14 +52,15 @@ struct TwCfg {
   static constexpr int FIT = 220 * 1024 / kTwWarps / STAGE;
   static constexpr int S = FIT < 6 ? FIT : 6;
   static constexpr int WARP_BYTES = S * STAGE;
-  static constexpr int BAR_OFF = kTwWarps * WARP_BYTES;
+  static constexpr int STG_OFF = kTwWarps * WARP_BYTES;   // 1 KB H_new staging tile per warp
+  static constexpr int BAR_OFF = STG_OFF + kTwWarps * 1024;
   static constexpr int E = (MP + 8) * 8;        // partial floats per CTA: P rows, then Q rows
   static constexpr int RED_FLOATS = kTwWarps * (E + 64);   // + the transposed Q block
   static constexpr int SMEM = BAR_OFF + kTwWarps * S * 8 + 1024;
   static_assert(MP == 16 || MP == 32, "row bucket");
   static_assert(STAGE % 1024 == 0 && XBOX % 1024 == 0, "swizzle atoms of 1024 bytes");
   static_assert(S >= 2, "pipeline depth");
-  static_assert(RED_FLOATS * 4 <= BAR_OFF, "reduction scratch");
+  static_assert(RED_FLOATS * 4 <= STG_OFF, "reduction scratch");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -116,10 +117,11 @@ __device__ __forceinline__ void split3_pair(float2 v, uint32_t* t) {
   t[2] = pack_bf16(r1.x - b.x, r1.y - b.y);
 }
 
-// Byte offset of FP32 element (rank, col) of a stage's H box (col < 64).
-__device__ __forceinline__ uint32_t h_off(int rank, int col) {
-  const int line = rank * 2 + (col >> 5), w = col & 31;
-  return (uint32_t)(line * 128 + (((w >> 2) ^ (line & 7)) << 4) + (w & 3) * 4);
+// Compile-time part of the byte offset of H box element (i, c0 + g + 8 h)
+// (line 2 i + (c0 >> 5), chunk (A ^ (2 i & 6)) + ((g >> 2) ^ half) with
+// A = ((c0 & 31) >> 2) + 2 h); the lane adds ((g >> 2) ^ half) * 16 + (g & 3) * 4.
+__device__ __forceinline__ constexpr int h_ct(int i, int c0, int h) {
+  return (2 * i + (c0 >> 5)) * 128 + (((((c0 & 31) >> 2) + 2 * h) ^ ((2 * i) & 6)) << 4);
 }
 
 template <class C>
@@ -161,10 +163,14 @@ mu_pass_tcw_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
       bw[ks][0][h] = pack_bf16(w1, w1);
       bw[ks][1][h] = pack_bf16(w2, w2);
     }
-  // G rows 2t, 2t + 1 as pairs over i
-  float2 g2[8];
+  // G_W entries (2t, i) and (2t + 1, i), each as a pair for the lane's two columns
+  float2 ge[8], go[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) g2[i] = make_float2(p.G[(2 * t) * 8 + i], p.G[(2 * t + 1) * 8 + i]);
+  for (int i = 0; i < 8; ++i) {
+    const float a = p.G[(2 * t) * 8 + i], b = p.G[(2 * t + 1) * 8 + i];
+    ge[i] = make_float2(a, a);
+    go[i] = make_float2(b, b);
+  }
   __syncthreads();
 
   const int gw = blockIdx.x * kTwWarps + warp;
@@ -200,8 +206,34 @@ mu_pass_tcw_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
     for (int mt = 0; mt < MT; ++mt) accP[mt][i] = sumP[mt][i] = 0.0f;
   }
   const float eps = p.eps;
-  // ldmatrix lane roles: matrix j = lane >> 3, its row i = lane & 7
+  // ldmatrix lane roles: matrix j = lane >> 3, its row i = lane & 7.  The
+  // lane's row is line 16 x + li + 8 (lj >> 1) (Y, transposed) or
+  // 16 x + li + 8 (lj & 1) (P); line mod 8 = li, so the 16-byte chunk of
+  // columns 8 (2 ck) + 8 (lj & 1) (Y) is 2 ck ^ li ^ (lj & 1).
   const int lj = lane >> 3, li = lane & 7;
+  const uint32_t ly = (uint32_t)((li + 8 * (lj >> 1)) * 128), lamy = (uint32_t)(li ^ (lj & 1));
+  const uint32_t lp = (uint32_t)((li + 8 * (lj & 1)) * 128), lamp = (uint32_t)(li ^ (lj >> 1));
+  // H box element (i, c0 + g + 8 h): line 2 i + half (half = c0 >> 5), chunk
+  // (A ^ (2 i & 6)) + ((g >> 2) ^ half) with A = ((c0 & 31) >> 2) + 2 h, word
+  // g & 3: a compile-time part (h_ct) and the lane's part for half = 0, 1
+  const uint32_t hq0 = (uint32_t)(((g >> 2) << 4) + (g & 3) * 4);
+  const uint32_t hq1 = (uint32_t)((((g >> 2) ^ 1) << 4) + (g & 3) * 4);
+  // the warp's H_new staging tile: word (rank, col) at rank * 32 + (col ^ 8 pi(rank)),
+  // pi(k) = (k & 3) ^ (k >> 2): the lane's four stores (ranks 2t + e, columns
+  // g + 8 h) and its two B-fragment loads (rank g, columns 2t + 8 h, + 1) each
+  // cover the 32 banks once
+  float* stw = reinterpret_cast<float*>(smem + C::STG_OFF + warp * 1024);
+  auto pi = [](int kk) { return (kk & 3) ^ (kk >> 2); };
+  int sto[2][2], ldo[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) sto[e][h] = (2 * t + e) * 32 + ((g + 8 * h) ^ (8 * pi(2 * t + e)));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) ldo[h] = g * 32 + ((2 * t + 8 * h) ^ (8 * pi(g)));
+  float* Hr0 = p.H + (int64_t)(2 * t) * p.n;
+  float* Hr1 = p.H + (int64_t)(2 * t + 1) * p.n;
+  const bool w0 = 2 * t < p.r, w1 = 2 * t + 1 < p.r;
 
   bool err = false;
   int k = 0;
@@ -212,71 +244,69 @@ mu_pass_tcw_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
       err = true;
       break;
     }
-    uint8_t* xs = wbuf + s * C::STAGE;
-    uint8_t* hs = xs + C::XBOX;
+    const uint8_t* xs = wbuf + s * C::STAGE;
+    const uint8_t* hs = xs + C::XBOX;
     const uint32_t xs_u = smem_u32(xs);
-#pragma unroll 1
+#pragma unroll
     for (int ck = 0; ck < kSegCols / 16; ++ck) {
       const int c0 = ck * 16;
       // ---- Y^T = X^T W over the 2 MP lines, W1 and W2 in two chains
       float y1[4] = {0.f, 0.f, 0.f, 0.f}, y2[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint32_t xy = ((uint32_t)(2 * ck) ^ lamy) << 4;
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
-        // matrices: (lines +0, cols +0), (lines +0, cols +8), (lines +8, cols +0), (lines +8, cols +8)
-        const int line = 16 * ks + li + 8 * (lj >> 1);
-        const int chunk = (c0 >> 3) + (lj & 1);
         uint32_t a[4];
-        ldsm_x4_t(xs_u + line * 128 + ((chunk ^ (line & 7)) << 4), a);
+        ldsm_x4_t(xs_u + ks * 2048 + ly + xy, a);
         mma16816(y1, a, bw[ks][0][0], bw[ks][0][1]);
         mma16816(y2, a, bw[ks][1][0], bw[ks][1][1]);
       }
-      // ---- H update of (cols c0 + g, c0 + g + 8) x (ranks 2t, 2t + 1)
-      const int ca = c0 + g, cb = c0 + g + 8;
-      float2 gha = make_float2(0.f, 0.f), ghb = make_float2(0.f, 0.f);
+      // ---- H update of (cols ca = c0 + g, cb = c0 + g + 8) x (ranks 2t, 2t + 1)
+      const uint8_t* hb = hs + ((c0 >> 5) ? hq1 : hq0);
+      float2 hp[8];   // (H[i][ca], H[i][cb])
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const float ha = *reinterpret_cast<const float*>(hs + h_off(i, ca));
-        const float hb = *reinterpret_cast<const float*>(hs + h_off(i, cb));
-        gha = __ffma2_rn(g2[i], make_float2(ha, ha), gha);
-        ghb = __ffma2_rn(g2[i], make_float2(hb, hb), ghb);
+        hp[i].x = *reinterpret_cast<const float*>(hb + h_ct(i, c0, 0));
+        hp[i].y = *reinterpret_cast<const float*>(hb + h_ct(i, c0, 1));
       }
-      const float h0a0 = *reinterpret_cast<const float*>(hs + h_off(2 * t, ca));
-      const float h0a1 = *reinterpret_cast<const float*>(hs + h_off(2 * t + 1, ca));
-      const float h0b0 = *reinterpret_cast<const float*>(hs + h_off(2 * t, cb));
-      const float h0b1 = *reinterpret_cast<const float*>(hs + h_off(2 * t + 1, cb));
-      // D layout: y[0] = (col g, rank 2t), y[1] = (g, 2t + 1), y[2] = (g + 8, 2t), y[3] = (g + 8, 2t + 1)
-      const float na0 = fmaxf(0.0f, __fdividef(h0a0 * (y1[0] + y2[0]), gha.x + eps));
-      const float na1 = fmaxf(0.0f, __fdividef(h0a1 * (y1[1] + y2[1]), gha.y + eps));
-      const float nb0 = fmaxf(0.0f, __fdividef(h0b0 * (y1[2] + y2[2]), ghb.x + eps));
-      const float nb1 = fmaxf(0.0f, __fdividef(h0b1 * (y1[3] + y2[3]), ghb.y + eps));
+      float2 gk0 = make_float2(0.f, 0.f), gk1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        gk0 = __ffma2_rn(ge[i], hp[i], gk0);   // (G H)[2t][ca, cb]
+        gk1 = __ffma2_rn(go[i], hp[i], gk1);   // (G H)[2t + 1][ca, cb]
+      }
+      const float2 h0e = t == 0 ? hp[0] : (t == 1 ? hp[2] : (t == 2 ? hp[4] : hp[6]));
+      const float2 h0o = t == 0 ? hp[1] : (t == 1 ? hp[3] : (t == 2 ? hp[5] : hp[7]));
+      // D layout: y[0] = (col ca, rank 2t), y[1] = (ca, 2t + 1), y[2] = (cb, 2t), y[3] = (cb, 2t + 1)
+      const float na0 = fmaxf(0.0f, __fdividef(h0e.x * (y1[0] + y2[0]), gk0.x + eps));
+      const float na1 = fmaxf(0.0f, __fdividef(h0o.x * (y1[1] + y2[1]), gk1.x + eps));
+      const float nb0 = fmaxf(0.0f, __fdividef(h0e.y * (y1[2] + y2[2]), gk0.y + eps));
+      const float nb1 = fmaxf(0.0f, __fdividef(h0o.y * (y1[3] + y2[3]), gk1.y + eps));
       const int64_t gcol = (int64_t)seg * kSegCols + c0 + g;   // n % 64 == 0: in range
-      if (2 * t < p.r) {
-        p.H[(int64_t)(2 * t) * p.n + gcol] = na0;
-        p.H[(int64_t)(2 * t) * p.n + gcol + 8] = nb0;
+      if (w0) {
+        Hr0[gcol] = na0;
+        Hr0[gcol + 8] = nb0;
       }
-      if (2 * t + 1 < p.r) {
-        p.H[(int64_t)(2 * t + 1) * p.n + gcol] = na1;
-        p.H[(int64_t)(2 * t + 1) * p.n + gcol + 8] = nb1;
+      if (w1) {
+        Hr1[gcol] = na1;
+        Hr1[gcol + 8] = nb1;
       }
-      __syncwarp();   // every lane has read the old H of this chunk
-      *reinterpret_cast<float*>(hs + h_off(2 * t, ca)) = na0;
-      *reinterpret_cast<float*>(hs + h_off(2 * t + 1, ca)) = na1;
-      *reinterpret_cast<float*>(hs + h_off(2 * t, cb)) = nb0;
-      *reinterpret_cast<float*>(hs + h_off(2 * t + 1, cb)) = nb1;
+      __syncwarp();   // the previous chunk's fragment loads from the tile are done
+      stw[sto[0][0]] = na0;
+      stw[sto[1][0]] = na1;
+      stw[sto[0][1]] = nb0;
+      stw[sto[1][1]] = nb1;
       __syncwarp();
       // ---- B fragments of H_new^T (K = the chunk's 16 columns, N = rank g),
       // each split in three BF16 terms
       uint32_t hb0[3], hb1[3];
-      split3_pair(*reinterpret_cast<const float2*>(hs + h_off(g, c0 + 2 * t)), hb0);
-      split3_pair(*reinterpret_cast<const float2*>(hs + h_off(g, c0 + 2 * t + 8)), hb1);
+      split3_pair(*reinterpret_cast<const float2*>(stw + ldo[0]), hb0);
+      split3_pair(*reinterpret_cast<const float2*>(stw + ldo[1]), hb1);
       // ---- P_line += X_line H_new^T per 16-line tile
+      const uint32_t xp = ((uint32_t)(2 * ck) ^ lamp) << 4;
 #pragma unroll
       for (int mt = 0; mt < MT; ++mt) {
-        // matrices: (lines +0, cols +0), (lines +8, cols +0), (lines +0, cols +8), (lines +8, cols +8)
-        const int line = 16 * mt + li + 8 * (lj & 1);
-        const int chunk = (c0 >> 3) + (lj >> 1);
         uint32_t a[4];
-        ldsm_x4(xs_u + line * 128 + ((chunk ^ (line & 7)) << 4), a);
+        ldsm_x4(xs_u + mt * 2048 + lp + xp, a);
 #pragma unroll
         for (int h = 0; h < 3; ++h) mma16816(accP[mt], a, hb0[h], hb1[h]);
       }

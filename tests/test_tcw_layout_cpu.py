@@ -227,3 +227,55 @@ def test_split_layout_is_interleaved_by_segment():
         seg = X[:, sg * SEG:(sg + 1) * SEG]
         assert np.array_equal(out[:, sg * 2 * SEG:sg * 2 * SEG + SEG], bf16(seg))
         assert np.array_equal(out[:, sg * 2 * SEG + SEG:(sg + 1) * 2 * SEG], bf16(seg - bf16(seg)))
+
+
+def test_precomputed_lane_offsets_match_the_layout():
+    """The kernel's per-lane address parts: ldmatrix rows (a lane offset plus
+    2048 per K step or line tile, chunk 2 ck ^ lane constant), H box reads
+    (a compile-time part plus the lane's part for the 32-column half), and the
+    H_new staging tile (word rank * 32 + (col ^ 8 pi(rank))), whose four stores
+    and two 8-byte loads per lane each cover the 32 banks once."""
+    def h_ct(i, c0, h):
+        return (2 * i + (c0 >> 5)) * 128 + (((((c0 & 31) >> 2) + 2 * h) ^ ((2 * i) & 6)) << 4)
+
+    def pi(k):
+        return (k & 3) ^ (k >> 2)
+
+    for ck in range(4):
+        c0 = 16 * ck
+        for lane in range(32):
+            g, t, lj, li = lane >> 2, lane & 3, lane >> 3, lane & 7
+            ly, lamy = (li + 8 * (lj >> 1)) * 128, li ^ (lj & 1)
+            lp, lamp = (li + 8 * (lj & 1)) * 128, li ^ (lj >> 1)
+            for x in range(4):
+                line = 16 * x + li + 8 * (lj >> 1)
+                chunk = (c0 >> 3) + (lj & 1)
+                assert x * 2048 + ly + (((2 * ck) ^ lamy) << 4) == line * 128 + ((chunk ^ (line & 7)) << 4)
+                line = 16 * x + li + 8 * (lj & 1)
+                chunk = (c0 >> 3) + (lj >> 1)
+                assert x * 2048 + lp + (((2 * ck) ^ lamp) << 4) == line * 128 + ((chunk ^ (line & 7)) << 4)
+            hq = [((g >> 2) << 4) + (g & 3) * 4, (((g >> 2) ^ 1) << 4) + (g & 3) * 4]
+            for i in range(8):
+                for h in range(2):
+                    assert h_ct(i, c0, h) + hq[c0 >> 5] == h_off(i, c0 + g + 8 * h)
+    # staging tile
+    for e in range(2):
+        for h in range(2):
+            words = [(2 * (l & 3) + e) * 32 + (((l >> 2) + 8 * h) ^ (8 * pi(2 * (l & 3) + e))) for l in range(32)]
+            assert len({w % 32 for w in words}) == 32
+            assert all(0 <= w < 256 for w in words)
+    tile = {}
+    for lane in range(32):
+        g, t = lane >> 2, lane & 3
+        for e in range(2):
+            for h in range(2):
+                tile[(2 * t + e) * 32 + ((g + 8 * h) ^ (8 * pi(2 * t + e)))] = (2 * t + e, g + 8 * h)
+    for h in range(2):
+        for p0 in (0, 16):
+            banks = []
+            for lane in range(p0, p0 + 16):
+                g, t = lane >> 2, lane & 3
+                w = g * 32 + ((2 * t + 8 * h) ^ (8 * pi(g)))
+                assert tile[w] == (g, 2 * t + 8 * h) and tile[w + 1] == (g, 2 * t + 8 * h + 1)
+                banks += [w % 32, (w + 1) % 32]
+            assert len(set(banks)) == 32
