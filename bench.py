@@ -48,8 +48,8 @@ FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 f
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture, valid
 # only for the engine and kernel source it was measured on (hash of that file).
-NCU_TRAFFIC = {"engine": "fma_narrow", "kernel_file": "mu_pass_narrow.cu", "kernel_sha": "8c6b5110f25a4b89",
-               "bytes_per_launch": 6.300e9}   # 787.5 MB on 32 x 4194304, x 8 for 33554432 columns
+NCU_TRAFFIC = {"engine": "tc_narrow", "kernel_file": "mu_pass_tcw.cu", "kernel_sha": "8f9c365ea42af363",
+               "bytes_per_launch": 6.304e9}   # 788.0 MB on 32 x 4194304, x 8 for 33554432 columns
 
 
 def _env_int(name, default):
@@ -674,7 +674,8 @@ def main():
             and NCU_TRAFFIC["kernel_sha"] == _kernel_sha(NCU_TRAFFIC["kernel_file"])):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     kernel_of = {"fma_pass": "mu_pass_kernel", "grouped": "gpass_kernel", "tc_bf16": "mu_pass_tcs_kernel (BF16 form)",
-                 "tc_split": "mu_pass_tcs_kernel", "fma_narrow": "mu_pass_narrow_kernel"}
+                 "tc_split": "mu_pass_tcs_kernel", "fma_narrow": "mu_pass_narrow_kernel",
+                 "tc_narrow": "mu_pass_tcw_kernel"}
     kname = (f"{kernel_of.get(st1.get('engine'), st1.get('engine'))}<m={st1['m']},r={st1['r']},"
              f"{'bf16' if x_dtype == 'bf16' else 'f32'} X> + combine, "
              f"stage {dom + 1} ({st1['m']} x {st1['n']}, r={st1['r']})")
