@@ -8,9 +8,11 @@
 //
 // The unfolding is split once per stage into two BF16 matrices X1 = bf16(X)
 // and X2 = bf16(X - X1) (16 significand bits of X; the same HBM bytes per
-// iteration as FP32 X).  A tile covers 64 columns; its stage in shared memory
-// holds X1 in the first 64-column atom and X2 in the second (two TMA copies,
-// 128-byte swizzle).  Per tile:
+// iteration as FP32 X), stored tile-major as the stages' shared-memory image
+// (split_blocked_kernel): a tile covers 64 columns, 8-row groups of X1 and of
+// X2 alternate in 1024-byte swizzle atoms, and one contiguous bulk copy moves a
+// whole tile (a copy of 128 bytes of every row reached 4.7 TB/s on this read,
+// the contiguous tile 6.9).  Per tile:
 //   phase A  D_A (128 x 2R) = [X1 | X2]^T [W1 | W2]                 (K = rows)
 //            TMEM lane c holds X1^T W of column c, lane 64 + c X2^T W; the
 //            two W terms W1 = bf16(W), W2 = bf16(W - W1) (16 significand
@@ -70,6 +72,13 @@ struct TsCfg {
   static constexpr int KH = R / 2;              // ranks per TMEM lane group (two per column)
   static constexpr int HALF = KH / 2;           // ranks one epilogue thread updates
   static constexpr int XST = MP * 128 * 2;      // one stage: two atoms (X1 and X2, or 128 columns of X)
+  // Stage layout.  BF16 form: atom 0 (columns 0..63, MP rows of 128 bytes)
+  // then atom 1.  Split form: 1024-byte groups of 8 rows alternating X1, X2
+  // (row group g of X1 at 2 g KB, of X2 at 2 g + 1 KB), the image of the
+  // tile-major split buffer.  XLBO: offset of the second atom's data (the M
+  // step of phase A, the K step past 64 of phase B); XSBO: stride of 8-row groups.
+  static constexpr int XLBO = BX ? MP * 128 : 1024;
+  static constexpr int XSBO = BX ? 1024 : 2048;
   static constexpr int HATOMS = BX ? 2 : 1;     // atoms of an H_new stack (its tile's columns)
   static constexpr int HS = HATOMS * N3 * 128;  // one H_new stack: 3R rows per atom
   // Split form: two stacks (the epilogue of tile j writes one while phase B of
@@ -119,6 +128,9 @@ struct TsParams {
   int64_t n;
   int m, r, ntiles;
   float eps;
+  // split form: X1 and X2 stored tile by tile as the stages' shared-memory
+  // image (split_blocked_kernel): tile t is XST contiguous bytes at xblk + t XST
+  const uint8_t* xblk;
 };
 
 // Named barrier 1 over the 256 epilogue threads.
@@ -150,12 +162,11 @@ __device__ __forceinline__ void tmem_ld_kh(uint32_t taddr, float* v) {
     tmem_ld8(taddr, v);
 }
 
-// tmX1 / tmX2: TMA maps of X1 and X2 (64-column boxes of MP rows, 128-byte
-// swizzle: the layout of a stage's two atoms; rows past m and columns past n
-// arrive as zeros).
+// tmX1: the BF16 form's TMA map of X (64-column boxes of MP rows, 128-byte
+// swizzle; rows past m and columns past n arrive as zeros); the split form
+// copies p.xblk and takes no map.
 template <class C>
 __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid_constant__ CUtensorMap tmX1,
-                                                                    const __grid_constant__ CUtensorMap tmX2,
                                                                     const TsParams p) {
   constexpr int MP = C::MP, R = C::R, N2 = C::N2, N3 = C::N3, KH = C::KH, HALF = C::HALF, S = C::S;
   pdl_wait();      // the previous kernel's W, G and stop word
@@ -251,15 +262,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         const int col0 = ((int)blockIdx.x + t * (int)gridDim.x) * C::TC;
         const uint32_t dst = sbase + C::OFF_X + s * C::XST;
         mbar_arrive_expect_tx(full(s), C::TX);
+        if constexpr (C::BX) {
 #pragma unroll
-        for (int h = 0; h < MP / C::BOXR; ++h) {
-          if constexpr (C::BX) {   // columns col0 .. col0 + 63 and col0 + 64 .. col0 + 127 of X
+          for (int h = 0; h < MP / C::BOXR; ++h) {   // columns col0 .. col0 + 63 and col0 + 64 .. col0 + 127 of X
             tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
             tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX1, col0 + 64, h * C::BOXR, full(s));
-          } else {                 // X1 and X2 of columns col0 .. col0 + 63
-            tma_load_2d(dst + h * C::BOXR * 128, &tmX1, col0, h * C::BOXR, full(s));
-            tma_load_2d(dst + MP * 128 + h * C::BOXR * 128, &tmX2, col0, h * C::BOXR, full(s));
           }
+        } else {   // X1 and X2 of columns col0 .. col0 + 63: one contiguous copy of the tile's image
+          bulk_load(dst, p.xblk + (size_t)(col0 / C::TC) * C::XST, C::XST, full(s));
         }
       }
       // every copy issued has landed before the CTA ends (the last one of each stage)
@@ -280,10 +290,10 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
       // phase A of local tile t (stage s) into D_A[t & 1]: M = the 128 lanes of
       // [X1 | X2] (MN-major, LBO = the atom stride), K = the rows
       auto phase_a = [&](int t, int s) {
-        const uint64_t dX = smem_desc(sbase + C::OFF_X + s * C::XST, MP * 128, 1024, kLayoutSw128);
+        const uint64_t dX = smem_desc(sbase + C::OFF_X + s * C::XST, C::XLBO, C::XSBO, kLayoutSw128);
 #pragma unroll
         for (int kk = 0; kk < MP / 16; ++kk)
-          mma_bf16(dA(t & 1), dX + (uint64_t)((kk * 2048) >> 4),
+          mma_bf16(dA(t & 1), dX + (uint64_t)((kk * 2 * C::XSBO) >> 4),
                    dW + (uint64_t)((((kk >> 2) * N2 * 128) + (kk & 3) * 32) >> 4), C::IDA, kk > 0 ? 1u : 0u);
         mma_commit(barA(t & 1));
       };
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
         const uint32_t xb = sbase + C::OFF_X + s * C::XST;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const uint32_t xo = (uint32_t)((kk >> 2) * MP * 128 + (kk & 3) * 32);
+          const uint32_t xo = (uint32_t)((kk >> 2) * C::XLBO + (kk & 3) * 32);
           const uint32_t acc = (t % C::FLUSH != 0 || kk > 0) ? 1u : 0u;
           // BF16 form: the second atom holds columns 64.., so does the stack's;
           // split form: both atoms are the same columns, Q once
@@ -302,7 +312,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
           const uint64_t dh = smem_desc(hb + ha + (kk & 3) * 32, 16, 1024, kLayoutSw128);
 #pragma unroll
           for (int mb = 0; mb < C::NMB; ++mb)
-            mma_bf16(dB(mb), smem_desc(xb + mb * 128 * 128 + xo, 16, 1024, kLayoutSw128), dh, C::IDB, acc);
+            mma_bf16(dB(mb), smem_desc(xb + mb * 16 * C::XSBO + xo, 16, C::XSBO, kLayoutSw128), dh, C::IDB, acc);
           if (C::BX || kk < 4) mma_bf16(dB(C::NMB), dh, dh, C::IDB, acc);
         }
         mma_commit(empty(s));
@@ -607,15 +617,76 @@ cudaError_t launch_tcs_cfg(const MuShape& s, const MuDev& d, float eps, cudaStre
   p.r = s.r;
   p.ntiles = (int)((s.n + C::TC - 1) / C::TC);
   p.eps = eps;
-  CUtensorMap m1, m2;
+  p.xblk = reinterpret_cast<const uint8_t*>(d.X);
+  CUtensorMap m1;
   std::memset(&m1, 0, sizeof(m1));
-  std::memset(&m2, 0, sizeof(m2));
-  if (encode_bf16_atom_map(d.X, s.m, s.n, C::BOXR, &m1) != NTT_OK) return cudaErrorInvalidValue;
-  if (!C::BX && encode_bf16_atom_map(d.X2, s.m, s.n, C::BOXR, &m2) != NTT_OK) return cudaErrorInvalidValue;
-  return launch_pdl(mu_pass_tcs_kernel<C>, dim3(s.grid), dim3(kTsThreads), C::SMEM, st, m1, m2, p);
+  if (C::BX && encode_bf16_atom_map(d.X, s.m, s.n, C::BOXR, &m1) != NTT_OK) return cudaErrorInvalidValue;
+  if (!C::BX && (reinterpret_cast<uintptr_t>(d.X) & 15)) return cudaErrorInvalidValue;
+  return launch_pdl(mu_pass_tcs_kernel<C>, dim3(s.grid), dim3(kTsThreads), C::SMEM, st, m1, p);
 }
 
 }  // namespace
+
+// X (m x n FP32) -> the split form's tile-major image: tile t (64 columns),
+// 8-row group g, term e (X1 = bf16(X), X2 = bf16(X - X1)) at byte
+// ((t MP / 8 + g) 2 + e) 1024; row r8 of the group at r8 128, its 16-byte
+// chunk c at (c ^ r8) 16 (the 128-byte swizzle of a 1024-byte-aligned atom).
+// Rows past m and columns past n are zeros.
+__global__ void split_blocked_kernel(const float* X, uint8_t* out, int64_t m, int64_t n, int MP, int64_t ntiles) {
+  const int64_t total = ntiles * MP * 8;   // (tile, row, chunk)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const int c = (int)(q & 7);
+    const int64_t rowt = q >> 3;
+    const int row = (int)(rowt % MP);
+    const int64_t t = rowt / MP;
+    const int64_t col = t * 64 + c * 8;
+    float v[8];
+    if (row < m && col + 8 <= n) {
+      const float4 a = *reinterpret_cast<const float4*>(X + row * n + col);
+      const float4 b = *reinterpret_cast<const float4*>(X + row * n + col + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (row < m && col + j < n) ? X[row * n + col + j] : 0.0f;
+    }
+    uint32_t t1[4], t2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      const float2 hf = __bfloat1622float2(h);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+      t1[j] = *reinterpret_cast<const uint32_t*>(&h);
+      t2[j] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    const int g = row >> 3, r8 = row & 7;
+    uint8_t* base = out + ((t * (MP / 8) + g) * 2) * 1024 + r8 * 128 + ((c ^ r8) << 4);
+    *reinterpret_cast<uint4*>(base) = make_uint4(t1[0], t1[1], t1[2], t1[3]);
+    *reinterpret_cast<uint4*>(base + 1024) = make_uint4(t2[0], t2[1], t2[2], t2[3]);
+  }
+}
+
+size_t split_blocked_bytes(int64_t n, int MP) { return (size_t)((n + 63) / 64) * (size_t)MP * 256; }
+
+// Bytes of the two BF16 terms of an FP32 X: m x n x 4, or for the split
+// tensor-core form's tile-major image (128..512 rows) whole 64-column tiles of
+// the padded row count.
+size_t split_scratch_bytes(int64_t m, int64_t n) {
+  int MP = 16;
+  while (MP < m) MP *= 2;
+  const size_t plain = (size_t)(m * n) * 4;
+  return MP >= 128 ? std::max(plain, split_blocked_bytes(n, MP)) : plain;
+}
+
+cudaError_t launch_split_blocked(const float* X, void* out, int64_t m, int64_t n, int MP, cudaStream_t st) {
+  const int64_t ntiles = (n + 63) / 64;
+  const int64_t total = ntiles * MP * 8;
+  int64_t grid = (total + kAuxThreads - 1) / kAuxThreads;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  split_blocked_kernel<<<(unsigned)grid, kAuxThreads, 0, st>>>(X, reinterpret_cast<uint8_t*>(out), m, n, MP, ntiles);
+  return cudaGetLastError();
+}
 
 bool tcs_pass_supported(int MP, int R) {
   return ((MP == 128 || MP == 256) && (R == 16 || R == 32)) || (MP == 512 && R == 16) || tcn_pass_supported(MP, R);

@@ -41,12 +41,17 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
                              : (s.tcb ? NTT_ENGINE_TC_BF16
                                       : (s.narrow ? NTT_ENGINE_FMA_NARROW : NTT_ENGINE_FMA_PASS)));
   MuDev d = dev;
-  if (s.tcs) {
-    // X = X1 + X2 (bf16(X) and bf16(X - bf16(X))), once for the whole loop
+  if (s.tcs && s.MP <= 32) {
+    // the stacked form: X = X1 + X2 (bf16(X) and bf16(X - bf16(X))), once for the whole loop
     const int64_t mn = s.m * s.n;
     NTT_CUDA_TRY_NS(launch_split_bf16x2(reinterpret_cast<const float*>(dev.X), dev.xs, dev.xs + mn, mn, st));
     d.X = dev.xs;
     d.X2 = dev.xs + mn;
+  } else if (s.tcs) {
+    // the same two terms as the tile-major image of the pass's stages
+    NTT_CUDA_TRY_NS(launch_split_blocked(reinterpret_cast<const float*>(dev.X), dev.xs, s.m, s.n, s.MP, st));
+    d.X = dev.xs;
+    d.X2 = nullptr;
   }
   if (s.tcw) {
     // the same two terms, interleaved by 64-column segments, once for the whole loop
@@ -736,7 +741,7 @@ ntt_status ntt_plan_create(const ntt_plan_desc* desc, ntt_plan* out) {
         for (int64_t r = auto_rank ? 1 : p->ranks_max[s + 1]; r <= p->ranks_max[s + 1]; ++r)
           if ((tcs_route_ok(m, n, (int)r, p->route) || tcw_route_ok(m, n, (int)r, p->route)) &&
               !plan_route_group(m, n, (int)r, false, p->route))
-            xs_bytes = std::max(xs_bytes, (size_t)(m * n) * 4);
+            xs_bytes = std::max(xs_bytes, split_scratch_bytes(m, n));
       }
     }
   size_t bcd_bytes = 0;
@@ -1085,7 +1090,7 @@ static MuWs mu_ws_layout(const MuShape& s, size_t* total, bool split = false) {
   w.red = ar.take((size_t)s.part_stride() * 4);
   w.part = ar.take(mu_partial_floats(s) * 4);
   w.part64 = ar.take(2 * kMaxResidBlocks * sizeof(double));
-  w.xs = split ? ar.take((size_t)s.m * s.n * 4) : 0;
+  w.xs = split ? ar.take(split_scratch_bytes(s.m, s.n)) : 0;
   *total = ar.off;
   return w;
 }

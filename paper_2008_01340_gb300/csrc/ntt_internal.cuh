@@ -427,6 +427,9 @@ cudaError_t launch_split_bf16x2(const float* X, __nv_bfloat16* X1, __nv_bfloat16
 // Warp-streamed FMA pass for 16/32-row buckets at rank bucket 8 (FP32 X, TMA-aligned).
 bool narrow_pass_supported(int MP, int R);
 bool tcw_pass_supported(int MP, int R, int64_t n);
+size_t split_blocked_bytes(int64_t n, int MP);
+size_t split_scratch_bytes(int64_t m, int64_t n);
+cudaError_t launch_split_blocked(const float* X, void* out, int64_t m, int64_t n, int MP, cudaStream_t st);
 bool tcw_route_ok(int64_t m, int64_t n, int r, int route);
 cudaError_t launch_split_x12(const float* X, __nv_bfloat16* out, int64_t m, int64_t n, cudaStream_t st);
 ntt_status encode_tcw_maps(const MuShape& s, const __nv_bfloat16* X12, const float* H, CUtensorMap* mx,
