@@ -651,9 +651,19 @@ def main():
     for _ in range(e2e_steps):
         ntt.ntt_decompose_host(plan, A_host, cores_h, ws_host, err_h, stream)
     f1.record(stream)
+    enqueue_ms = (time.perf_counter() - t0) * 1e3   # host time to enqueue every step (no waits inside)
     torch.cuda.synchronize(dev)
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    # the host-to-device copy of one step's input alone, for reading the e2e figure
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        Ad.copy_(A_host, non_blocking=True)
+        g1.record(stream)
+    torch.cuda.synchronize(dev)
+    h2d_alone_ms = g0.elapsed_time(g1)
     h2d = N * 4
     d2h = sum(math.prod(s) for s in plan.core_shapes()) * 4 + 3 * 8
 
@@ -723,7 +733,9 @@ def main():
                    "parallelism": f"independent jobs x{world}"},
         "roofline": roofline,
         "e2e": {"value": round(whole_job_rate(world, e2e_ms), 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+                "host_enqueue_ms": round(enqueue_ms, 2), "h2d_alone_ms": round(h2d_alone_ms, 2),
+                "input_pinned": bool(A_host.is_pinned())},
         "gpu_launches": launches,
         "clocks": clocks,
         "rel_error": rel_err,
