@@ -370,9 +370,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
 #pragma unroll
       for (int l = 0; l < R; ++l) hv[l] = (l < r && col_ < n) ? p.H[(int64_t)l * n + col_] : 0.0f;
     };
-    float hnext[PREFETCH_H ? R : 1];
+    // split form at rank 16: two tiles ahead (the loads wait on DRAM under a
+    // full copy stream; one tile of epilogue did not cover them)
+    constexpr bool AHEAD2 = !C::BX && R <= 16;
+    float hnext[PREFETCH_H ? R : 1], hnext2[AHEAD2 ? R : 1];
     if constexpr (PREFETCH_H) {
       if (count > 0) load_h((int)blockIdx.x, hnext);
+      if constexpr (AHEAD2)
+        if (count > 1) load_h((int)blockIdx.x + (int)gridDim.x, hnext2);
     }
     // rank bucket 16: the G rows of this thread's ranks in registers (their
     // shared-memory reads otherwise take a large share of the pass's
@@ -432,7 +437,13 @@ __global__ void __launch_bounds__(kTsThreads, 1) mu_pass_tcs_kernel(const __grid
       if constexpr (PREFETCH_H) {
 #pragma unroll
         for (int l = 0; l < R; ++l) h[l] = hnext[l];
-        if (j + 1 < count) load_h(tile + (int)gridDim.x, hnext);
+        if constexpr (AHEAD2) {
+#pragma unroll
+          for (int l = 0; l < R; ++l) hnext[l] = hnext2[l];
+          if (j + 2 < count) load_h(tile + 2 * (int)gridDim.x, hnext2);
+        } else {
+          if (j + 1 < count) load_h(tile + (int)gridDim.x, hnext);
+        }
       } else {
         load_h(tile, h);
       }
