@@ -587,6 +587,102 @@ def sharded_nmf_mu(X_shard, W, H_shard, iters, ops, all_reduce=None):
     return trace
 
 
+def shard_bounds(n, world):
+    """Contiguous column blocks of n columns over `world` ranks: rank p owns
+    columns bounds[p] .. bounds[p + 1] - 1 (block sizes differ by at most one)."""
+    return [int(n) * p // int(world) for p in range(int(world) + 1)]
+
+
+def handoff_plan(r, n, n_next_dim, world):
+    """The exchange that turns a column-sharded H (r x n, blocks shard_bounds(n,
+    world)) into the column-sharded next unfolding X' = reshape(H, r n_next_dim,
+    n / n_next_dim) (C order: X'[i n_next_dim + j, c] = H[i, j n' + c], n' =
+    n / n_next_dim).  Returns (n', sends) with sends[q][p] = the H columns, in
+    increasing order, that rank q sends to rank p: those j n' + c owned by q
+    with c in p's block of X'.  Every column of H goes to exactly one rank."""
+    if n % n_next_dim:
+        raise ValueError("n must be a multiple of the next mode size")
+    n2 = n // n_next_dim
+    hb, xb = shard_bounds(n, world), shard_bounds(n2, world)
+    sends = [[[] for _ in range(world)] for _ in range(world)]
+    for q in range(world):
+        for k in range(hb[q], hb[q + 1]):
+            c = k % n2
+            p = next(i for i in range(world) if xb[i] <= c < xb[i + 1])
+            sends[q][p].append(k)
+    return n2, sends
+
+
+def sharded_ntt_decompose(X_shard, dims, ranks, iters, rank, world, ops_factory, init, all_reduce=None,
+                          exchange=None):
+    """Algorithm 2 on column-sharded unfoldings (Section III-B's 1-D column
+    distribution), every stage's NMF by sharded_nmf_mu.  This rank holds the
+    columns shard_bounds(n, world)[rank] .. of the first unfolding (dims[0] x
+    prod(dims[1:])).  Per stage: the sharded MU iterations (all-reduce of
+    [P ; Q]), the column-L1 hand-off of W (replicated) folded into this rank's H
+    rows, the core from W, then the exchange of H columns that lays out the next
+    unfolding in the same column blocks (handoff_plan: an all-to-all; the last
+    core, H of the last stage, is gathered on every rank).
+      ops_factory(m, n_shard, r): ShardOps (or any object with its interface)
+      init(m, n, r, stage, c0, c1): (W0 m x r, H0 columns c0 .. c1 - 1), the
+        unsharded initial factors' values (the counter RNG is column-indexable)
+      all_reduce(t): in-place sum over the ranks (None on one rank)
+      exchange(sends): sends[p] = tensor (rows x k_p) for rank p; returns the
+        list of tensors received from every rank (None on one rank).
+    Returns (cores, traces): cores as tensors on every rank."""
+    import torch
+    d = len(dims)
+    if len(ranks) != d + 1 or ranks[0] != 1 or ranks[-1] != 1:
+        raise ValueError("ranks must have d + 1 entries with r_0 = r_d = 1")
+    xchg = exchange or (lambda sends: sends)
+    cores, traces = [], []
+    X = X_shard
+    for s in range(d - 1):
+        m, r = ranks[s] * dims[s], ranks[s + 1]
+        n = 1
+        for v in dims[s + 1:]:
+            n *= v
+        b = shard_bounds(n, world)
+        c0, c1 = b[rank], b[rank + 1]
+        if X.shape != (m, c1 - c0):
+            raise ValueError(f"stage {s}: this rank's unfolding block must be {m} x {c1 - c0}")
+        W0, H0 = init(m, n, r, s, c0, c1)
+        W = W0.clone()
+        H = H0.clone()
+        traces.append(sharded_nmf_mu(X, W, H, iters, ops_factory(m, c1 - c0, r), all_reduce))
+        # column-L1 hand-off: W's column sums are the same on every rank
+        norms = W.sum(dim=0)
+        scale = torch.where(norms > 0, norms, torch.ones_like(norms))
+        W = W / scale
+        H = H * scale[:, None]
+        cores.append(W.reshape(ranks[s], dims[s], r))
+        last = s == d - 2
+        if last:
+            # the last core: every rank's H columns to every rank
+            got = xchg([H for _ in range(world)])
+            cores.append(torch.cat(list(got), dim=1).reshape(r, dims[d - 1], 1))
+            break
+        n2, plan = handoff_plan(r, n, dims[s + 1], world)
+        sends = []
+        for p in range(world):
+            cols = torch.tensor(plan[rank][p], dtype=torch.long) - c0
+            sends.append(H[:, cols.to(H.device)].contiguous() if cols.numel() else H[:, :0].contiguous())
+        got = xchg(sends)
+        xb = shard_bounds(n2, world)
+        e0, e1 = xb[rank], xb[rank + 1]
+        Xn = H.new_zeros((r * dims[s + 1], e1 - e0))
+        for q in range(world):
+            ks = torch.tensor(plan[q][rank], dtype=torch.long)
+            if ks.numel() == 0:
+                continue
+            j, c = ks // n2, ks % n2 - e0
+            blk = got[q]                                  # r x len(ks), columns in increasing k
+            for i in range(r):
+                Xn[i * dims[s + 1] + j.to(Xn.device), c.to(Xn.device)] = blk[i]
+        X = Xn
+    return cores, traces
+
+
 def _many_args(Xs, Ws, Hs):
     import torch
     count = len(Xs)

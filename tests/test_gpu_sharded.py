@@ -80,3 +80,24 @@ def test_driver_with_one_shard_equals_nmf_mu_step(ntt):
     torch.cuda.synchronize()
     assert _rel(W.cpu(), Wd.cpu()) <= 1e-6 and _rel(H.cpu(), Hd.cpu()) <= 1e-6
     assert len(trace) == 6 and all(np.diff(trace) <= 1e-9 * trace[0])
+
+
+def test_sharded_ntt_driver_one_rank_on_device(ntt):
+    """The sharded nTT driver (stage hand-off included) with the library's
+    device ShardOps on one rank: its cores against the FP64 oracle's, within
+    the chained per-core bound used for every decomposition (1e-4 (k + 1))."""
+    dims, ranks, iters, seed = (8, 12, 10, 9), (1, 4, 6, 3, 1), 10, 21
+    A, _ = synth.tt_tensor(dims, ranks, "uniform", 0.01, seed=6)
+    X1 = torch.from_numpy(np.ascontiguousarray(A.reshape(dims[0], -1).astype(np.float32))).cuda()
+
+    def init(m, n, r, stage, c0, c1):
+        W0, H0 = oracle.init_factors(m, n, r, seed, stage, 0)
+        return (torch.from_numpy(np.asarray(W0, np.float32)).cuda(),
+                torch.from_numpy(np.ascontiguousarray(np.asarray(H0, np.float32)[:, c0:c1])).cuda())
+
+    cores, _ = ntt.sharded_ntt_decompose(X1, dims, ranks, iters, 0, 1, ntt.ShardOps, init)
+    torch.cuda.synchronize()
+    cores_o, _ = oracle.ntt_decompose(A.astype(np.float64), ranks, iters, seed=seed)
+    for k, (g, o) in enumerate(zip(cores, cores_o)):
+        assert tuple(g.shape) == o.shape
+        assert _rel(g.cpu().numpy(), o) <= 1e-4 * (k + 1), f"core {k}"
