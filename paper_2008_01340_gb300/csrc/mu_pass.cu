@@ -146,6 +146,16 @@ void mu_finalize_shape(MuShape* s, const void* X, const float* H, int num_sms) {
     s->grid = (int)grid;
     return;
   }
+  if (s->bf16 && s->tma && tcwb_route_ok(s->m, s->n, s->r, s->route)) {
+    s->tcw = 1;
+    s->T = 512;   // 8 warps x 64-column stages per CTA round
+    const int64_t ntiles = (s->n + s->T - 1) / s->T;
+    int64_t grid = num_sms > 0 ? num_sms : 152;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > s->grid_cap) grid = s->grid_cap;
+    s->grid = (int)grid;
+    return;
+  }
   if (s->bf16 && s->tma && s->n % 8 == 0 && tcb_pass_supported(s->MP, s->R) && tcb_enabled(s->MP, s->route)) {
     s->tcb = 1;
     s->T = 128;
@@ -214,6 +224,23 @@ ntt_status encode_bf16_atom_map(const void* base, int64_t rows, int64_t cols, in
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return e == CUDA_SUCCESS ? NTT_OK : NTT_ERR_CUDA;
+}
+
+ntt_status encode_tcwb_maps(const MuShape& s, const void* X, const float* H, CUtensorMap* mx, CUtensorMap* mh) {
+  auto fn = encode_fn();
+  if (!fn || s.n % 64 != 0) return NTT_ERR_CUDA;
+  // X: 64-column boxes of the 16 rows (128-byte swizzle)
+  if (encode_bf16_atom_map(X, s.m, s.n, 16, mx) != NTT_OK) return NTT_ERR_CUDA;
+  // H: (32 columns, n / 32 halves, ranks), a box of two halves x the 16 rank rows
+  cuuint64_t dims[3] = {32, (cuuint64_t)(s.n / 32), (cuuint64_t)s.r};
+  cuuint64_t strides[2] = {128, (cuuint64_t)(s.n * 4)};
+  cuuint32_t box[3] = {32, 2, 16};
+  cuuint32_t es[3] = {1, 1, 1};
+  if (fn(mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(H), dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return NTT_ERR_CUDA;
+  return NTT_OK;
 }
 
 ntt_status encode_tcw_maps(const MuShape& s, const __nv_bfloat16* X12, const float* H, CUtensorMap* mx,
@@ -298,7 +325,7 @@ ntt_status mu_encode_maps(const MuShape& s, const void* X, const float* H, CUten
 cudaError_t launch_mu_pass(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
                            const CUtensorMap& mh, cudaStream_t st) {
   if (s.tcs) return launch_mu_pass_tcs(s, d, eps, st);
-  if (s.tcw) return launch_mu_pass_tcw(s, d, eps, mx, mh, st);
+  if (s.tcw) return s.bf16 ? launch_mu_pass_tcwb(s, d, eps, mx, mh, st) : launch_mu_pass_tcw(s, d, eps, mx, mh, st);
   if (s.tcb) return launch_mu_pass_tcb(s, d, eps, st);
   if (s.narrow) return launch_mu_pass_narrow(s, d, eps, mx, mh, st);
 #define NTT_CASE(MPV)                                                       \

@@ -53,7 +53,9 @@ ntt_status run_mu_iters(const MuShape& shp, const MuDev& dev, float eps, int ite
     d.X = dev.xs;
     d.X2 = nullptr;
   }
-  if (s.tcw) {
+  if (s.tcw && s.bf16) {
+    NTT_TRY_NS(encode_tcwb_maps(s, dev.X, dev.H, &mx, &mh));
+  } else if (s.tcw) {
     // the same two terms, interleaved by 64-column segments, once for the whole loop
     NTT_CUDA_TRY_NS(launch_split_x12(reinterpret_cast<const float*>(dev.X), dev.xs, s.m, s.n, st));
     NTT_TRY_NS(encode_tcw_maps(s, dev.xs, dev.H, &mx, &mh));
@@ -350,6 +352,8 @@ bool plan_route_group(int64_t m, int64_t n, int r, bool xbf16, int route, bool s
   // FP32 stages of 128/256 rows at rank 16/32: the split tensor-core form
   if (!xbf16 && split_ok && tcs_route_ok(m, n, r, route)) return false;
   if (route != NTT_ROUTE_FMA && xbf16 && tcb_pass_supported(MP, R) && MP >= 128) return false;
+  // BF16 stages of <= 16 rows at rank 9..16: the warp-level MMA form
+  if (xbf16 && tcwb_route_ok(m, n, r, route)) return false;
   return MP <= 256 && R >= 16;
 }
 
@@ -479,7 +483,7 @@ ntt_status enqueue_stage(ntt_plan p, int s, const float* A, float* const* cores,
       if (main_loop) p->st[s].engine = eng;
       // per iteration the pass and the combine's two launches; the split form's
       // X1, X2 once per loop
-      launches += 3LL * iters + (eng == NTT_ENGINE_TC_SPLIT || eng == NTT_ENGINE_TC_NARROW ? 1 : 0);
+      launches += 3LL * iters + (eng == NTT_ENGINE_TC_SPLIT || (eng == NTT_ENGINE_TC_NARROW && !shp.bf16) ? 1 : 0);
       return e;
     }
     if (main_loop) p->st[s].engine = NTT_ENGINE_GROUPED;

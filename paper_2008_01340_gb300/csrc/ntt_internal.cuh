@@ -328,7 +328,8 @@ struct MuShape {
   int tcb = 0;       // BF16-X tensor-core pass (kind::f16, three-term split of the factors)
   int tcs = 0;       // FP32 X split in two BF16 matrices on the same tensor-core pass
   int narrow = 0;    // warp-streamed FMA pass for <= 32 rows, rank bucket 8, FP32 X (2: its 3-D-copy form)
-  int tcw = 0;       // warp-level MMA pass on the interleaved split of FP32 X (<= 32 rows, rank bucket 8)
+  int tcw = 0;       // warp-level MMA pass: on the interleaved split of FP32 X (17..32 rows, rank bucket 8),
+                     // or with bf16 on BF16 X (<= 16 rows, rank bucket 16)
   int route = NTT_ROUTE_AUTO;   // ntt_route restricting the pass choice
   int split_ok = 0;  // scratch for the two BF16 terms of X exists (MuDev::xs)
   int64_t ldh = 0;   // row stride of H when it is a column block of a wider H (generic pass only)
@@ -431,6 +432,10 @@ size_t split_blocked_bytes(int64_t n, int MP);
 size_t split_scratch_bytes(int64_t m, int64_t n);
 cudaError_t launch_split_blocked(const float* X, void* out, int64_t m, int64_t n, int MP, cudaStream_t st);
 bool tcw_route_ok(int64_t m, int64_t n, int r, int route);
+bool tcwb_route_ok(int64_t m, int64_t n, int r, int route);
+ntt_status encode_tcwb_maps(const MuShape& s, const void* X, const float* H, CUtensorMap* mx, CUtensorMap* mh);
+cudaError_t launch_mu_pass_tcwb(const MuShape& s, const MuDev& d, float eps, const CUtensorMap& mx,
+                                const CUtensorMap& mh, cudaStream_t st);
 cudaError_t launch_split_x12(const float* X, __nv_bfloat16* out, int64_t m, int64_t n, cudaStream_t st);
 ntt_status encode_tcw_maps(const MuShape& s, const __nv_bfloat16* X12, const float* H, CUtensorMap* mx,
                            CUtensorMap* mh);

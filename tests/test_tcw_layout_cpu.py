@@ -279,3 +279,161 @@ def test_precomputed_lane_offsets_match_the_layout():
                 assert tile[w] == (g, 2 * t + 8 * h) and tile[w + 1] == (g, 2 * t + 8 * h + 1)
                 banks += [w % 32, (w + 1) % 32]
             assert len(set(banks)) == 32
+
+
+# ---------------------------------------------------------------------------
+# The BF16-X form (mu_pass_tcwb.cu): 16 rows as X lines (row = line), rank 16
+# in two n-tiles, G H on the MMAs from an H^T A fragment, Q = Qa + Qb + Qb^T.
+
+def _h16_addr(t, g, c0, e, q, h):
+    """The kernel's H box offset of (rank 2t + e + 8q, column c0 + g + 8h)."""
+    hl = [4 * t * 128 + ((g >> 2) << 4) + (g & 3) * 4, 4 * t * 128 + 128 + (((g >> 2) ^ 1) << 4) + (g & 3) * 4]
+    A = ((c0 & 31) >> 2) + 2 * h
+    return hl[c0 >> 5] + (2 * e + 16 * q) * 128 + (((A ^ (2 * e)) ^ (4 * (t & 1))) << 4)
+
+
+def test_bf16_form_stage_model_reproduces_the_products():
+    rng = np.random.default_rng(9)
+    m = r = 16
+    X = bf16(rng.random((m, SEG)).astype(np.float32))          # exact BF16 operand
+    W = rng.random((m, r)).astype(np.float32)
+    H = rng.random((r, SEG)).astype(np.float32)
+    G = (W.astype(np.float64).T @ W).astype(np.float32)
+    eps = 1e-12
+    xmem = {}
+    for i in range(m):
+        for c in range(SEG):
+            xmem[i * 128 + (((c >> 3) ^ (i & 7)) << 4) + (c & 7) * 2] = X[i, c]
+    hmem = {}
+    for k in range(r):
+        for c in range(SEG):
+            hmem[h_off(k, c)] = H[k, c]
+    # the kernel's H address formula equals the layout's
+    for lane in range(32):
+        g, t = lane >> 2, lane & 3
+        for ck in range(4):
+            for e in range(2):
+                for q in range(2):
+                    for h in range(2):
+                        assert _h16_addr(t, g, 16 * ck, e, q, h) == h_off(2 * t + e + 8 * q, 16 * ck + g + 8 * h)
+    Wt3 = split3(W)
+    Gt = split3(G)
+    def pi(k):
+        return (k & 7 & 3) ^ ((k & 7) >> 2)
+    accP = [np.zeros((32, 4)) for _ in range(2)]
+    Qa = [np.zeros((32, 4)) for _ in range(2)]
+    Qb = [np.zeros((32, 4)) for _ in range(2)]
+    Hn_all = np.zeros((r, SEG))
+    for ck in range(4):
+        c0 = 16 * ck
+        # Y: one K step over the 16 rows
+        addrs = []
+        for lane in range(32):
+            lj, li = lane >> 3, lane & 7
+            ly, lamy = (li + 8 * (lj >> 1)) * 128, li ^ (lj & 1)
+            addrs.append(ly + (((2 * ck) ^ lamy) << 4))
+        check_phases(addrs)
+        a = ldmatrix_x4(xmem, addrs, trans=True)
+        y = [np.zeros((32, 4)) for _ in range(2)]
+        for nt in range(2):
+            for Wt in Wt3:
+                b = []
+                for lane in range(32):
+                    g, t = lane >> 2, lane & 3
+                    b.append([(Wt[2 * t, 8 * nt + g], Wt[2 * t + 1, 8 * nt + g]),
+                              (Wt[2 * t + 8, 8 * nt + g], Wt[2 * t + 9, 8 * nt + g])])
+                mma(a, b, y[nt])
+        # G H from the H^T fragment (three terms) and G (three terms)
+        hv = []
+        for lane in range(32):
+            g, t = lane >> 2, lane & 3
+            v = {}
+            for q in range(2):
+                for h in range(2):
+                    v[(q, h)] = np.array([hmem[_h16_addr(t, g, c0, 0, q, h)], hmem[_h16_addr(t, g, c0, 1, q, h)]],
+                                         dtype=np.float32)
+            hv.append(v)
+        ht = [{key: split3(val) for key, val in hv[l].items()} for l in range(32)]
+        def afr(term):
+            return [[tuple(ht[l][(0, 0)][term]), tuple(ht[l][(0, 1)][term]), tuple(ht[l][(1, 0)][term]),
+                     tuple(ht[l][(1, 1)][term])] for l in range(32)]
+        gh = [np.zeros((32, 4)) for _ in range(2)]
+        for nt in range(2):
+            def bgf(term):
+                return [[(Gt[term][2 * (l & 3), 8 * nt + (l >> 2)], Gt[term][2 * (l & 3) + 1, 8 * nt + (l >> 2)]),
+                         (Gt[term][2 * (l & 3) + 8, 8 * nt + (l >> 2)], Gt[term][2 * (l & 3) + 9, 8 * nt + (l >> 2)])]
+                        for l in range(32)]
+            for ta, tb in ((0, 0), (0, 1), (1, 0), (0, 2), (2, 0), (1, 1)):
+                mma(afr(ta), bgf(tb), gh[nt])
+        Yref = W.astype(np.float64).T @ X.astype(np.float64)
+        GHref = G.astype(np.float64) @ H.astype(np.float64)
+        hn = [np.zeros((32, 4)) for _ in range(2)]
+        for lane in range(32):
+            g, t = lane >> 2, lane & 3
+            for nt in range(2):
+                for q in range(4):
+                    col, k = c0 + g + 8 * (q >> 1), 8 * nt + 2 * t + (q & 1)
+                    assert np.isclose(y[nt][lane][q], Yref[k, col], rtol=1e-6)
+                    assert np.isclose(gh[nt][lane][q], GHref[k, col], rtol=1e-6)
+                    h0 = hv[lane][(nt, q >> 1)][q & 1]
+                    assert h0 == H[k, col]
+                    hn[nt][lane][q] = max(0.0, h0 * y[nt][lane][q] / (gh[nt][lane][q] + eps))
+                    Hn_all[k, col] = hn[nt][lane][q]
+        # staging tile and the B fragments of H_new^T
+        tile = {}
+        for lane in range(32):
+            g, t = lane >> 2, lane & 3
+            for nt in range(2):
+                for e in range(2):
+                    k = 8 * nt + 2 * t + e
+                    for h in range(2):
+                        tile[k * 32 + ((g + 8 * h) ^ (8 * pi(k)))] = hn[nt][lane][2 * h + e]
+        hb = []
+        for lane in range(32):
+            g, t = lane >> 2, lane & 3
+            per = []
+            for nt in range(2):
+                k = 8 * nt + g
+                w0 = k * 32 + ((2 * t) ^ (8 * pi(k)))
+                w1 = k * 32 + ((2 * t + 8) ^ (8 * pi(k)))
+                per.append((split3(np.array([tile[w0], tile[w0 + 1]], dtype=np.float32)),
+                            split3(np.array([tile[w1], tile[w1 + 1]], dtype=np.float32))))
+            hb.append(per)
+        # P
+        addrs = []
+        for lane in range(32):
+            lj, li = lane >> 3, lane & 7
+            lp, lamp = (li + 8 * (lj & 1)) * 128, li ^ (lj >> 1)
+            addrs.append(lp + (((2 * ck) ^ lamp) << 4))
+        check_phases(addrs)
+        a = ldmatrix_x4(xmem, addrs, trans=False)
+        for nt in range(2):
+            for term in range(3):
+                mma(a, [[tuple(hb[l][nt][0][term]), tuple(hb[l][nt][1][term])] for l in range(32)], accP[nt])
+        # Q
+        def qa(term):
+            return [[tuple(hb[l][0][0][term]), tuple(hb[l][1][0][term]), tuple(hb[l][0][1][term]),
+                     tuple(hb[l][1][1][term])] for l in range(32)]
+        for nt in range(2):
+            def qb(term):
+                return [[tuple(hb[l][nt][0][term]), tuple(hb[l][nt][1][term])] for l in range(32)]
+            mma(qa(0), qb(0), Qa[nt])
+            mma(qa(1), qb(1), Qa[nt])
+            mma(qa(0), qb(1), Qb[nt])
+            mma(qa(0), qb(2), Qb[nt])
+    P = np.zeros((m, r))
+    Qm = np.zeros((r, r))
+    Qt = np.zeros((r, r))
+    for lane in range(32):
+        g, t = lane >> 2, lane & 3
+        for nt in range(2):
+            for q in range(4):
+                row, col = g + 8 * (q >> 1), 8 * nt + 2 * t + (q & 1)
+                P[row, col] = accP[nt][lane][q]
+                Qm[row, col] = Qa[nt][lane][q] + Qb[nt][lane][q]
+                Qt[row, col] = Qb[nt][lane][q]
+    Q = Qm + Qt.T
+    Hn_ref = np.maximum(0.0, H * (W.astype(np.float64).T @ X) / (G.astype(np.float64) @ H + eps))
+    assert np.allclose(Hn_all, Hn_ref, rtol=5e-5)
+    assert np.allclose(P, X.astype(np.float64) @ Hn_all.T, rtol=1e-6)
+    assert np.allclose(Q, Hn_all @ Hn_all.T, rtol=1e-6)
