@@ -140,7 +140,8 @@ typedef struct {
 #define NTT_ENGINE_FMA_NARROW 4       /* warp-streamed FMA pass: <= 32 rows, rank <= 8, FP32 X */
 #define NTT_ENGINE_BCD_PASS 5         /* the fused pass in its BCD (Algorithm 3) mode */
 #define NTT_ENGINE_TC_SPLIT 6         /* FP32 X split in two BF16 matrices on the tensor-core pass */
-#define NTT_ENGINE_TC_NARROW 7        /* <= 32 rows, rank <= 8, FP32 X split in two BF16 terms: warp-level MMAs */
+#define NTT_ENGINE_TC_NARROW 7        /* warp-level BF16 MMAs: FP32 X of 17..32 rows at rank <= 8 split in two
+                                         BF16 terms, or BF16 X of <= 16 rows at rank 9..16 */
 
 /* Human-readable name of a status code (static string). */
 const char* ntt_status_string(ntt_status s);
