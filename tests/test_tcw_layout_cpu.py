@@ -437,3 +437,30 @@ def test_bf16_form_stage_model_reproduces_the_products():
     assert np.allclose(Hn_all, Hn_ref, rtol=5e-5)
     assert np.allclose(P, X.astype(np.float64) @ Hn_all.T, rtol=1e-6)
     assert np.allclose(Q, Hn_all @ Hn_all.T, rtol=1e-6)
+
+
+def test_bf16_form_staging_tile_is_conflict_free():
+    """The 16-rank staging tile of the BF16-X form: the lane's eight stores
+    (ranks 8 nt + 2t + e, columns g + 8h) and four 8-byte B-fragment loads
+    (rank 8 nt + g, columns 2t + 8h, + 1) each cover the 32 banks once, and
+    every (rank, column) of the 16 x 16 chunk has its own word."""
+    def pi(k):
+        return (k & 7 & 3) ^ ((k & 7) >> 2)
+
+    seen = set()
+    for nt in range(2):
+        for e in range(2):
+            for h in range(2):
+                words = [(8 * nt + 2 * (l & 3) + e) * 32 + (((l >> 2) + 8 * h) ^ (8 * pi(8 * nt + 2 * (l & 3) + e)))
+                         for l in range(32)]
+                assert len({w % 32 for w in words}) == 32
+                seen.update(words)
+        for h in range(2):
+            for p0 in (0, 16):
+                banks = []
+                for l in range(p0, p0 + 16):
+                    g, t = l >> 2, l & 3
+                    w = (8 * nt + g) * 32 + ((2 * t + 8 * h) ^ (8 * pi(8 * nt + g)))
+                    banks += [w % 32, (w + 1) % 32]
+                assert len(set(banks)) == 32
+    assert len(seen) == 256 and max(seen) < 512
