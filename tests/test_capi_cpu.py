@@ -191,3 +191,24 @@ def test_many_validation(lib):
     ptrs = (vp * 1)(None)
     assert lib.nmf_mu_many(1, i64(8), i64(8), i32(2), ptrs, ptrs, ptrs, 1, ctypes.c_float(1e-12),
                            vp(256), None) == 1                                                  # null factors
+
+
+def test_split_scratch_in_single_nmf_workspaces(lib):
+    """The tensor-core forms that read a split X get its scratch in the
+    nmf_mu_step_route workspace, and only where their route lets them run:
+    4 m n bytes for the warp-level MMA form (17..32 rows, rank <= 8, n a
+    multiple of 64) on the default route, the tile-major image (whole 64-column
+    tiles of the padded rows) for the split form with route "tc", nothing for
+    BF16 X (an exact operand) or on the CUDA-core routes."""
+    m, n = 32, 64 * 100
+    auto = ntt.nmf_mu_workspace_size(m, n, 8, "f32", "auto")
+    fma = ntt.nmf_mu_workspace_size(m, n, 8, "f32", "fma")
+    assert auto - fma >= 4 * m * n
+    # n % 64 != 0: the narrow FMA pass, no split scratch
+    assert ntt.nmf_mu_workspace_size(m, n + 8, 8, "f32", "auto") == ntt.nmf_mu_workspace_size(m, n + 8, 8, "f32", "fma")
+    m2, n2 = 200, 64 * 50 + 8                        # 256-row bucket, ragged last tile
+    tc = ntt.nmf_mu_workspace_size(m2, n2, 16, "f32", "tc")
+    plain = ntt.nmf_mu_workspace_size(m2, n2, 16, "f32", "fma")
+    assert tc - plain >= ((n2 + 63) // 64) * 256 * 256
+    assert (ntt.nmf_mu_workspace_size(16, 64 * 100, 16, "bf16", "auto")
+            == ntt.nmf_mu_workspace_size(16, 64 * 100, 16, "bf16", "fma"))
